@@ -1,0 +1,208 @@
+/*
+ * sme.h -- C ABI of the GB300 shape-adaptive motion estimation library.
+ *
+ * The library implements, on one GPU, the per-macroblock procedure of
+ * Benboubker, Abdi and Ahaitouf, "Shape-Adaptive Motion Estimation Algorithm
+ * for MPEG-4 Video Coding": classification of each 16x16 macroblock (MB) from
+ * its binary alpha block (BAB) (Fig. 1, Sec. 3.1), the block recursive search
+ * over the neighbour and temporal candidates A, B, C, T (Fig. 1, Fig. 3) with
+ * a shape cost on boundary MBs and a texture (SAD) cost on opaque MBs, the
+ * pixel recursive gradient search of Sec. 3.2 (Eqs. 2-5, Fig. 4) on opaque
+ * MBs, and motion compensation with PSNR (Sec. 4).
+ *
+ * Conventions shared by every call
+ *  - Frames are 8-bit, row-major, pitch = width bytes, frame after frame
+ *    ([n_frames][height][width]); width and height are multiples of 16.
+ *    Luma is gray level; alpha is 0 (outside the object) or nonzero (inside).
+ *  - MB m = v * (width/16) + h is the MB at column h, row v.  M = MB count.
+ *  - Vectors (sme_mv) are in units of 1/subpel pixel.  The prediction of
+ *    current pixel p is reference(p + mv) (backward matching, Sec. 2).
+ *  - Valid vectors V: the displaced 16x16 block lies inside the reference
+ *    frame and |dx|, |dy| <= search_range * subpel.  Every vector the library
+ *    returns lies in V; every candidate is clamped into V before use.
+ *  - Pair k of a sequence uses frame k as reference and frame
+ *    k + ref_distance as current; P = n_frames - ref_distance pairs.  The
+ *    temporal candidate of pair k is the field of pair k-1 (temporal_in, or
+ *    zero vectors, for pair 0).
+ *  - Unless a call says "host", every data pointer is DEVICE memory owned by
+ *    the caller, must stay valid until the work queued on the context's
+ *    stream has finished, and is never freed or retained by the library.
+ *    Frame pointers must be 16-byte aligned.
+ *  - Calls are asynchronous on the context's stream unless they say they
+ *    synchronise.  Argument errors are returned immediately; a device-side
+ *    failure (a bounded wait that gave up) is reported by the next
+ *    sme_synchronize (or by a synchronising call).
+ *  - Every call returns an SME_* status; nothing throws or aborts.
+ *  - One context serves one stream at a time; calls that overlap on the GPU
+ *    through the same context race on its scratch buffers.
+ */
+#ifndef SME_H
+#define SME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SME_OK = 0,
+    SME_ERR_ARG = 1,     /* null or out-of-range argument, misaligned pointer */
+    SME_ERR_SIZE = 2,    /* width/height not a positive multiple of 16, or too large */
+    SME_ERR_CUDA = 3,    /* a CUDA runtime call failed */
+    SME_ERR_TIMEOUT = 4, /* a bounded device wait gave up (results are incomplete) */
+    SME_ERR_STATE = 5,   /* call made in the wrong state (e.g. estimate before set_current) */
+    SME_ERR_NOMEM = 6,   /* device or host allocation failed */
+    SME_ERR_RANGE = 7    /* a caller-supplied vector lies outside V */
+};
+
+enum { SME_TRANSPARENT = 0, SME_OPAQUE = 1, SME_BOUNDARY = 2 };
+
+typedef struct sme_ctx sme_ctx;
+
+typedef struct {
+    int width, height;  /* pixels, multiples of 16, 16..8192 */
+    int search_range;   /* S in pixels, 1..64 (window (2S+1)^2, Eq. 6) */
+    int subpel;         /* 1 = full-pel, 2 = half-pel (MPEG-4 bilinear, rounding control 0) */
+    float theta;        /* Theta of Eq. 4 (gradient threshold), > 0; default 2 */
+    float epsilon;      /* convergence factor of Eq. 2, (0, 4]; default 1 */
+    int max_iters;      /* cap on pixel-recursive iterations, 0..16; default 8 */
+    int ref_distance;   /* frames between reference and current, >= 1; default 1 */
+} sme_params;
+
+typedef struct {
+    int16_t dx, dy;
+} sme_mv;
+
+/* Per-MB and per-pair results of an estimate.  `mv` is required; every other
+ * pointer may be NULL.  Sizes are for P pairs of M MBs. */
+typedef struct {
+    sme_mv* mv;               /* [P][M] final vectors */
+    uint32_t* cost;           /* [P][M] final cost: SAD (opaque) or alpha mismatches (boundary) */
+    float* disp;              /* [P][M][2] last FP32 gradient update (pixels), Eq. 3; 0 if none */
+    uint8_t* iters;           /* [P][M] pixel-recursive iterations run */
+    uint8_t* npos;            /* [P][M] distinct vectors whose cost was evaluated (Table 1 unit) */
+    uint8_t* mb_class;        /* [P][M] class of the current frame's MB (SME_TRANSPARENT...) */
+    uint32_t* sse_mb;         /* [P][M] sum of squared prediction errors of the MB */
+    unsigned long long* sse;  /* [P] whole-frame sum of squared prediction errors */
+    uint8_t* pred;            /* [P][height][width] motion-compensated prediction */
+} sme_outputs;
+
+/* Fill *p with the defaults above for a width x height sequence. */
+void sme_default_params(sme_params* p, int width, int height);
+
+/* Static text for a status code. */
+const char* sme_strerror(int status);
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Allocates the
+ * context's own device scratch (packed alpha, class map, ready flags),
+ * grown on demand by later calls.  Returns SME_ERR_ARG/SIZE on bad params. */
+int sme_create(sme_ctx** out, const sme_params* p, void* cuda_stream);
+
+/* Free the context and its device scratch (synchronises its stream). */
+int sme_destroy(sme_ctx* ctx);
+
+/* Rebind the context to another stream. */
+int sme_set_stream(sme_ctx* ctx, void* cuda_stream);
+
+/* Wait for the context's stream, then report (and clear) a device-side
+ * failure of the work queued since the previous sme_synchronize. */
+int sme_synchronize(sme_ctx* ctx);
+
+/* Fig. 1 "Block_Type": classify every MB of `n_frames` alpha frames.
+ *   alpha    [n_frames][H][W] device, 16-byte aligned
+ *   mb_class [n_frames][M] device out: 0 transparent (no pixel inside),
+ *            1 opaque (all 256 inside), 2 boundary
+ *   packed   optional device out [n_frames][H][sme_packed_words(W)] uint32:
+ *            bit b of word k of a row = (alpha[32k+b] != 0); trailing words 0. */
+int sme_classify(sme_ctx* ctx, const uint8_t* alpha, int n_frames, uint8_t* mb_class,
+                 uint32_t* packed);
+
+/* Words per row of the packed alpha layout above. */
+int sme_packed_words(int width);
+
+/* The whole per-MB pass of Fig. 1 over a sequence (classification, block
+ * recursive search, pixel recursive search, motion compensation and SSE),
+ * for all P pairs in one persistent launch.
+ *   luma, alpha  [n_frames][H][W] device
+ *   temporal_in  [M] device or NULL: temporal candidates of pair 0
+ *   seed         [P][M][2] device FP32 pixels or NULL: an extra candidate per
+ *                MB evaluated after T (rounded to the MV grid, clamped to V)
+ *   out          outputs as described in sme_outputs (device pointers)
+ * Needs n_frames > ref_distance. */
+int sme_estimate_sequence(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha, int n_frames,
+                          const sme_mv* temporal_in, const float* seed, const sme_outputs* out);
+
+/* Same as sme_estimate_sequence with every pointer (inputs and outputs) in
+ * HOST memory: copies inputs to context-owned device buffers, runs, copies
+ * the requested outputs back and synchronises.  Pinned host memory gives the
+ * fastest copies. */
+int sme_estimate_sequence_host(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha,
+                               int n_frames, const sme_mv* temporal_in, const float* seed,
+                               const sme_outputs* out);
+
+/* Stateful pair interface (Sec. 2 problem statement: find, for every block
+ * of the current frame, the vector minimising the matching error against
+ * the reference).  set_reference / set_current copy one luma + alpha frame
+ * (device) into context-owned buffers.  sme_estimate runs one pair with the
+ * context's temporal field as T and keeps the result; sme_advance makes the
+ * current frame the reference and the result the temporal field.  sme_score
+ * synchronises and returns the PSNR (dB) of the last estimate's prediction. */
+int sme_set_reference(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha);
+int sme_set_current(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha);
+int sme_estimate(sme_ctx* ctx, const sme_outputs* out /* P = 1; may be NULL */);
+int sme_advance(sme_ctx* ctx);
+int sme_score(sme_ctx* ctx, double* psnr_db);
+int sme_get_temporal_field(sme_ctx* ctx, sme_mv* field /* [M] device out */);
+int sme_set_temporal_field(sme_ctx* ctx, const sme_mv* field /* [M] device, NULL = zeros */);
+
+/* Motion compensation of one frame pair with a caller-supplied field (Sec. 4):
+ * pred(p) = ref(p + mv(mb(p))) with half-sample interpolation, and the SSE
+ * against cur.  Every vector must lie in V: otherwise the MB is skipped and
+ * the next sme_synchronize returns SME_ERR_RANGE.
+ *   ref, cur [H][W] device; mv [M] device; pred [H][W] device or NULL;
+ *   sse one device unsigned long long (overwritten). */
+int sme_compensate(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur, const sme_mv* mv,
+                   uint8_t* pred, unsigned long long* sse);
+
+/* PSNR in dB of an 8-bit width x height frame from its SSE (Sec. 4);
+ * +infinity when sse == 0.  Host only. */
+double sme_psnr(unsigned long long sse, int width, int height);
+
+/* Cost queries through the same device code as the estimate.  queries is
+ * [n][3] int32 device (mb, dx, dy) with (dx, dy) in V of that MB.  Outputs
+ * [n] device, either may be NULL: the texture SAD of the 16x16 block
+ * (Fig. 1 opaque branch) and the alpha mismatch count (boundary branch,
+ * full-pel part trunc(d/subpel)).  ref/cur luma [H][W], aref/acur alpha. */
+int sme_eval_costs(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur, const uint8_t* aref,
+                   const uint8_t* acur, const int32_t* queries, int n, uint32_t* texture_sad,
+                   uint32_t* shape_sad);
+
+/* One FP32 gradient update (Eqs. 3-5) per query (mb, dx, dy) through the
+ * same device code as the estimate; delta [n][2] device out, in pixels. */
+int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
+                      const int32_t* queries, int n, float* delta);
+
+/* Stage timing (tracing).  sme_profile_begin makes every following
+ * sme_estimate_sequence* call record CUDA events around its two launches on
+ * the context's stream (classification, then the persistent ME launch), for
+ * up to max_calls calls.  sme_profile_end synchronises and returns the number
+ * of calls recorded and the summed device time of each stage in ms, then
+ * stops recording.  Any output pointer may be NULL. */
+int sme_profile_begin(sme_ctx* ctx, int max_calls);
+int sme_profile_end(sme_ctx* ctx, int* calls, double* classify_ms, double* me_ms);
+
+/* Failure injection for tests.  With skip_ticket >= 0 the estimate's MB of
+ * that schedule position never publishes its result, so the MBs that depend
+ * on it wait until `timeout_ns` and the launch ends with SME_ERR_TIMEOUT.
+ * skip_ticket = -1 restores normal operation; timeout_ns <= 0 restores the
+ * default wait limit (1 s). */
+int sme_debug_set_fault(sme_ctx* ctx, int skip_ticket, long long timeout_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SME_H */

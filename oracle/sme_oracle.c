@@ -268,9 +268,9 @@ int orc_estimate_pair(const orc_params* P, const uint8_t* ref, const uint8_t* cu
             if (v > 0 && u < mbw - 1) { cx[2] = mv[m - mbw + 1].dx; cy[2] = mv[m - mbw + 1].dy; } /* C */
             if (temporal) { cx[3] = temporal[m].dx; cy[3] = temporal[m].dy; }              /* T */
             int nc = 4;
-            if (seed) { /* injected proposal: rounded to the MV grid */
-                cx[4] = (int)roundf((float)h * seed[2 * m]);
-                cy[4] = (int)roundf((float)h * seed[2 * m + 1]);
+            if (seed) { /* injected proposal: saturated to +-1024 MV units, rounded to the grid */
+                cx[4] = (int)roundf(fminf(fmaxf((float)h * seed[2 * m], -1024.0f), 1024.0f));
+                cy[4] = (int)roundf(fminf(fmaxf((float)h * seed[2 * m + 1], -1024.0f), 1024.0f));
                 nc = 5;
             }
             pos_set ps;

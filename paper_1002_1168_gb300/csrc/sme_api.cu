@@ -1,0 +1,623 @@
+// C ABI of the shape-adaptive motion estimation library (declared in
+// include/sme.h): argument checks, context-owned device scratch, the
+// wavefront schedule, and the launch sequence of each call.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "sme_internal.h"
+
+using namespace sme;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct sme_ctx {
+    sme_params prm;
+    Geom g;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0, me_blocks_per_sm = 0;
+    DevStatus* status = nullptr;
+    DevBuf packed, cls, ready, sched, qpacked, qcls;
+    std::vector<int> sched_host;
+    int sched_P = -1;
+    unsigned epoch = 0;
+    int fault_ticket = -1;
+    long long timeout_ns = kDefaultTimeoutNs;
+    // pair interface
+    DevBuf pair_luma, pair_alpha, temporal, last_mv, last_sse;
+    bool have_ref = false, have_cur = false, have_temporal = false, have_result = false;
+    // stage timing: three events per recorded call
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_max = 0, prof_n = 0;
+    // host-buffer interface
+    DevBuf h_luma, h_alpha, h_tmp, h_seed, h_mv, h_cost, h_disp, h_iters, h_npos, h_cls, h_ssemb,
+        h_sse, h_pred;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? SME_OK : SME_ERR_CUDA; }
+
+int ensure(DevBuf& b, size_t bytes, bool zero = false, cudaStream_t s = nullptr)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return SME_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SME_ERR_NOMEM;
+    }
+    b.bytes = bytes;
+    if (zero && cudaMemsetAsync(b.p, 0, bytes, s) != cudaSuccess) return SME_ERR_CUDA;
+    return SME_OK;
+}
+
+void release(DevBuf& b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_params(const sme_params* p)
+{
+    if (!p) return SME_ERR_ARG;
+    if (p->width <= 0 || p->height <= 0 || p->width % 16 || p->height % 16 || p->width > kMaxDim ||
+        p->height > kMaxDim)
+        return SME_ERR_SIZE;
+    if (p->search_range < 1 || p->search_range > kMaxSearch) return SME_ERR_ARG;
+    if (p->subpel != 1 && p->subpel != 2) return SME_ERR_ARG;
+    if (!(p->theta > 0.0f) || !isfinite(p->theta)) return SME_ERR_ARG;
+    if (!(p->epsilon > 0.0f) || !(p->epsilon <= 4.0f)) return SME_ERR_ARG;
+    if (p->max_iters < 0 || p->max_iters > kMaxIters) return SME_ERR_ARG;
+    if (p->ref_distance < 1) return SME_ERR_ARG;
+    return SME_OK;
+}
+
+Geom make_geom(const sme_params& p)
+{
+    Geom g;
+    g.W = p.width;
+    g.H = p.height;
+    g.MBW = p.width / 16;
+    g.MBH = p.height / 16;
+    g.M = g.MBW * g.MBH;
+    g.Wp = (p.width + 31) / 32 + 1;
+    g.S = p.search_range;
+    g.h = p.subpel;
+    g.K = p.max_iters;
+    g.theta = p.theta;
+    g.eps = p.epsilon;
+    return g;
+}
+
+// Ticket order of the persistent launch: MB (u, v) of pair k becomes ready
+// at wavefront step t = u + 2v + k (A, B, C of Fig. 3 sit at steps t-1,
+// t-2, t-1 of the same pair; T is step t-1 of the previous pair), so listing
+// MBs by increasing t puts every dependency before its dependents.
+int build_schedule(sme_ctx* c, int P)
+{
+    if (c->sched_P == P) return SME_OK;
+    const Geom& g = c->g;
+    const size_t total = (size_t)P * g.M;
+    if (total > (size_t)INT32_MAX) return SME_ERR_SIZE;
+    try {
+        c->sched_host.assign(total, 0);
+    } catch (...) {
+        return SME_ERR_NOMEM;
+    }
+    const int tmax = (g.MBW - 1) + 2 * (g.MBH - 1) + (P - 1);
+    size_t n = 0;
+    for (int t = 0; t <= tmax; ++t)
+        for (int k = 0; k < P; ++k)
+            for (int v = 0; v < g.MBH; ++v) {
+                const int u = t - 2 * v - k;
+                if (u < 0) break;
+                if (u < g.MBW) c->sched_host[n++] = k * g.M + v * g.MBW + u;
+            }
+    if (n != total) return SME_ERR_STATE;
+    int rc = ensure(c->sched, total * sizeof(int));
+    if (rc) return rc;
+    if (cudaMemcpyAsync(c->sched.p, c->sched_host.data(), total * sizeof(int), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess)
+        return SME_ERR_CUDA;
+    c->sched_P = P;
+    return SME_OK;
+}
+
+int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, const sme_mv* temporal_in,
+                 const float* seed, const sme_outputs* out)
+{
+    const Geom& g = c->g;
+    if (!luma || !alpha || !out || !out->mv) return SME_ERR_ARG;
+    if (!aligned16(luma) || !aligned16(alpha)) return SME_ERR_ARG;
+    const int rd = c->prm.ref_distance;
+    if (F <= rd) return SME_ERR_ARG;
+    const int P = F - rd;
+    const size_t total = (size_t)P * g.M;
+    int rc;
+    if ((rc = ensure(c->packed, (size_t)F * g.H * g.Wp * sizeof(uint32_t)))) return rc;
+    if ((rc = ensure(c->cls, (size_t)F * g.M))) return rc;
+    if ((rc = ensure(c->ready, total * sizeof(unsigned), true, c->stream))) return rc;
+    if ((rc = build_schedule(c, P))) return rc;
+
+    ClassifyArgs ca{};
+    ca.alpha = alpha;
+    ca.n_frames = F;
+    ca.cls = (uint8_t*)c->cls.p;
+    ca.packed = (uint32_t*)c->packed.p;
+    ca.status = c->status;
+    ca.sse = out->sse;
+    ca.n_sse = P;
+    cudaEvent_t* ev = nullptr;
+    if (c->prof_n < c->prof_max) {
+        ev = &c->prof_ev[3 * c->prof_n++];
+        if (cudaEventRecord(ev[0], c->stream) != cudaSuccess) return SME_ERR_CUDA;
+    }
+    if (launch_classify(g, ca, c->stream) != cudaSuccess) return SME_ERR_CUDA;
+    if (ev && cudaEventRecord(ev[1], c->stream) != cudaSuccess) return SME_ERR_CUDA;
+
+    if (++c->epoch == 0) c->epoch = 1;
+    MeArgs a{};
+    a.luma = luma;
+    a.packed = (const uint32_t*)c->packed.p;
+    a.cls = (const uint8_t*)c->cls.p;
+    a.temporal_in = temporal_in;
+    a.seed = seed;
+    a.mv = out->mv;
+    a.cost = out->cost;
+    a.disp = out->disp;
+    a.iters = out->iters;
+    a.npos = out->npos;
+    a.out_cls = out->mb_class;
+    a.sse_mb = out->sse_mb;
+    a.sse = out->sse;
+    a.pred = out->pred;
+    a.sched = (const int*)c->sched.p;
+    a.ready = (unsigned*)c->ready.p;
+    a.status = c->status;
+    a.epoch = c->epoch;
+    a.P = P;
+    a.rd = rd;
+    a.total = (int)total;
+    a.fault_ticket = c->fault_ticket;
+    a.timeout_ns = c->timeout_ns;
+    const long long cap = (long long)c->num_sms * c->me_blocks_per_sm;
+    const int grid = (int)std::max(1LL, std::min<long long>(cap, (long long)total));
+    if (launch_me(g, a, grid, c->stream) != cudaSuccess) return SME_ERR_CUDA;
+    if (ev && cudaEventRecord(ev[2], c->stream) != cudaSuccess) return SME_ERR_CUDA;
+    return SME_OK;
+}
+
+void profile_free(sme_ctx* c)
+{
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof_max = c->prof_n = 0;
+}
+
+int read_status(sme_ctx* c)
+{
+    int err = 0;
+    if (cudaMemcpy(&err, &c->status->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SME_ERR_CUDA;
+    if (err) {
+        if (cudaMemset(&c->status->err, 0, sizeof(int)) != cudaSuccess) return SME_ERR_CUDA;
+        return err;
+    }
+    return SME_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sme_default_params(sme_params* p, int width, int height)
+{
+    if (!p) return;
+    p->width = width;
+    p->height = height;
+    p->search_range = 16;
+    p->subpel = 1;
+    p->theta = 2.0f;
+    p->epsilon = 1.0f;
+    p->max_iters = 8;
+    p->ref_distance = 1;
+}
+
+const char* sme_strerror(int s)
+{
+    switch (s) {
+    case SME_OK: return "ok";
+    case SME_ERR_ARG: return "invalid argument";
+    case SME_ERR_SIZE: return "width/height must be positive multiples of 16 (at most 8192)";
+    case SME_ERR_CUDA: return "CUDA runtime error";
+    case SME_ERR_TIMEOUT: return "a bounded device wait gave up; results are incomplete";
+    case SME_ERR_STATE: return "call made in the wrong state";
+    case SME_ERR_NOMEM: return "allocation failed";
+    case SME_ERR_RANGE: return "a supplied motion vector lies outside the valid set";
+    default: return "unknown status";
+    }
+}
+
+int sme_packed_words(int width) { return width > 0 ? (width + 31) / 32 + 1 : 0; }
+
+int sme_create(sme_ctx** out, const sme_params* p, void* stream)
+{
+    if (!out) return SME_ERR_ARG;
+    *out = nullptr;
+    int rc = check_params(p);
+    if (rc) return rc;
+    sme_ctx* c = new (std::nothrow) sme_ctx();
+    if (!c) return SME_ERR_NOMEM;
+    c->prm = *p;
+    c->g = make_geom(*p);
+    c->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        me_occupancy(c->g, &c->me_blocks_per_sm) != cudaSuccess || c->me_blocks_per_sm < 1) {
+        cudaGetLastError();
+        delete c;
+        return SME_ERR_CUDA;
+    }
+    if (cudaMalloc(&c->status, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMemset(c->status, 0, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->status) cudaFree(c->status);
+        delete c;
+        return SME_ERR_NOMEM;
+    }
+    *out = c;
+    return SME_OK;
+}
+
+int sme_destroy(sme_ctx* c)
+{
+    if (!c) return SME_ERR_ARG;
+    cudaStreamSynchronize(c->stream);
+    DevBuf* bufs[] = {&c->packed, &c->cls, &c->ready, &c->sched, &c->qpacked, &c->qcls,
+                      &c->pair_luma, &c->pair_alpha, &c->temporal, &c->last_mv, &c->last_sse,
+                      &c->h_luma, &c->h_alpha, &c->h_tmp, &c->h_seed, &c->h_mv, &c->h_cost,
+                      &c->h_disp, &c->h_iters, &c->h_npos, &c->h_cls, &c->h_ssemb, &c->h_sse,
+                      &c->h_pred};
+    for (DevBuf* b : bufs) release(*b);
+    profile_free(c);
+    if (c->status) cudaFree(c->status);
+    delete c;
+    return SME_OK;
+}
+
+int sme_set_stream(sme_ctx* c, void* stream)
+{
+    if (!c) return SME_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return SME_OK;
+}
+
+int sme_synchronize(sme_ctx* c)
+{
+    if (!c) return SME_ERR_ARG;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SME_ERR_CUDA;
+    return read_status(c);
+}
+
+int sme_classify(sme_ctx* c, const uint8_t* alpha, int n_frames, uint8_t* mb_class, uint32_t* packed)
+{
+    if (!c || !alpha || !mb_class || n_frames < 1 || !aligned16(alpha)) return SME_ERR_ARG;
+    ClassifyArgs ca{};
+    ca.alpha = alpha;
+    ca.n_frames = n_frames;
+    ca.cls = mb_class;
+    ca.packed = packed;
+    return cuda_status(launch_classify(c->g, ca, c->stream));
+}
+
+int sme_estimate_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_frames,
+                          const sme_mv* temporal_in, const float* seed, const sme_outputs* out)
+{
+    if (!c) return SME_ERR_ARG;
+    return run_sequence(c, luma, alpha, n_frames, temporal_in, seed, out);
+}
+
+int sme_estimate_sequence_host(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_frames,
+                               const sme_mv* temporal_in, const float* seed, const sme_outputs* out)
+{
+    if (!c || !luma || !alpha || !out || !out->mv) return SME_ERR_ARG;
+    const Geom& g = c->g;
+    const int rd = c->prm.ref_distance;
+    if (n_frames <= rd) return SME_ERR_ARG;
+    const size_t FS = (size_t)g.W * g.H, P = (size_t)(n_frames - rd), PM = P * g.M;
+    const cudaStream_t s = c->stream;
+    int rc;
+    if ((rc = ensure(c->h_luma, FS * n_frames)) || (rc = ensure(c->h_alpha, FS * n_frames)) ||
+        (rc = ensure(c->h_mv, PM * sizeof(sme_mv))))
+        return rc;
+    if (cudaMemcpyAsync(c->h_luma.p, luma, FS * n_frames, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->h_alpha.p, alpha, FS * n_frames, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return SME_ERR_CUDA;
+    const sme_mv* dtmp = nullptr;
+    const float* dseed = nullptr;
+    if (temporal_in) {
+        if ((rc = ensure(c->h_tmp, g.M * sizeof(sme_mv)))) return rc;
+        if (cudaMemcpyAsync(c->h_tmp.p, temporal_in, g.M * sizeof(sme_mv), cudaMemcpyHostToDevice, s))
+            return SME_ERR_CUDA;
+        dtmp = (const sme_mv*)c->h_tmp.p;
+    }
+    if (seed) {
+        if ((rc = ensure(c->h_seed, PM * 2 * sizeof(float)))) return rc;
+        if (cudaMemcpyAsync(c->h_seed.p, seed, PM * 2 * sizeof(float), cudaMemcpyHostToDevice, s))
+            return SME_ERR_CUDA;
+        dseed = (const float*)c->h_seed.p;
+    }
+    sme_outputs d{};
+    d.mv = (sme_mv*)c->h_mv.p;
+    struct Opt {
+        void* host;
+        DevBuf* buf;
+        size_t bytes;
+        void** dev;
+    } opts[] = {
+        {out->cost, &c->h_cost, PM * 4, (void**)&d.cost},
+        {out->disp, &c->h_disp, PM * 8, (void**)&d.disp},
+        {out->iters, &c->h_iters, PM, (void**)&d.iters},
+        {out->npos, &c->h_npos, PM, (void**)&d.npos},
+        {out->mb_class, &c->h_cls, PM, (void**)&d.mb_class},
+        {out->sse_mb, &c->h_ssemb, PM * 4, (void**)&d.sse_mb},
+        {out->sse, &c->h_sse, P * 8, (void**)&d.sse},
+        {out->pred, &c->h_pred, P * FS, (void**)&d.pred},
+    };
+    for (Opt& o : opts) {
+        if (!o.host) continue;
+        if ((rc = ensure(*o.buf, o.bytes))) return rc;
+        *o.dev = o.buf->p;
+    }
+    rc = run_sequence(c, (const uint8_t*)c->h_luma.p, (const uint8_t*)c->h_alpha.p, n_frames, dtmp, dseed, &d);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(out->mv, d.mv, PM * sizeof(sme_mv), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SME_ERR_CUDA;
+    for (Opt& o : opts)
+        if (o.host && cudaMemcpyAsync(o.host, *o.dev, o.bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return SME_ERR_CUDA;
+    return sme_synchronize(c);
+}
+
+int sme_set_reference(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha)
+{
+    if (!c || !luma || !alpha) return SME_ERR_ARG;
+    const size_t FS = (size_t)c->g.W * c->g.H;
+    int rc;
+    if ((rc = ensure(c->pair_luma, 2 * FS)) || (rc = ensure(c->pair_alpha, 2 * FS))) return rc;
+    if (cudaMemcpyAsync(c->pair_luma.p, luma, FS, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->pair_alpha.p, alpha, FS, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return SME_ERR_CUDA;
+    c->have_ref = true;
+    return SME_OK;
+}
+
+int sme_set_current(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha)
+{
+    if (!c || !luma || !alpha) return SME_ERR_ARG;
+    const size_t FS = (size_t)c->g.W * c->g.H;
+    int rc;
+    if ((rc = ensure(c->pair_luma, 2 * FS)) || (rc = ensure(c->pair_alpha, 2 * FS))) return rc;
+    if (cudaMemcpyAsync((uint8_t*)c->pair_luma.p + FS, luma, FS, cudaMemcpyDeviceToDevice, c->stream) ||
+        cudaMemcpyAsync((uint8_t*)c->pair_alpha.p + FS, alpha, FS, cudaMemcpyDeviceToDevice, c->stream))
+        return SME_ERR_CUDA;
+    c->have_cur = true;
+    return SME_OK;
+}
+
+int sme_estimate(sme_ctx* c, const sme_outputs* out)
+{
+    if (!c) return SME_ERR_ARG;
+    if (!c->have_ref || !c->have_cur) return SME_ERR_STATE;
+    const Geom& g = c->g;
+    int rc;
+    if ((rc = ensure(c->last_mv, g.M * sizeof(sme_mv))) || (rc = ensure(c->last_sse, 8))) return rc;
+    sme_outputs o = out ? *out : sme_outputs{};
+    const bool user_mv = o.mv != nullptr, user_sse = o.sse != nullptr;
+    if (!user_mv) o.mv = (sme_mv*)c->last_mv.p;
+    if (!user_sse) o.sse = (unsigned long long*)c->last_sse.p;
+    // The pair always has reference distance 1 inside the context buffers.
+    const int rd = c->prm.ref_distance;
+    c->prm.ref_distance = 1;
+    rc = run_sequence(c, (const uint8_t*)c->pair_luma.p, (const uint8_t*)c->pair_alpha.p, 2,
+                      c->have_temporal ? (const sme_mv*)c->temporal.p : nullptr, nullptr, &o);
+    c->prm.ref_distance = rd;
+    if (rc) return rc;
+    if (user_mv && cudaMemcpyAsync(c->last_mv.p, o.mv, g.M * sizeof(sme_mv), cudaMemcpyDeviceToDevice, c->stream))
+        return SME_ERR_CUDA;
+    if (user_sse && cudaMemcpyAsync(c->last_sse.p, o.sse, 8, cudaMemcpyDeviceToDevice, c->stream))
+        return SME_ERR_CUDA;
+    c->have_result = true;
+    return SME_OK;
+}
+
+int sme_advance(sme_ctx* c)
+{
+    if (!c) return SME_ERR_ARG;
+    if (!c->have_cur || !c->have_result) return SME_ERR_STATE;
+    const Geom& g = c->g;
+    const size_t FS = (size_t)g.W * g.H;
+    int rc;
+    if ((rc = ensure(c->temporal, g.M * sizeof(sme_mv)))) return rc;
+    if (cudaMemcpyAsync(c->pair_luma.p, (uint8_t*)c->pair_luma.p + FS, FS, cudaMemcpyDeviceToDevice, c->stream) ||
+        cudaMemcpyAsync(c->pair_alpha.p, (uint8_t*)c->pair_alpha.p + FS, FS, cudaMemcpyDeviceToDevice, c->stream) ||
+        cudaMemcpyAsync(c->temporal.p, c->last_mv.p, g.M * sizeof(sme_mv), cudaMemcpyDeviceToDevice, c->stream))
+        return SME_ERR_CUDA;
+    c->have_temporal = true;
+    c->have_cur = false;
+    c->have_result = false;
+    return SME_OK;
+}
+
+int sme_score(sme_ctx* c, double* psnr_db)
+{
+    if (!c || !psnr_db) return SME_ERR_ARG;
+    if (!c->have_result) return SME_ERR_STATE;
+    int rc = sme_synchronize(c);
+    if (rc) return rc;
+    unsigned long long sse = 0;
+    if (cudaMemcpy(&sse, c->last_sse.p, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return SME_ERR_CUDA;
+    *psnr_db = sme_psnr(sse, c->g.W, c->g.H);
+    return SME_OK;
+}
+
+int sme_get_temporal_field(sme_ctx* c, sme_mv* field)
+{
+    if (!c || !field) return SME_ERR_ARG;
+    const size_t bytes = c->g.M * sizeof(sme_mv);
+    if (!c->have_temporal) return cuda_status(cudaMemsetAsync(field, 0, bytes, c->stream));
+    return cuda_status(cudaMemcpyAsync(field, c->temporal.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+}
+
+int sme_set_temporal_field(sme_ctx* c, const sme_mv* field)
+{
+    if (!c) return SME_ERR_ARG;
+    if (!field) {
+        c->have_temporal = false;
+        return SME_OK;
+    }
+    const size_t bytes = c->g.M * sizeof(sme_mv);
+    int rc = ensure(c->temporal, bytes);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(c->temporal.p, field, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return SME_ERR_CUDA;
+    c->have_temporal = true;
+    return SME_OK;
+}
+
+int sme_compensate(sme_ctx* c, const uint8_t* ref, const uint8_t* cur, const sme_mv* mv, uint8_t* pred,
+                   unsigned long long* sse)
+{
+    if (!c || !ref || !cur || !mv || !sse) return SME_ERR_ARG;
+    if (cudaMemsetAsync(sse, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return SME_ERR_CUDA;
+    CompArgs a{ref, cur, mv, pred, sse, c->status};
+    return cuda_status(launch_compensate(c->g, a, c->stream));
+}
+
+double sme_psnr(unsigned long long sse, int width, int height)
+{
+    if (sse == 0) return INFINITY;
+    return 10.0 * log10(255.0 * 255.0 * (double)width * (double)height / (double)sse);
+}
+
+static int run_queries(sme_ctx* c, const uint8_t* ref, const uint8_t* cur, const uint8_t* aref,
+                       const uint8_t* acur, const int32_t* q, int n, uint32_t* tsad, uint32_t* ssad,
+                       float* delta)
+{
+    if (!c || !ref || !cur || !q || n < 0) return SME_ERR_ARG;
+    const Geom& g = c->g;
+    QueryArgs a{};
+    a.ref = ref;
+    a.cur = cur;
+    a.q = q;
+    a.n = n;
+    a.tsad = tsad;
+    a.ssad = ssad;
+    a.delta = delta;
+    a.status = c->status;
+    if (ssad) {
+        if (!aref || !acur || !aligned16(aref) || !aligned16(acur)) return SME_ERR_ARG;
+        const size_t pw = (size_t)g.H * g.Wp;
+        int rc;
+        if ((rc = ensure(c->qpacked, 2 * pw * sizeof(uint32_t))) || (rc = ensure(c->qcls, 2 * (size_t)g.M)))
+            return rc;
+        uint32_t* pk = (uint32_t*)c->qpacked.p;
+        uint8_t* cl = (uint8_t*)c->qcls.p;
+        ClassifyArgs ca{};
+        ca.n_frames = 1;
+        ca.alpha = aref;
+        ca.cls = cl;
+        ca.packed = pk;
+        if (launch_classify(g, ca, c->stream) != cudaSuccess) return SME_ERR_CUDA;
+        ca.alpha = acur;
+        ca.cls = cl + g.M;
+        ca.packed = pk + pw;
+        if (launch_classify(g, ca, c->stream) != cudaSuccess) return SME_ERR_CUDA;
+        a.pref = pk;
+        a.pcur = pk + pw;
+    }
+    return cuda_status(launch_queries(g, a, c->stream));
+}
+
+int sme_eval_costs(sme_ctx* c, const uint8_t* ref, const uint8_t* cur, const uint8_t* aref,
+                   const uint8_t* acur, const int32_t* queries, int n, uint32_t* texture_sad,
+                   uint32_t* shape_sad)
+{
+    return run_queries(c, ref, cur, aref, acur, queries, n, texture_sad, shape_sad, nullptr);
+}
+
+int sme_gradient_step(sme_ctx* c, const uint8_t* ref, const uint8_t* cur, const int32_t* queries, int n,
+                      float* delta)
+{
+    if (!delta) return SME_ERR_ARG;
+    return run_queries(c, ref, cur, nullptr, nullptr, queries, n, nullptr, nullptr, delta);
+}
+
+int sme_profile_begin(sme_ctx* c, int max_calls)
+{
+    if (!c || max_calls < 1 || max_calls > (1 << 20)) return SME_ERR_ARG;
+    profile_free(c);
+    try {
+        c->prof_ev.assign(3 * (size_t)max_calls, nullptr);
+    } catch (...) {
+        return SME_ERR_NOMEM;
+    }
+    for (cudaEvent_t& e : c->prof_ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            profile_free(c);
+            return SME_ERR_CUDA;
+        }
+    c->prof_max = max_calls;
+    c->prof_n = 0;
+    return SME_OK;
+}
+
+int sme_profile_end(sme_ctx* c, int* calls, double* classify_ms, double* me_ms)
+{
+    if (!c) return SME_ERR_ARG;
+    double tc = 0.0, tm = 0.0;
+    const int n = c->prof_n;
+    if (n > 0 && cudaEventSynchronize(c->prof_ev[3 * (n - 1) + 2]) != cudaSuccess) return SME_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+        float a = 0.0f, b = 0.0f;
+        if (cudaEventElapsedTime(&a, c->prof_ev[3 * i], c->prof_ev[3 * i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&b, c->prof_ev[3 * i + 1], c->prof_ev[3 * i + 2]) != cudaSuccess)
+            return SME_ERR_CUDA;
+        tc += a;
+        tm += b;
+    }
+    if (calls) *calls = n;
+    if (classify_ms) *classify_ms = tc;
+    if (me_ms) *me_ms = tm;
+    profile_free(c);
+    return SME_OK;
+}
+
+int sme_debug_set_fault(sme_ctx* c, int skip_ticket, long long timeout_ns)
+{
+    if (!c) return SME_ERR_ARG;
+    c->fault_ticket = skip_ticket < 0 ? -1 : skip_ticket;
+    c->timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
+    return SME_OK;
+}
+
+}  // extern "C"

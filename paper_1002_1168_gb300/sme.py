@@ -1,0 +1,287 @@
+"""Python binding of the C ABI in include/sme.h (argument marshalling only).
+
+Every step of the motion-estimation pass runs in the CUDA library
+``_build/libsme.so``; PyTorch only provides device memory and the stream.
+There is no CPU fallback: if the library or a GPU is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsme.so")
+
+SME_TRANSPARENT, SME_OPAQUE, SME_BOUNDARY = 0, 1, 2
+STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4: "SME_ERR_TIMEOUT",
+          5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE"}
+
+# Every entry point declared in include/sme.h.
+EXPORTS = [
+    "sme_default_params", "sme_strerror", "sme_create", "sme_destroy", "sme_set_stream",
+    "sme_synchronize", "sme_classify", "sme_packed_words", "sme_estimate_sequence",
+    "sme_estimate_sequence_host", "sme_set_reference", "sme_set_current", "sme_estimate",
+    "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field",
+    "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
+    "sme_profile_end", "sme_debug_set_fault",
+]
+
+
+class SmeError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        name = STATUS.get(status, str(status))
+        msg = _lib().sme_strerror(status).decode() if _LIB is not None else name
+        super().__init__(f"{what}: {name} ({msg})")
+
+
+class Params(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("search_range", C.c_int),
+                ("subpel", C.c_int), ("theta", C.c_float), ("epsilon", C.c_float),
+                ("max_iters", C.c_int), ("ref_distance", C.c_int)]
+
+
+class Outputs(C.Structure):
+    _fields_ = [("mv", C.c_void_p), ("cost", C.c_void_p), ("disp", C.c_void_p),
+                ("iters", C.c_void_p), ("npos", C.c_void_p), ("mb_class", C.c_void_p),
+                ("sse_mb", C.c_void_p), ("sse", C.c_void_p), ("pred", C.c_void_p)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def _lib():
+    """Load libsme.so (built by build.py / __graft_entry__.build())."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run build())")
+        lib = C.CDLL(LIB_PATH)
+        vp, i, ip = C.c_void_p, C.c_int, C.POINTER(C.c_void_p)
+        sig = {
+            "sme_default_params": (None, [C.POINTER(Params), i, i]),
+            "sme_strerror": (C.c_char_p, [i]),
+            "sme_create": (i, [ip, C.POINTER(Params), vp]),
+            "sme_destroy": (i, [vp]),
+            "sme_set_stream": (i, [vp, vp]),
+            "sme_synchronize": (i, [vp]),
+            "sme_classify": (i, [vp, vp, i, vp, vp]),
+            "sme_packed_words": (i, [i]),
+            "sme_estimate_sequence": (i, [vp, vp, vp, i, vp, vp, C.POINTER(Outputs)]),
+            "sme_estimate_sequence_host": (i, [vp, vp, vp, i, vp, vp, C.POINTER(Outputs)]),
+            "sme_set_reference": (i, [vp, vp, vp]),
+            "sme_set_current": (i, [vp, vp, vp]),
+            "sme_estimate": (i, [vp, C.POINTER(Outputs)]),
+            "sme_advance": (i, [vp]),
+            "sme_score": (i, [vp, C.POINTER(C.c_double)]),
+            "sme_get_temporal_field": (i, [vp, vp]),
+            "sme_set_temporal_field": (i, [vp, vp]),
+            "sme_compensate": (i, [vp, vp, vp, vp, vp, vp]),
+            "sme_psnr": (C.c_double, [C.c_ulonglong, i, i]),
+            "sme_eval_costs": (i, [vp, vp, vp, vp, vp, vp, i, vp, vp]),
+            "sme_gradient_step": (i, [vp, vp, vp, vp, i, vp]),
+            "sme_profile_begin": (i, [vp, i]),
+            "sme_profile_end": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+            "sme_debug_set_fault": (i, [vp, i, C.c_longlong]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+        return lib
+
+
+def psnr(sse, width, height) -> float:
+    """PSNR (dB) of an 8-bit frame from its SSE (host computation in the library)."""
+    return _lib().sme_psnr(int(sse), int(width), int(height))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise SmeError(rc, what)
+
+
+OUTPUT_FIELDS = ("mv", "cost", "disp", "iters", "npos", "mb_class", "sse_mb", "sse", "pred")
+
+
+class Estimator:
+    """One context of the library bound to the current CUDA device."""
+
+    def __init__(self, width, height, search_range=16, subpel=1, theta=2.0, epsilon=1.0,
+                 max_iters=8, ref_distance=1):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required (no CPU fallback)")
+        self.torch = torch
+        lib = _lib()
+        self.params = Params(width, height, search_range, subpel, theta, epsilon, max_iters, ref_distance)
+        self.width, self.height = width, height
+        self.M = (width // 16) * (height // 16)
+        self.ref_distance = ref_distance
+        h = C.c_void_p()
+        _check(lib.sme_create(C.byref(h), C.byref(self.params), self._stream()), "sme_create")
+        self._h = h
+
+    # ------------------------------------------------------------ plumbing
+    def _stream(self):
+        return C.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def _bind(self):
+        _check(_lib().sme_set_stream(self._h, self._stream()), "sme_set_stream")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().sme_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        _check(_lib().sme_synchronize(self._bind()), "sme_synchronize")
+
+    def _alloc_outputs(self, P, want, device):
+        t = self.torch
+        M, H, W = self.M, self.height, self.width
+        shapes = {"mv": ((P, M, 2), t.int16), "cost": ((P, M), t.int32), "disp": ((P, M, 2), t.float32),
+                  "iters": ((P, M), t.uint8), "npos": ((P, M), t.uint8), "mb_class": ((P, M), t.uint8),
+                  "sse_mb": ((P, M), t.int32), "sse": ((P,), t.int64), "pred": ((P, H, W), t.uint8)}
+        out = {}
+        for k in OUTPUT_FIELDS:
+            if k == "mv" or k in want:
+                shp, dt = shapes[k]
+                out[k] = t.empty(shp, dtype=dt, device=device)
+        return out
+
+    @staticmethod
+    def _outputs_struct(out):
+        return Outputs(*[_ptr(out.get(k)) for k in OUTPUT_FIELDS])
+
+    # ---------------------------------------------------------- interface
+    def estimate_sequence(self, luma, alpha, temporal_in=None, seed=None,
+                          want=("cost", "disp", "iters", "npos", "mb_class", "sse"), out=None,
+                          sync=True):
+        """Fig. 1 over a sequence: luma/alpha uint8 CUDA tensors [F, H, W]."""
+        F = luma.shape[0]
+        P = F - self.ref_distance
+        assert luma.is_cuda and alpha.is_cuda and luma.is_contiguous() and alpha.is_contiguous()
+        if out is None:
+            out = self._alloc_outputs(P, want, luma.device)
+        st = self._outputs_struct(out)
+        rc = _lib().sme_estimate_sequence(self._bind(), _ptr(luma), _ptr(alpha), F, _ptr(temporal_in),
+                                          _ptr(seed), C.byref(st))
+        _check(rc, "sme_estimate_sequence")
+        if sync:
+            self.synchronize()
+        return out
+
+    def estimate_sequence_host(self, luma, alpha, temporal_in=None, seed=None,
+                               want=("cost", "disp", "iters", "npos", "mb_class", "sse"), out=None):
+        """Same as estimate_sequence with host tensors (pinned for fast copies)."""
+        F = luma.shape[0]
+        P = F - self.ref_distance
+        if out is None:
+            out = self._alloc_outputs(P, want, "cpu")
+        st = self._outputs_struct(out)
+        rc = _lib().sme_estimate_sequence_host(self._bind(), _ptr(luma), _ptr(alpha), F,
+                                               _ptr(temporal_in), _ptr(seed), C.byref(st))
+        _check(rc, "sme_estimate_sequence_host")
+        return out
+
+    def classify(self, alpha, want_packed=True):
+        t = self.torch
+        F = alpha.shape[0]
+        cls = t.empty((F, self.M), dtype=t.uint8, device=alpha.device)
+        wp = _lib().sme_packed_words(self.width)
+        packed = t.empty((F, self.height, wp), dtype=t.int32, device=alpha.device) if want_packed else None
+        _check(_lib().sme_classify(self._bind(), _ptr(alpha), F, _ptr(cls), _ptr(packed)), "sme_classify")
+        self.synchronize()
+        return cls, packed
+
+    def compensate(self, ref, cur, mv, want_pred=True):
+        t = self.torch
+        sse = t.zeros(1, dtype=t.int64, device=ref.device)
+        pred = t.empty_like(ref) if want_pred else None
+        _check(_lib().sme_compensate(self._bind(), _ptr(ref), _ptr(cur), _ptr(mv), _ptr(pred), _ptr(sse)),
+               "sme_compensate")
+        self.synchronize()
+        return int(sse.item()), pred
+
+    def eval_costs(self, ref, cur, aref, acur, queries):
+        t = self.torch
+        q = t.as_tensor(np.asarray(queries, np.int32).reshape(-1, 3)).to(ref.device)
+        n = q.shape[0]
+        ts = t.empty(n, dtype=t.int32, device=ref.device)
+        ss = t.empty(n, dtype=t.int32, device=ref.device) if aref is not None else None
+        _check(_lib().sme_eval_costs(self._bind(), _ptr(ref), _ptr(cur), _ptr(aref), _ptr(acur), _ptr(q), n,
+                                     _ptr(ts), _ptr(ss)), "sme_eval_costs")
+        self.synchronize()
+        return ts, ss
+
+    def gradient_step(self, ref, cur, queries):
+        t = self.torch
+        q = t.as_tensor(np.asarray(queries, np.int32).reshape(-1, 3)).to(ref.device)
+        n = q.shape[0]
+        d = t.empty((n, 2), dtype=t.float32, device=ref.device)
+        _check(_lib().sme_gradient_step(self._bind(), _ptr(ref), _ptr(cur), _ptr(q), n, _ptr(d)),
+               "sme_gradient_step")
+        self.synchronize()
+        return d
+
+    # ------------------------------------------------ stateful pair API
+    def set_reference(self, luma, alpha):
+        _check(_lib().sme_set_reference(self._bind(), _ptr(luma), _ptr(alpha)), "sme_set_reference")
+
+    def set_current(self, luma, alpha):
+        _check(_lib().sme_set_current(self._bind(), _ptr(luma), _ptr(alpha)), "sme_set_current")
+
+    def estimate(self, want=("cost", "sse")):
+        out = self._alloc_outputs(1, want, "cuda")
+        st = self._outputs_struct(out)
+        _check(_lib().sme_estimate(self._bind(), C.byref(st)), "sme_estimate")
+        return out
+
+    def advance(self):
+        _check(_lib().sme_advance(self._bind()), "sme_advance")
+
+    def score(self):
+        v = C.c_double()
+        _check(_lib().sme_score(self._bind(), C.byref(v)), "sme_score")
+        return v.value
+
+    def get_temporal_field(self):
+        t = self.torch
+        f = t.empty((self.M, 2), dtype=t.int16, device="cuda")
+        _check(_lib().sme_get_temporal_field(self._bind(), _ptr(f)), "sme_get_temporal_field")
+        return f
+
+    def set_temporal_field(self, field):
+        _check(_lib().sme_set_temporal_field(self._bind(), _ptr(field)), "sme_set_temporal_field")
+
+    def profile_begin(self, max_calls):
+        _check(_lib().sme_profile_begin(self._h, int(max_calls)), "sme_profile_begin")
+
+    def profile_end(self):
+        """Returns (calls, classify_ms_total, me_ms_total) since profile_begin."""
+        n, a, b = C.c_int(), C.c_double(), C.c_double()
+        _check(_lib().sme_profile_end(self._h, C.byref(n), C.byref(a), C.byref(b)), "sme_profile_end")
+        return n.value, a.value, b.value
+
+    def debug_set_fault(self, skip_ticket=-1, timeout_ns=0):
+        _check(_lib().sme_debug_set_fault(self._h, int(skip_ticket), int(timeout_ns)), "sme_debug_set_fault")

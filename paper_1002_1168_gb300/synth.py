@@ -152,7 +152,7 @@ def make_sequence(W, H, F, seed, n_objects=1, vmax=8.0, bg_step=(1.0, 0.5), nois
     for i in range(n_objects):
         a = obj_frac * min(W, H) * rng.uniform(0.8, 1.2) / np.sqrt(n_objects)
         b = a * rng.uniform(0.6, 0.9)
-        ext = (a * 1.5, a * 1.5)
+        ext = (min(a * 1.5, 0.45 * W), min(a * 1.5, 0.45 * H))
         start = (rng.uniform(ext[0], W - ext[0]), rng.uniform(ext[1], H - ext[1]))
         centers = _bounce_path(rng, start, F, vmax, ext, W, H, change_every, integer_motion)
         rot_rate = np.deg2rad(rng.uniform(-max_rot_deg, max_rot_deg))

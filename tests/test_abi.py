@@ -1,0 +1,71 @@
+"""The C-ABI library loads and exports every entry point of include/sme.h.
+
+CPU only: no call here touches a GPU (host-only helpers and argument checks
+that return before any CUDA call)."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+from paper_1002_1168_gb300 import build as cuda_build
+from paper_1002_1168_gb300 import sme
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cuda_build.build()
+    return sme._lib()
+
+
+def header_entry_points():
+    text = open(os.path.join(ROOT, "include", "sme.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sme_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_entry_points()
+    assert len(names) >= 20
+    assert sorted(sme.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_exports_are_plain_c_symbols():
+    out = os.popen(f"nm -D --defined-only {sme.LIB_PATH}").read()
+    for n in header_entry_points():
+        assert re.search(rf"\bT {n}$", out, re.M), n
+
+
+def test_host_only_helpers(lib):
+    assert lib.sme_psnr(0, 64, 64) == math.inf
+    assert lib.sme_psnr(64 * 64, 64, 64) == pytest.approx(20 * math.log10(255.0), abs=1e-12)
+    assert lib.sme_strerror(4).decode().startswith("a bounded device wait")
+    assert lib.sme_packed_words(176) == 7 and lib.sme_packed_words(352) == 12
+    p = sme.Params()
+    lib.sme_default_params(C.byref(p), 352, 288)
+    assert (p.search_range, p.subpel, p.theta, p.epsilon, p.max_iters, p.ref_distance) == (16, 1, 2.0, 1.0, 8, 1)
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("width", 100, 2), ("height", 0, 2), ("width", 8208, 2), ("search_range", 0, 1),
+    ("search_range", 65, 1), ("subpel", 4, 1), ("theta", 0.0, 1), ("epsilon", 5.0, 1),
+    ("max_iters", 17, 1), ("ref_distance", 0, 1),
+])
+def test_create_rejects_bad_params_before_touching_cuda(lib, field, value, code):
+    p = sme.Params()
+    lib.sme_default_params(C.byref(p), 176, 144)
+    setattr(p, field, value)
+    h = C.c_void_p()
+    assert lib.sme_create(C.byref(h), C.byref(p), None) == code
+    assert not h.value
+
+
+def test_null_context_is_an_argument_error(lib):
+    assert lib.sme_destroy(None) == 1
+    assert lib.sme_synchronize(None) == 1
+    assert lib.sme_estimate(None, None) == 1
+    assert lib.sme_debug_set_fault(None, 0, 0) == 1

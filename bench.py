@@ -113,14 +113,14 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def algorithmic_bytes(cls, P, M):
-    """Minimum DRAM bytes of one ME launch: each pair's reference and current
-    luma once (every MB's prediction error needs both), the MB class map, the
-    packed alpha rows the boundary MBs compare (two 16-row x 8-byte strips per
-    boundary MB), and the requested per-MB outputs (mv 4, cost 4, disp 8,
-    iters 1, npos 1, class 1 bytes) plus 8 bytes of SSE per pair."""
-    n_bound = int((cls == 2).sum())
-    return P * (2 * W * H) + P * M + n_bound * 2 * 16 * 8 + P * M * 19 + P * 8
+def algorithmic_bytes(P, M, F):
+    """Minimum DRAM bytes of one ME launch: every luma frame once (each frame
+    is the current frame of one pair and the reference of the next), the packed
+    alpha rows of every frame once, the class of every estimated MB, the
+    requested per-MB outputs (mv 4, cost 4, disp 8, iters 1, npos 1, class 1
+    bytes) and 8 bytes of SSE per pair."""
+    wp = (W + 31) // 32 + 1
+    return F * W * H + F * H * wp * 4 + P * M + P * M * 19 + P * 8
 
 
 def run_reference(args):
@@ -254,7 +254,7 @@ def run_ours(args):
     cls = res["mb_class"]
     hbm, peak_kind = peaks()
     me_avg_s = me_ms / max(calls, 1) / 1e3
-    alg = algorithmic_bytes(cls, P, M)
+    alg = algorithmic_bytes(P, M, FRAMES)
     achieved = alg / me_avg_s / 1e9
     cb, orc = cpu_baseline(seq, budget_s=args.cpu_seconds)
     match = float((res["mv"] == orc["mv"]).all(axis=-1).mean())

@@ -54,7 +54,8 @@ enum {
     SME_ERR_TIMEOUT = 4, /* a bounded device wait gave up (results are incomplete) */
     SME_ERR_STATE = 5,   /* call made in the wrong state (e.g. estimate before set_current) */
     SME_ERR_NOMEM = 6,   /* device or host allocation failed */
-    SME_ERR_RANGE = 7    /* a caller-supplied vector lies outside V */
+    SME_ERR_RANGE = 7,   /* a caller-supplied vector lies outside V */
+    SME_ERR_SCRATCH = 8  /* problem larger than sme_estimate_sequence_noalloc's fixed scratch */
 };
 
 enum { SME_TRANSPARENT = 0, SME_OPAQUE = 1, SME_BOUNDARY = 2 };
@@ -193,6 +194,34 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  * stops recording.  Any output pointer may be NULL. */
 int sme_profile_begin(sme_ctx* ctx, int max_calls);
 int sme_profile_end(sme_ctx* ctx, int* calls, double* classify_ms, double* me_ms);
+
+/* The paper has no counterpart of this call: it exists for callers that
+ * cannot allocate device memory (code running inside another framework's
+ * memory pool or a custom allocator that must own every device allocation,
+ * or real-time / embedded callers that forbid allocation after start-up).
+ * It computes exactly what sme_estimate_sequence computes, for the params
+ * given here, without a context: its scratch (packed alpha, MB classes, ready
+ * words, schedule, status) lives in one fixed 4 MiB array in device memory
+ * that every GPU loading this library holds until exit, and the call makes no
+ * cudaMalloc, cudaFree or other allocating call.
+ *   p            parameters as for sme_create
+ *   luma, alpha  [n_frames][H][W] device, 16-byte aligned (caller-owned)
+ *   temporal_in, seed, out   as for sme_estimate_sequence (device, caller-owned)
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
+ * Scratch needed: F*H*Wp*4 + F*M + 8*P*M + 4*(steps+1) bytes, each part
+ * rounded up to 256, where Wp = ceil(W/32)+1, steps = (W/16-1) + 2*(H/16-1)
+ * + P and P = F - ref_distance; a problem that needs more than 4 MiB (for
+ * example more than 241 CIF frames, or more than 12 frames of 1920x1088) returns
+ * SME_ERR_SCRATCH before any GPU work.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and should come before any stream capture.  The call
+ * synchronises the stream and returns the device-side status of its own
+ * work.  All calls share the array: calls that overlap on the GPU (e.g. on
+ * two streams, or from two threads) race and must be serialised by the
+ * caller. */
+int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t* luma, const uint8_t* alpha,
+                                  int n_frames, const sme_mv* temporal_in, const float* seed,
+                                  const sme_outputs* out, void* cuda_stream);
 
 /* Failure injection for tests.  With skip_ticket >= 0 the estimate's MB of
  * that schedule position never publishes its result, so the MBs that depend

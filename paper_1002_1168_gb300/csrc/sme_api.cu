@@ -253,6 +253,7 @@ const char* sme_strerror(int s)
     case SME_ERR_STATE: return "call made in the wrong state";
     case SME_ERR_NOMEM: return "allocation failed";
     case SME_ERR_RANGE: return "a supplied motion vector lies outside the valid set";
+    case SME_ERR_SCRATCH: return "problem exceeds the fixed 4 MiB scratch of sme_estimate_sequence_noalloc";
     default: return "unknown status";
     }
 }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsme.so")
 
 SME_TRANSPARENT, SME_OPAQUE, SME_BOUNDARY = 0, 1, 2
 STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4: "SME_ERR_TIMEOUT",
-          5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE"}
+          5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE", 8: "SME_ERR_SCRATCH"}
 
 # Every entry point declared in include/sme.h.
 EXPORTS = [
@@ -26,7 +26,7 @@ EXPORTS = [
     "sme_estimate_sequence_host", "sme_set_reference", "sme_set_current", "sme_estimate",
     "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field",
     "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
-    "sme_profile_end", "sme_debug_set_fault",
+    "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_debug_set_fault",
 ]
 
 
@@ -88,6 +88,7 @@ def _lib():
             "sme_gradient_step": (i, [vp, vp, vp, vp, i, vp]),
             "sme_profile_begin": (i, [vp, i]),
             "sme_profile_end": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+            "sme_estimate_sequence_noalloc": (i, [C.POINTER(Params), vp, vp, i, vp, vp, C.POINTER(Outputs), vp]),
             "sme_debug_set_fault": (i, [vp, i, C.c_longlong]),
         }
         for name, (res, args) in sig.items():

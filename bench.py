@@ -185,6 +185,7 @@ def run_ours(args):
     seq = workload(rank)
     P, M = FRAMES - 1, (W // 16) * (H // 16)
     est = sme.Estimator(W, H, search_range=S, subpel=SUBPEL)
+    est.set_schedule(args.schedule)
     luma = torch.from_numpy(seq.luma).cuda()
     alpha = torch.from_numpy(seq.alpha[0]).cuda()
     out = est._alloc_outputs(P, OUT_FIELDS, luma.device)
@@ -271,7 +272,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs": P, "mbs_per_step": mbs_step, "seed": 1002,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "schedule": args.schedule},
         "clocks": clk,
         "e2e": {"value": ws * mbs_step * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -302,6 +303,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--schedule", default="auto", choices=["auto", "pair", "mb"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -117,7 +117,8 @@ int sme_synchronize(sme_ctx* ctx);
  *   mb_class [n_frames][M] device out: 0 transparent (no pixel inside),
  *            1 opaque (all 256 inside), 2 boundary
  *   packed   optional device out [n_frames][H][sme_packed_words(W)] uint32:
- *            bit b of word k of a row = (alpha[32k+b] != 0); trailing words 0. */
+ *            bit b of word k of a row = (alpha[32k+b] != 0); trailing words 0
+ *            (at least one, rows padded to a multiple of 4 words). */
 int sme_classify(sme_ctx* ctx, const uint8_t* alpha, int n_frames, uint8_t* mb_class,
                  uint32_t* packed);
 
@@ -186,6 +187,21 @@ int sme_eval_costs(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur, const u
 int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
                       const int32_t* queries, int n, float* delta);
 
+/* Execution options (no counterpart in the paper: they choose how the
+ * raster dependency of Fig. 1 is mapped onto the GPU, never what is computed;
+ * every option gives bit-identical results).
+ *   SME_OPT_SCHEDULE: SME_SCHED_PAIR -- one CTA per frame pair, one warp per
+ *     MB row, the row above handed over in shared memory and the reference
+ *     windows fetched by TMA; SME_SCHED_MB -- one warp per MB, tickets in
+ *     wavefront order, every dependency through global memory;
+ *     SME_SCHED_AUTO (default) -- chosen per workload.
+ *   SME_OPT_PAIR_WARPS: warps (MB rows in flight) per CTA of the pair
+ *     schedule, 1..16; 0 (default) = automatic.
+ * Returns SME_ERR_ARG for an unknown option or value. */
+enum { SME_OPT_SCHEDULE = 1, SME_OPT_PAIR_WARPS = 2 };
+enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2 };
+int sme_set_option(sme_ctx* ctx, int option, int value);
+
 /* Stage timing (tracing).  sme_profile_begin makes every following
  * sme_estimate_sequence* call record CUDA events around its two launches on
  * the context's stream (classification, then the persistent ME launch), for
@@ -208,10 +224,10 @@ int sme_profile_end(sme_ctx* ctx, int* calls, double* classify_ms, double* me_ms
  *   luma, alpha  [n_frames][H][W] device, 16-byte aligned (caller-owned)
  *   temporal_in, seed, out   as for sme_estimate_sequence (device, caller-owned)
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
- * Scratch needed: F*H*Wp*4 + F*M + 8*P*M + 4*(steps+1) bytes, each part
- * rounded up to 256, where Wp = ceil(W/32)+1, steps = (W/16-1) + 2*(H/16-1)
+ * Scratch needed: F*H*Wp*4 + F*M + 12*P*M + 4*(steps+1) + 512 bytes, each part
+ * rounded up to 256, where Wp = sme_packed_words(W), steps = (W/16-1) + 2*(H/16-1)
  * + P and P = F - ref_distance; a problem that needs more than 4 MiB (for
- * example more than 241 CIF frames, or more than 12 frames of 1920x1088) returns
+ * example more than 221 CIF frames, or more than 11 frames of 1920x1088) returns
  * SME_ERR_SCRATCH before any GPU work.
  * The first call on each device looks up the array's device address (with
  * that device current) and should come before any stream capture.  The call
@@ -223,9 +239,11 @@ int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t* luma, cons
                                   int n_frames, const sme_mv* temporal_in, const float* seed,
                                   const sme_outputs* out, void* cuda_stream);
 
-/* Failure injection for tests.  With skip_ticket >= 0 the estimate's MB of
- * that schedule position never publishes its result, so the MBs that depend
- * on it wait until `timeout_ns` and the launch ends with SME_ERR_TIMEOUT.
+/* Failure injection for tests.  With skip_ticket >= 0 the MB with index
+ * k*M + m (pair k, MB m) of the next estimates never publishes its result to
+ * global memory, so the MBs that wait on it there (all its dependants in the
+ * per-MB schedule; the next pair's T candidate in the pair schedule) wait
+ * until `timeout_ns` and the launch ends with SME_ERR_TIMEOUT.
  * skip_ticket = -1 restores normal operation; timeout_ns <= 0 restores the
  * default wait limit (1 s). */
 int sme_debug_set_fault(sme_ctx* ctx, int skip_ticket, long long timeout_ns);

@@ -1,7 +1,8 @@
-// Internal declarations shared by the C-ABI layer (sme_api.cu) and the
-// kernels (sme_kernels.cu).  Not part of the public interface.
+// Internal declarations shared by the C-ABI layer (sme_api.cu, sme_noalloc.cu)
+// and the kernels (sme_kernels.cu).  Not part of the public interface.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the layout only; no driver library is linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,8 +17,14 @@ constexpr int kMaxDim = 8192;
 // pixel-recursive iteration, one proposal and eight neighbours.
 constexpr int kMaxLog = 5 + 9 * kMaxIters;
 constexpr long long kDefaultTimeoutNs = 1000000000LL;
+constexpr int kMeWarps = 8;     // warps (one MB each) per CTA of the per-MB ME kernel
+constexpr int kPairWarpsMax = 16;  // warps (MB rows) per CTA of the per-pair ME kernel
 
-// Device status words (ctx scratch).  `err` is sticky until read by
+// ME schedules: one warp per MB with tickets in wavefront order, or one CTA
+// per frame pair with one warp per MB row.
+enum Schedule { kSchedAuto = 0, kSchedMB = 1, kSchedPair = 2 };
+
+// Device status words (scratch).  `err` is sticky until read by
 // sme_synchronize; `abort` and `ticket` are reset by the classify kernel at
 // the start of every estimate.
 struct DevStatus {
@@ -27,26 +34,22 @@ struct DevStatus {
     unsigned pad;
 };
 
-// Geometry + method parameters as the kernels see them.
-struct Geom {
-    int W, H, M, MBW, MBH, Wp;  // Wp = packed alpha words per row
+// Method parameters shared by every sequence of a launch.
+struct Method {
     int S, h, K;
     float theta, eps;
 };
 
-struct ClassifyArgs {
-    const uint8_t* alpha;
-    int n_frames;
-    uint8_t* cls;        // [F][M]
-    uint32_t* packed;    // [F][H][Wp]
-    DevStatus* status;   // reset here when non-null
-    unsigned long long* sse;  // [P] zeroed here when non-null
-    int n_sse;
+// Per-frame geometry.
+struct Geom {
+    int W, H, M, MBW, MBH, Wp;  // Wp = packed alpha words per row
 };
 
-struct MeArgs {
-    const uint8_t* luma;
-    const uint32_t* packed;
+// One sequence (one VOP) of an ME launch.  Global MB id of MB `mb` of pair k
+// = gid_base + k*M + mb; ready words are indexed by global MB id.
+struct SeqDesc {
+    const uint8_t* luma;      // [F][H][W]
+    const uint32_t* packed;   // [F][H][Wp]
     const uint8_t* cls;       // [F][M]
     const sme_mv* temporal_in;
     const float* seed;        // [P][M][2]
@@ -57,13 +60,39 @@ struct MeArgs {
     uint8_t* npos;
     uint8_t* out_cls;
     uint32_t* sse_mb;
-    unsigned long long* sse;
+    unsigned long long* sse;  // [P]
     uint8_t* pred;
-    const int* sched;         // ticket -> k*M + mb, ordered by wavefront step
-    unsigned* ready;          // [P][M] epoch stamps
+    int W, H, MBW, MBH, M, Wp, P, rd;
+    int gid_base;
+    int pad;
+};
+
+struct ClassifyArgs {
+    const uint8_t* alpha;
+    int n_frames;
+    uint8_t* cls;        // [F][M]
+    uint32_t* packed;    // [F][H][Wp]
+    DevStatus* status;   // reset here when non-null
+    unsigned long long* sse;  // [P] zeroed here when non-null
+    int n_sse;
+    SeqDesc* desc_out;   // when non-null, block (0,0) stores `desc` there
+    SeqDesc desc;
+};
+
+struct MeArgs {
+    const SeqDesc* seqs;      // [nseq] in device memory
+    const int* sched;         // per-MB schedule: ticket -> global MB id, by wavefront step
+    const int* sched_seq;     // per-MB schedule: ticket -> sequence index (NULL: sequence 0)
+    const int* unit_seq;      // per-pair schedule: ticket -> sequence (NULL: sequence 0)
+    const int* unit_pair;     // per-pair schedule: ticket -> pair (NULL: pair = ticket)
+    const CUtensorMap* tmaps; // per-pair schedule: luma tensor map per sequence (NULL: kernel parameter)
+    int total_units;
+    int mbw_max;
+    unsigned long long* ready;  // [total] (epoch << 32) | packed vector
     DevStatus* status;
+    Method m;
     unsigned epoch;
-    int P, rd, total;
+    int total;
     int fault_ticket;
     long long timeout_ns;
 };
@@ -92,11 +121,20 @@ struct QueryArgs {
 
 // Launchers (sme_kernels.cu).  Return cudaSuccess or the launch error.
 cudaError_t launch_classify(const Geom& g, const ClassifyArgs& a, cudaStream_t s);
-cudaError_t launch_me(const Geom& g, const MeArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_compensate(const Geom& g, const CompArgs& a, cudaStream_t s);
-cudaError_t launch_queries(const Geom& g, const QueryArgs& a, cudaStream_t s);
-// Resident CTAs per SM of the persistent ME kernel for this geometry.
-cudaError_t me_occupancy(const Geom& g, int* blocks_per_sm);
-size_t me_smem_bytes(const Geom& g);
+cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s);
+// `maps` points to 4 CUtensorMaps (128-byte aligned): luma window box, current
+// block box, packed-alpha reference strip, packed-alpha current BAB.
+cudaError_t launch_me_pair(const Method& m, const MeArgs& a, const void* maps, int nwarps, int grid, cudaStream_t s);
+cudaError_t me_pair_occupancy(int S, int nwarps, int mbw_max, int* blocks_per_sm);
+size_t me_pair_smem_bytes(int S, int nwarps, int mbw_max);
+// Boxes (elements wide, rows high) of the four TMA copies of the per-pair
+// kernel: luma window, current block, packed-alpha reference strip (u32),
+// packed-alpha current BAB (u32).
+void pair_boxes(int S, unsigned (&box)[4][2]);
+cudaError_t launch_compensate(const Geom& g, const Method& m, const CompArgs& a, cudaStream_t s);
+cudaError_t launch_queries(const Geom& g, const Method& m, const QueryArgs& a, cudaStream_t s);
+// Resident CTAs per SM of the persistent ME kernel for search range S.
+cudaError_t me_occupancy(int S, int* blocks_per_sm);
+size_t me_smem_bytes(int S);
 
 }  // namespace sme

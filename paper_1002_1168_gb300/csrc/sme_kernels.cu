@@ -3,19 +3,21 @@
 //   classify_pack_kernel  Fig. 1 "Block_Type": per-MB class from the binary
 //                         alpha block + bit-packed alpha rows (one pass).
 //   me_kernel             Fig. 1 / Sec. 3.1 / Sec. 3.2 for every MB of every
-//                         frame pair of a sequence, one persistent launch:
-//                         tickets in wavefront order, bounded waits on the
-//                         A/B/C/T results, block recursive search (shape cost
-//                         on boundary MBs, texture SAD on opaque MBs), pixel
-//                         recursive gradient search (Eqs. 3-5, Fig. 4) and the
-//                         fused motion compensation + SSE of Sec. 4.
+//                         frame pair of one or more sequences, one persistent
+//                         launch: one warp per MB, tickets in wavefront order,
+//                         bounded waits on the A/B/C/T results, block
+//                         recursive search (shape cost on boundary MBs, texture
+//                         SAD on opaque MBs), pixel recursive gradient search
+//                         (Eqs. 3-5, Fig. 4) and the fused motion compensation
+//                         + SSE of Sec. 4.
 //   compensate_kernel     Sec. 4 motion compensation of a given field.
 //   query_kernel          Single cost / gradient evaluations through the same
 //                         device functions as me_kernel (unit checks).
 //
-// One CTA of 256 threads handles one MB: thread t owns pixel (t & 15, t >> 4)
-// of the 16x16 block, so block-wide sums over the 256 pixels follow the
-// row-major pixel order.
+// Lane l of the warp that owns an MB holds the 8 pixels (8*(l&1) .. +7) of
+// row l>>1 of the 16x16 block, i.e. pixels 8l .. 8l+7 in row-major order, as
+// two packed 32-bit words.  Sums over the 256 pixels therefore follow the
+// row-major pixel order: a lane's 8 terms, then the lanes.
 #include <stdint.h>
 
 #include "sme_internal.h"
@@ -23,14 +25,16 @@
 namespace sme {
 namespace {
 
-constexpr int kThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------ sync --
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+// The ready word carries the published vector itself, so a consumer needs no
+// other data from the producer: relaxed (coherent, unfenced) 64-bit accesses
+// at GPU scope are enough -- an aligned 64-bit access is single-copy atomic.
+__device__ __forceinline__ unsigned long long ld_ready(const unsigned long long* p)
 {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p)
@@ -39,9 +43,9 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p)
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+__device__ __forceinline__ void st_ready(unsigned long long* p, unsigned long long v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ unsigned long long globaltimer()
 {
@@ -50,15 +54,25 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-// Spin until *flag == epoch.  Bounded by `timeout_ns` of %globaltimer and by
-// an iteration cap; gives up early when another CTA raised the abort word.
-__device__ bool wait_flag(const unsigned* flag, unsigned epoch, const DevStatus* st,
-                          long long timeout_ns)
+// Wait until the ready word carries `epoch` in its high half; its low half
+// (the published vector) is returned in `val`.  Bounded by `timeout_ns` of
+// %globaltimer and by an iteration cap; gives up early when the launch's
+// abort word is raised.
+__device__ bool wait_ready(const unsigned long long* w, unsigned epoch, const DevStatus* st,
+                           long long timeout_ns, unsigned& val)
 {
-    if (ld_acquire(flag) == epoch) return true;
+    unsigned long long v = ld_ready(w);
+    if ((unsigned)(v >> 32) == epoch) {
+        val = (unsigned)v;
+        return true;
+    }
     const unsigned long long t0 = globaltimer();
     for (unsigned it = 1; it < (1u << 24); ++it) {
-        if (ld_acquire(flag) == epoch) return true;
+        v = ld_ready(w);
+        if ((unsigned)(v >> 32) == epoch) {
+            val = (unsigned)v;
+            return true;
+        }
         if ((it & 15u) == 0) {
             if (ld_relaxed(&st->abort)) return false;
             if ((long long)(globaltimer() - t0) > timeout_ns) return false;
@@ -73,59 +87,15 @@ __device__ __forceinline__ void raise_error(DevStatus* st, int code, bool abort_
     if (abort_launch) atomicExch(&st->abort, 1u);
 }
 
-// ------------------------------------------------------------ reductions --
-// Integer block sums of N per-thread values (every thread gets the totals).
-// `red` is one of two alternating [16][8] buffers: one barrier per call.
-template <int N>
-__device__ __forceinline__ void block_sum(unsigned (&v)[N], unsigned (*red)[8], int lane, int warp)
-{
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-        unsigned s = __reduce_add_sync(kFull, v[c]);
-        if (lane == 0) red[c][warp] = s;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-        unsigned s = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) s += red[c][w];
-        v[c] = s;
-    }
-}
-
-// FP32 sum of one term per thread over the 256 pixels as a contiguous
-// pairwise tree in row-major pixel order: within a warp, offsets 1..16 pair
-// neighbouring partial sums; across the eight warps ((w0+w1)+(w2+w3)) +
-// ((w4+w5)+(w6+w7)).  Round-to-nearest adds only (no contraction).
-__device__ __forceinline__ void tree_sum2(float& a, float& b, float (*red)[8], int lane, int warp)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        float pa = __shfl_down_sync(kFull, a, o);
-        float pb = __shfl_down_sync(kFull, b, o);
-        a = __fadd_rn(a, pa);
-        b = __fadd_rn(b, pb);
-    }
-    if (lane == 0) {
-        red[0][warp] = a;
-        red[1][warp] = b;
-    }
-    __syncthreads();
-    float r[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const float* p = red[c];
-        r[c] = __fadd_rn(__fadd_rn(__fadd_rn(p[0], p[1]), __fadd_rn(p[2], p[3])),
-                         __fadd_rn(__fadd_rn(p[4], p[5]), __fadd_rn(p[6], p[7])));
-    }
-    a = r[0];
-    b = r[1];
-}
-
 // --------------------------------------------------------------- geometry --
-__device__ __forceinline__ int ceil16(int v) { return (v + 15) & ~15; }
-__device__ __forceinline__ int win_pitch(const Geom& g) { return 16 + 2 * ceil16(g.S); }
+__host__ __device__ __forceinline__ int ceil16(int v) { return (v + 15) & ~15; }
+__host__ __device__ __forceinline__ int win_pitch(int S) { return 16 + 2 * ceil16(S); }
+__host__ __device__ __forceinline__ int win_rows(int S) { return 16 + 2 * S; }
+// Per-warp shared memory: the reference window (+32 bytes of slack for the
+// 16- and 24-byte row reads at the right edge) and the evaluated-position log.
+__host__ __device__ __forceinline__ int win_bytes(int S) { return ceil16(win_rows(S) * win_pitch(S) + 32); }
+__host__ __device__ __forceinline__ int warp_smem(int S) { return win_bytes(S) + ceil16(kMaxLog * 4); }
+
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 __device__ __forceinline__ int pack_mv(int dx, int dy)
 {
@@ -139,37 +109,87 @@ struct VRange {
 };
 // Valid set V of the MB at (X0, Y0): displaced block inside the frame and
 // |d| <= S*h per component (MV units).
-__device__ __forceinline__ VRange valid_range(const Geom& g, int X0, int Y0)
+__device__ __forceinline__ VRange valid_range(int W, int H, const Method& m, int X0, int Y0)
 {
     VRange r;
-    r.lox = max(-g.S * g.h, -X0 * g.h);
-    r.hix = min(g.S * g.h, (g.W - 16 - X0) * g.h);
-    r.loy = max(-g.S * g.h, -Y0 * g.h);
-    r.hiy = min(g.S * g.h, (g.H - 16 - Y0) * g.h);
+    r.lox = max(-m.S * m.h, -X0 * m.h);
+    r.hix = min(m.S * m.h, (W - 16 - X0) * m.h);
+    r.loy = max(-m.S * m.h, -Y0 * m.h);
+    r.hiy = min(m.S * m.h, (H - 16 - Y0) * m.h);
     return r;
 }
 
-// Stage the reference rows/columns every vector of V can touch into shared
-// memory with coalesced 16-byte loads.  Window origin returned in wx0/wy0.
-__device__ __forceinline__ void stage_window(uint8_t* win, const uint8_t* ref, const Geom& g,
-                                             int X0, int Y0, int tid, int& wx0, int& wy0)
+// Stage the reference rows/columns every vector of V can touch into this
+// warp's window with coalesced 16-byte loads.  Window origin in wx0/wy0.
+__device__ __forceinline__ void stage_window(uint8_t* win, const uint8_t* ref, int W, int H, int S,
+                                             int X0, int Y0, int lane, int& wx0, int& wy0)
 {
-    const int cs = ceil16(g.S), pitch = win_pitch(g);
-    wy0 = max(0, Y0 - g.S);
-    const int wy1 = min(g.H - 1, Y0 + 15 + g.S);
+    const int cs = ceil16(S), pitch = win_pitch(S);
+    wy0 = max(0, Y0 - S);
+    const int wy1 = min(H - 1, Y0 + 15 + S);
     wx0 = max(0, X0 - cs);
-    const int wx1 = min(g.W, X0 + 16 + cs);
+    const int wx1 = min(W, X0 + 16 + cs);
     const int nch = (wx1 - wx0) >> 4, n = (wy1 - wy0 + 1) * nch;
-    for (int c = tid; c < n; c += kThreads) {
+    for (int c = lane; c < n; c += 32) {
         const int r = c / nch, ch = c - r * nch;
-        const uint4 val = __ldg(reinterpret_cast<const uint4*>(ref + (size_t)(wy0 + r) * g.W + wx0 + 16 * ch));
+        const uint4 val = __ldg(reinterpret_cast<const uint4*>(ref + (size_t)(wy0 + r) * W + wx0 + 16 * ch));
         *reinterpret_cast<uint4*>(win + r * pitch + 16 * ch) = val;
     }
+    __syncwarp();
 }
 
-// Reference sample at this thread's pixel displaced by d, from the window.
-// MPEG-4 bilinear half-sample interpolation, rounding control 0.
-__device__ __forceinline__ int ref_at(const uint8_t* win, int pitch, int lx, int ly, int dx, int dy, int h)
+// ------------------------------------------------- packed 8-pixel samples --
+struct P8 {
+    unsigned lo, hi;  // pixel k in byte k (k = 0..3 in lo, 4..7 in hi)
+};
+
+// 16 bytes of a window row starting at the 8-byte boundary at or before
+// byte `pos`; `off` = pos & 7.
+__device__ __forceinline__ void row16(const uint8_t* win, int pos, unsigned (&w)[4], int& off)
+{
+    off = pos & 7;
+    const uint2 a = *reinterpret_cast<const uint2*>(win + (pos - off));
+    const uint2 b = *reinterpret_cast<const uint2*>(win + (pos - off) + 8);
+    w[0] = a.x;
+    w[1] = a.y;
+    w[2] = b.x;
+    w[3] = b.y;
+}
+
+// Bytes off .. off+7 (off in 0..8) of the 16 bytes in w.
+__device__ __forceinline__ P8 extract8(const unsigned (&w)[4], int off)
+{
+    unsigned a = w[0], b = w[1], c = w[2];
+    if (off >= 4) {
+        a = w[1];
+        b = w[2];
+        c = w[3];
+        off -= 4;
+    }
+    P8 r;
+    r.lo = __funnelshift_rc(a, b, 8 * off);
+    r.hi = __funnelshift_rc(b, c, 8 * off);
+    return r;
+}
+
+// Per-byte (a + b + 1) >> 1 (MPEG-4 rounding control 0, one axis).
+__device__ __forceinline__ unsigned avg2w(unsigned a, unsigned b)
+{
+    return (a | b) - ((a ^ b) >> 1 & 0x7f7f7f7fu);
+}
+// Per-byte (a + b + c + d + 2) >> 2 (diagonal half-sample), in 16-bit lanes.
+__device__ __forceinline__ unsigned avg4w(unsigned a, unsigned b, unsigned c, unsigned d)
+{
+    const unsigned m = 0x00ff00ffu;
+    const unsigned lo = (a & m) + (b & m) + (c & m) + (d & m) + 0x00020002u;
+    const unsigned hi = (a >> 8 & m) + (b >> 8 & m) + (c >> 8 & m) + (d >> 8 & m) + 0x00020002u;
+    return (lo >> 2 & m) | ((hi >> 2 & m) << 8);
+}
+
+// Reference samples of this lane's 8 pixels displaced by d, from the window
+// (window coordinates of the lane's first pixel: lx, ly).  MPEG-4 bilinear
+// half-sample interpolation, rounding control 0.
+__device__ __forceinline__ P8 ref8(const uint8_t* win, int pitch, int lx, int ly, int dx, int dy, int h)
 {
     int ix = dx, iy = dy, fx = 0, fy = 0;
     if (h == 2) {
@@ -178,35 +198,274 @@ __device__ __forceinline__ int ref_at(const uint8_t* win, int pitch, int lx, int
         fx = dx & 1;
         fy = dy & 1;
     }
-    const uint8_t* r = win + (ly + iy) * pitch + lx + ix;
-    const int a = r[0];
+    unsigned w[4];
+    int off;
+    const int pos = (ly + iy) * pitch + lx + ix;
+    row16(win, pos, w, off);
+    const P8 a = extract8(w, off);
+    if (!fx && !fy) return a;
+    P8 r;
     if (fx) {
-        const int b = r[1];
-        if (fy) return (a + b + r[pitch] + r[pitch + 1] + 2) >> 2;
-        return (a + b + 1) >> 1;
+        const P8 b = extract8(w, off + 1);
+        if (!fy) {
+            r.lo = avg2w(a.lo, b.lo);
+            r.hi = avg2w(a.hi, b.hi);
+            return r;
+        }
+        unsigned v[4];
+        int o2;
+        row16(win, pos + pitch, v, o2);
+        const P8 c = extract8(v, o2), d = extract8(v, o2 + 1);
+        r.lo = avg4w(a.lo, b.lo, c.lo, d.lo);
+        r.hi = avg4w(a.hi, b.hi, c.hi, d.hi);
+        return r;
     }
-    if (fy) return (a + r[pitch] + 1) >> 1;
-    return a;
+    unsigned v[4];
+    int o2;
+    row16(win, pos + pitch, v, o2);
+    const P8 c = extract8(v, o2);
+    r.lo = avg2w(a.lo, c.lo);
+    r.hi = avg2w(a.hi, c.hi);
+    return r;
 }
 
-// Eq. 4 / Eq. 5 factors of this pixel: u = 2/g when |g| >= 2*Theta, g the
-// central difference of the current frame (twice the derivative); 0 on the
-// frame's outer rows/columns.
-__device__ __forceinline__ void grad_factors(const uint8_t* cur, const Geom& g, int x, int y,
-                                             float& ux, float& uy)
+__device__ __forceinline__ unsigned sad8(const P8& r, const P8& c)
 {
-    ux = 0.0f;
-    uy = 0.0f;
-    const float lim = 2.0f * g.theta;
-    const uint8_t* p = cur + (size_t)y * g.W + x;
-    if (x > 0 && x < g.W - 1) {
-        const int gx = (int)__ldg(p + 1) - (int)__ldg(p - 1);
-        if (fabsf((float)gx) >= lim) ux = __fdiv_rn(2.0f, (float)gx);
+    return __vsadu4(r.lo, c.lo) + __vsadu4(r.hi, c.hi);
+}
+__device__ __forceinline__ int byte_of(const P8& p, int k)
+{
+    return (int)(((k < 4 ? p.lo : p.hi) >> (8 * (k & 3))) & 0xffu);
+}
+// Sum of squared differences of the 8 pixels: sum r^2 + sum c^2 - 2 sum rc
+// with unsigned byte dot products (exact integer arithmetic).
+__device__ __forceinline__ unsigned sq8(const P8& r, const P8& c)
+{
+    const unsigned rr = __dp4a(r.lo, r.lo, __dp4a(r.hi, r.hi, 0u));
+    const unsigned cc = __dp4a(c.lo, c.lo, __dp4a(c.hi, c.hi, 0u));
+    const unsigned rc = __dp4a(r.lo, c.lo, __dp4a(r.hi, c.hi, 0u));
+    return rr + cc - 2u * rc;
+}
+
+// Warp sums of two per-lane values below 2^16 whose totals stay below 2^16
+// (SADs of 8 pixels: at most 8*255 per lane, 65280 per MB), in one reduction.
+__device__ __forceinline__ void warp_sum2(unsigned a, unsigned b, unsigned& sa, unsigned& sb)
+{
+    const unsigned t = __reduce_add_sync(kFull, a | (b << 16));
+    sa = t & 0xffffu;
+    sb = t >> 16;
+}
+
+// 24 bytes of a window row from the 8-byte boundary at or before `pos`.
+__device__ __forceinline__ void row24(const uint8_t* win, int pos, unsigned (&w)[6], int& off)
+{
+    off = pos & 7;
+    const uint8_t* q = win + (pos - off);
+    const uint2 a = *reinterpret_cast<const uint2*>(q);
+    const uint2 b = *reinterpret_cast<const uint2*>(q + 8);
+    const uint2 c = *reinterpret_cast<const uint2*>(q + 16);
+    w[0] = a.x;
+    w[1] = a.y;
+    w[2] = b.x;
+    w[3] = b.y;
+    w[4] = c.x;
+    w[5] = c.y;
+}
+// Bytes off .. off+7 (off in 0..11) of the 24 bytes in w.
+__device__ __forceinline__ P8 extract8w(const unsigned (&w)[6], int off)
+{
+    const int b = off >> 2, sh = 8 * (off & 3);
+    unsigned a0 = w[0], a1 = w[1], a2 = w[2];
+    if (b == 1) {
+        a0 = w[1];
+        a1 = w[2];
+        a2 = w[3];
     }
-    if (y > 0 && y < g.H - 1) {
-        const int gy = (int)__ldg(p + g.W) - (int)__ldg(p - g.W);
-        if (fabsf((float)gy) >= lim) uy = __fdiv_rn(2.0f, (float)gy);
+    if (b == 2) {
+        a0 = w[2];
+        a1 = w[3];
+        a2 = w[4];
     }
+    if (b == 3) {
+        a0 = w[3];
+        a1 = w[4];
+        a2 = w[5];
+    }
+    P8 r;
+    r.lo = __funnelshift_r(a0, a1, sh);
+    r.hi = __funnelshift_r(a1, a2, sh);
+    return r;
+}
+__device__ __forceinline__ P8 avg2p(const P8& a, const P8& b)
+{
+    P8 r;
+    r.lo = avg2w(a.lo, b.lo);
+    r.hi = avg2w(a.hi, b.hi);
+    return r;
+}
+__device__ __forceinline__ P8 avg4p(const P8& a, const P8& b, const P8& c, const P8& d)
+{
+    P8 r;
+    r.lo = avg4w(a.lo, b.lo, c.lo, d.lo);
+    r.hi = avg4w(a.hi, b.hi, c.hi, d.hi);
+    return r;
+}
+
+// Half-sample positions d-1, d, d+1 along one axis, for the parity P of d:
+// position i reads integer sample (base) and, when frac, averages it with
+// the next one.  Even d: (-1,frac) (0) (0,frac); odd d: (0) (0,frac) (1).
+template <int P>
+__device__ __forceinline__ constexpr int rc_base(int i)
+{
+    return P ? (i == 2 ? 1 : 0) : (i == 0 ? -1 : 0);
+}
+template <int P>
+__device__ __forceinline__ constexpr bool rc_frac(int i)
+{
+    return P ? (i == 1) : (i != 1);
+}
+
+// Samples of the lane's 8 pixels at the nine positions d + (i, j), i, j in
+// {-1, 0, 1} MV units, s[(j+1)*3 + (i+1)], from the 3x3 integer
+// neighbourhood X (rows/columns -1..1 around floor(d/h)).  Same MPEG-4
+// rounding as ref8.
+template <int PX, int PY>
+__device__ __forceinline__ void combine9(const P8 (&X)[3][3], P8 (&s)[9])
+{
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int bx = rc_base<PX>(i) + 1, by = rc_base<PY>(j) + 1;
+            const bool fx = rc_frac<PX>(i), fy = rc_frac<PY>(j);
+            const P8 a = X[by][bx];
+            P8 r = a;
+            if (fx && !fy) r = avg2p(a, X[by][bx + 1]);
+            if (!fx && fy) r = avg2p(a, X[by + 1][bx]);
+            if (fx && fy) r = avg4p(a, X[by][bx + 1], X[by + 1][bx], X[by + 1][bx + 1]);
+            s[j * 3 + i] = r;
+        }
+}
+
+// All nine samples around d; every position d + (i, j) must lie in V.  Only
+// the integer rows/columns the nine positions use are read (for an odd
+// half-sample coordinate the row/column before floor(d/2) is not used, and
+// it may lie outside the window), so every read stays inside the window.
+__device__ __forceinline__ void block3x3(const uint8_t* win, int pitch, int lx, int ly, int dx, int dy, int h,
+                                         P8 (&s)[9])
+{
+    int cx = dx, cy = dy, px = 0, py = 0;
+    if (h == 2) {
+        cx = dx >> 1;
+        cy = dy >> 1;
+        px = dx & 1;
+        py = dy & 1;
+    }
+    P8 X[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) X[r][t] = P8{0u, 0u};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        if (r < py) continue;
+        unsigned w[6];
+        int off;
+        row24(win, (ly + cy + r - 1) * pitch + lx + cx - 1 + px, w, off);
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            if (t >= px) X[r][t] = extract8w(w, off + t - px);
+    }
+    if (h == 1) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) s[j * 3 + i] = X[j][i];
+        return;
+    }
+    if (!px && !py) combine9<0, 0>(X, s);
+    else if (px && !py) combine9<1, 0>(X, s);
+    else if (!px && py) combine9<0, 1>(X, s);
+    else combine9<1, 1>(X, s);
+}
+
+// Eq. 4 / Eq. 5 factors of the lane's 8 pixels (x0..x0+7, row y): u = 2/g
+// when |g| >= 2*Theta, g the central difference of the current frame (twice
+// the derivative); 0 on the frame's outer rows/columns.  `c` holds the 8
+// current pixels.
+// rcp[g + 255] = 2/g in IEEE FP32 (round to nearest), g = -255..255.
+__device__ __forceinline__ void fill_rcp(float* rcp)
+{
+    for (int i = threadIdx.x; i < 511; i += blockDim.x) {
+        const int g = i - 255;
+        rcp[i] = g ? __fdiv_rn(2.0f, (float)g) : 0.0f;
+    }
+}
+
+__device__ __forceinline__ void grad_factors8(const uint8_t* cur, int W, int H, int x0, int y, const P8& c,
+                                              float theta, const float* rcp, float (&ux)[8], float (&uy)[8])
+{
+    const float lim = 2.0f * theta;
+    const uint8_t* row = cur + (size_t)y * W;
+    const int left = x0 > 0 ? (int)__ldg(row + x0 - 1) : 0;
+    const int right = x0 + 8 < W ? (int)__ldg(row + x0 + 8) : 0;
+    P8 up = {0u, 0u}, dn = {0u, 0u};
+    if (y > 0) {
+        const uint2 t = __ldg(reinterpret_cast<const uint2*>(row - W + x0));
+        up.lo = t.x;
+        up.hi = t.y;
+    }
+    if (y < H - 1) {
+        const uint2 t = __ldg(reinterpret_cast<const uint2*>(row + W + x0));
+        dn.lo = t.x;
+        dn.hi = t.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int x = x0 + k;
+        ux[k] = 0.0f;
+        uy[k] = 0.0f;
+        if (x > 0 && x < W - 1) {
+            const int r = k < 7 ? byte_of(c, k + 1) : right;
+            const int l = k > 0 ? byte_of(c, k - 1) : left;
+            const int g = r - l;
+            if (fabsf((float)g) >= lim) ux[k] = rcp[g + 255];
+        }
+        if (y > 0 && y < H - 1) {
+            const int g = byte_of(dn, k) - byte_of(up, k);
+            if (fabsf((float)g) >= lim) uy[k] = rcp[g + 255];
+        }
+    }
+}
+
+// FP32 sums of the terms DPD*ux and DPD*uy over the 256 pixels as one
+// contiguous pairwise tree in row-major order: the lane's 8 terms
+// ((t0+t1)+(t2+t3))+((t4+t5)+(t6+t7)), then lanes paired at offsets 1..16.
+// Round-to-nearest products and adds only (no contraction).  Every lane
+// receives both sums.
+__device__ __forceinline__ void grad_sums(const P8& r, const P8& c, const float (&ux)[8], const float (&uy)[8],
+                                          float& sx, float& sy)
+{
+    float tx[8], ty[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float dpd = (float)(byte_of(r, k) - byte_of(c, k));
+        tx[k] = __fmul_rn(dpd, ux[k]);
+        ty[k] = __fmul_rn(dpd, uy[k]);
+    }
+    float a = __fadd_rn(__fadd_rn(__fadd_rn(tx[0], tx[1]), __fadd_rn(tx[2], tx[3])),
+                        __fadd_rn(__fadd_rn(tx[4], tx[5]), __fadd_rn(tx[6], tx[7])));
+    float b = __fadd_rn(__fadd_rn(__fadd_rn(ty[0], ty[1]), __fadd_rn(ty[2], ty[3])),
+                        __fadd_rn(__fadd_rn(ty[4], ty[5]), __fadd_rn(ty[6], ty[7])));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float pa = __shfl_down_sync(kFull, a, o);
+        const float pb = __shfl_down_sync(kFull, b, o);
+        a = __fadd_rn(a, pa);
+        b = __fadd_rn(b, pb);
+    }
+    sx = __shfl_sync(kFull, a, 0);
+    sy = __shfl_sync(kFull, b, 0);
 }
 
 // Eq. 3 block update from the pixel sums: -eps * mean over pixels with u != 0.
@@ -217,19 +476,52 @@ __device__ __forceinline__ float update_of(float sum, int n, float eps)
 
 // Alpha mismatches of one BAB row: current row bits vs the reference row
 // displaced by the full-pel vector (fdx, fdy).
-__device__ __forceinline__ unsigned shape_row(const uint32_t* pcur, const uint32_t* pref, const Geom& g,
-                                              int X0, int Y0, int r, int fdx, int fdy)
+__device__ __forceinline__ unsigned shape_row(const uint32_t* pcur, const uint32_t* pref, int Wp, int X0, int Y0,
+                                              int r, int fdx, int fdy)
 {
-    const uint32_t* rc = pcur + (size_t)(Y0 + r) * g.Wp;
+    const uint32_t* rc = pcur + (size_t)(Y0 + r) * Wp;
     const unsigned cb = (__ldg(rc + (X0 >> 5)) >> (X0 & 31)) & 0xffffu;
     const int xr = X0 + fdx;
-    const uint32_t* rr = pref + (size_t)(Y0 + r + fdy) * g.Wp;
+    const uint32_t* rr = pref + (size_t)(Y0 + r + fdy) * Wp;
     const unsigned rb = __funnelshift_r(__ldg(rr + (xr >> 5)), __ldg(rr + (xr >> 5) + 1), xr & 31) & 0xffffu;
     return __popc(cb ^ rb);
 }
 
+// Shape costs of up to 5 candidates (keys in cand[]) with one warp: lane l
+// takes row l&15 of candidates (l>>4), (l>>4)+2, (l>>4)+4.  All lanes get
+// the totals.
+__device__ __forceinline__ void shape_costs(const uint32_t* pcur, const uint32_t* pref, int Wp, int X0, int Y0,
+                                            const int (&cand)[5], int nc, int h, int lane, unsigned (&cost)[5])
+{
+    const int r = lane & 15, half = lane >> 4;
+    unsigned s[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int c = half + 2 * j;
+        if (c < nc) {
+            int key = cand[0];
+#pragma unroll
+            for (int q = 1; q < 5; ++q)
+                if (q == c) key = cand[q];
+            s[j] = shape_row(pcur, pref, Wp, X0, Y0, r, mv_x(key) / h, mv_y(key) / h);  // trunc toward zero
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        s[j] += __shfl_xor_sync(kFull, s[j], 8);
+        s[j] += __shfl_xor_sync(kFull, s[j], 4);
+        s[j] += __shfl_xor_sync(kFull, s[j], 2);
+        s[j] += __shfl_xor_sync(kFull, s[j], 1);
+    }
+    cost[0] = __shfl_sync(kFull, s[0], 0);
+    cost[1] = __shfl_sync(kFull, s[0], 16);
+    cost[2] = __shfl_sync(kFull, s[1], 0);
+    cost[3] = __shfl_sync(kFull, s[1], 16);
+    cost[4] = __shfl_sync(kFull, s[2], 0);
+}
+
 // ============================================================ classify ==
-__global__ void __launch_bounds__(kThreads) classify_pack_kernel(const Geom g, const ClassifyArgs a)
+__global__ void __launch_bounds__(256) classify_pack_kernel(const Geom g, const ClassifyArgs a)
 {
     __shared__ unsigned cnt[kMaxDim / 16];
     const int v = blockIdx.x, f = blockIdx.y, tid = threadIdx.x;
@@ -238,16 +530,17 @@ __global__ void __launch_bounds__(kThreads) classify_pack_kernel(const Geom g, c
             a.status->ticket = 0;
             a.status->abort = 0;
         }
+        if (a.desc_out && tid == 0) *a.desc_out = a.desc;
         if (a.sse)
-            for (int i = tid; i < a.n_sse; i += kThreads) a.sse[i] = 0ull;
+            for (int i = tid; i < a.n_sse; i += blockDim.x) a.sse[i] = 0ull;
     }
-    for (int i = tid; i < g.MBW; i += kThreads) cnt[i] = 0;
+    for (int i = tid; i < g.MBW; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     const size_t FS = (size_t)g.W * g.H;
     const uint8_t* al = a.alpha + (size_t)f * FS + (size_t)v * 16 * g.W;
     uint16_t* pk = a.packed ? reinterpret_cast<uint16_t*>(a.packed + ((size_t)f * g.H + v * 16) * g.Wp) : nullptr;
     const int segs = g.MBW, hw = 2 * g.Wp;  // 16-pixel segments per row; u16 slots per packed row
-    for (int it = tid; it < 16 * hw; it += kThreads) {
+    for (int it = tid; it < 16 * hw; it += blockDim.x) {
         const int r = it / hw, s = it - r * hw;
         unsigned m = 0;
         if (s < segs) {
@@ -264,257 +557,824 @@ __global__ void __launch_bounds__(kThreads) classify_pack_kernel(const Geom g, c
         if (pk) pk[(size_t)r * hw + s] = (uint16_t)m;
     }
     __syncthreads();
-    for (int s = tid; s < segs; s += kThreads) {
+    for (int s = tid; s < segs; s += blockDim.x) {
         const unsigned n = cnt[s];
         a.cls[(size_t)f * g.M + v * g.MBW + s] =
             (uint8_t)(n == 0 ? SME_TRANSPARENT : (n == 256 ? SME_OPAQUE : SME_BOUNDARY));
     }
 }
 
-// ================================================================== ME ==
-__global__ void __launch_bounds__(kThreads) me_kernel(const Geom g, const MeArgs a)
+// ======================================================= per-MB search ==
+struct MbResult {
+    int dx, dy, iters, nlog;
+    unsigned cost;
+    float lastx, lasty;
+    P8 r8;  // reference samples of the lane's pixels at the final vector
+};
+
+// Fig. 1 from the candidate comparison on: shape cost (boundary) or texture
+// SAD (opaque) of the candidates, first strict minimum, and on opaque MBs the
+// pixel recursive search of Sec. 3.2.  The candidates are already logged in
+// slog[0..nc); the evaluated PRS positions are appended by lane 0.  The
+// neighbours of the eight-direction check are evaluated together with the
+// proposal from one 3x3 neighbourhood when d is inside V; the decisions
+// follow the paper's order (proposal first, then the neighbours).
+__device__ __forceinline__ MbResult search_mb(const Method& m, int cls, const uint8_t* win, int pitch, int lx,
+                                              int ly, const P8& c8, const float (&ux)[8], const float (&uy)[8],
+                                              int nx, int ny, const VRange& V, const int (&cand)[5], int nc,
+                                              const uint32_t* pcur, const uint32_t* pref, int Wp, int X0, int Y0,
+                                              int* slog, int lane)
 {
-    extern __shared__ __align__(16) uint8_t win[];
-    __shared__ int s_ticket, s_stop;
-    __shared__ int s_cand[5];
-    __shared__ unsigned s_cost[5];
-    __shared__ unsigned s_red[2][16][8];
-    __shared__ float s_fred[2][2][8];
-    __shared__ int s_log[kMaxLog];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int pi = tid & 15, pj = tid >> 4;
-    const size_t FS = (size_t)g.W * g.H;
-    const int pitch = win_pitch(g), h = g.h;
-    int rb = 0;
-
-    for (;;) {
-        if (tid == 0) {
-            int t = (int)atomicAdd(&a.status->ticket, 1u);
-            if (ld_relaxed(&a.status->abort)) t = a.total;
-            s_ticket = t;
-            s_stop = 0;
-        }
-        __syncthreads();
-        const int t = s_ticket;
-        if (t >= a.total) break;
-        const int idx = a.sched[t];
-        const int k = idx / g.M, mb = idx - k * g.M;
-        const int u = mb % g.MBW, v = mb / g.MBW;
-        const int X0 = 16 * u, Y0 = 16 * v, x = X0 + pi, y = Y0 + pj;
-        const uint8_t* ref = a.luma + (size_t)k * FS;
-        const uint8_t* cur = a.luma + (size_t)(k + a.rd) * FS;
-        const int cls = __ldg(a.cls + (size_t)(k + a.rd) * g.M + mb);
-        const int cval = __ldg(cur + (size_t)y * g.W + x);
-
-        if (cls == SME_TRANSPARENT) {
-            // Fig. 1: no vector is computed; (0,0) is final at once.
-            if (tid == 0) {
-                a.mv[idx] = sme_mv{0, 0};
-                if (t != a.fault_ticket) st_release(a.ready + idx, a.epoch);
-                if (a.cost) a.cost[idx] = 0;
-                if (a.disp) { a.disp[2 * idx] = 0.0f; a.disp[2 * idx + 1] = 0.0f; }
-                if (a.iters) a.iters[idx] = 0;
-                if (a.npos) a.npos[idx] = 0;
-                if (a.out_cls) a.out_cls[idx] = (uint8_t)cls;
+    const int h = m.h;
+    MbResult res;
+    res.iters = 0;
+    res.lastx = 0.0f;
+    res.lasty = 0.0f;
+    int nlog = nc;
+    int dx, dy;
+    unsigned cost;
+    if (cls == SME_BOUNDARY) {
+        // Fig. 1 boundary branch: alpha mismatch of the BABs.
+        unsigned sc[5];
+        shape_costs(pcur, pref, Wp, X0, Y0, cand, nc, h, lane, sc);
+        int best = cand[0];
+        cost = sc[0];
+#pragma unroll
+        for (int c = 1; c < 5; ++c)
+            if (c < nc && sc[c] < cost) {
+                cost = sc[c];
+                best = cand[c];
             }
-            const int r = __ldg(ref + (size_t)y * g.W + x);
-            unsigned sq[1] = {(unsigned)((cval - r) * (cval - r))};
-            if (a.pred) a.pred[(size_t)k * FS + (size_t)y * g.W + x] = (uint8_t)r;
-            if (a.sse || a.sse_mb) {
-                block_sum<1>(sq, s_red[rb], lane, warp);
-                rb ^= 1;
-                if (tid == 0) {
-                    if (a.sse) atomicAdd(a.sse + k, (unsigned long long)sq[0]);
-                    if (a.sse_mb) a.sse_mb[idx] = sq[0];
-                }
-            }
-            __syncthreads();
-            continue;
+        dx = mv_x(best);
+        dy = mv_y(best);
+        res.r8 = ref8(win, pitch, lx, ly, dx, dy, h);
+    } else {
+        // Fig. 1 opaque branch: texture SAD of the candidates.
+        P8 cs8[5];
+        unsigned part[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            cs8[c] = c < nc ? ref8(win, pitch, lx, ly, mv_x(cand[c]), mv_y(cand[c]), h) : c8;
+            part[c] = sad8(cs8[c], c8);
         }
-
-        // ---- work that does not depend on the neighbours: prefetch ----
-        int wx0, wy0;
-        stage_window(win, ref, g, X0, Y0, tid, wx0, wy0);
-        const int lx = x - wx0, ly = y - wy0;
-        float ux = 0.0f, uy = 0.0f;
-        if (cls == SME_OPAQUE) grad_factors(cur, g, x, y, ux, uy);
-        const int nx = __syncthreads_count(ux != 0.0f);
-        const int ny = __syncthreads_count(uy != 0.0f);
-        const VRange V = valid_range(g, X0, Y0);
-
-        // ---- candidates A, B, C, T (Fig. 1, Fig. 3) + optional seed ----
-        if (tid < 4) {
-            int dep = -1;
-            if (tid == 0 && u > 0) dep = idx - 1;                          // A
-            if (tid == 1 && v > 0) dep = idx - g.MBW;                      // B
-            if (tid == 2 && v > 0 && u < g.MBW - 1) dep = idx - g.MBW + 1; // C
-            if (tid == 3 && k > 0) dep = idx - g.M;                        // T
-            int key = 0;
-            if (dep >= 0) {
-                if (wait_flag(a.ready + dep, a.epoch, a.status, a.timeout_ns)) {
-                    const unsigned raw = __ldcg(reinterpret_cast<const unsigned*>(a.mv + dep));
-                    key = (int)raw;
-                } else {
-                    if (!ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
-                    atomicExch(&s_stop, 1);
-                }
-            } else if (tid == 3 && a.temporal_in) {
-                key = (int)__ldg(reinterpret_cast<const unsigned*>(a.temporal_in + mb));
+        unsigned sad[5];
+        warp_sum2(part[0], part[1], sad[0], sad[1]);
+        warp_sum2(part[2], part[3], sad[2], sad[3]);
+        sad[4] = nc > 4 ? __reduce_add_sync(kFull, part[4]) : 0u;
+        int best = cand[0];
+        cost = sad[0];
+        P8 r8 = cs8[0];
+#pragma unroll
+        for (int c = 1; c < 5; ++c)
+            if (c < nc && sad[c] < cost) {
+                cost = sad[c];
+                best = cand[c];
+                r8 = cs8[c];
             }
-            s_cand[tid] = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
-        } else if (tid == 4 && a.seed) {
-            const float sx = fminf(fmaxf(__fmul_rn((float)h, __ldg(a.seed + 2 * (size_t)idx)), -1024.0f), 1024.0f);
-            const float sy = fminf(fmaxf(__fmul_rn((float)h, __ldg(a.seed + 2 * (size_t)idx + 1)), -1024.0f), 1024.0f);
-            s_cand[4] = pack_mv(clampi((int)roundf(sx), V.lox, V.hix), clampi((int)roundf(sy), V.loy, V.hiy));
-        }
-        __syncthreads();
-        if (s_stop) break;
-        const int nc = a.seed ? 5 : 4;
-        if (tid < nc) s_log[tid] = s_cand[tid];
-        int nlog = nc;
+        dx = mv_x(best);
+        dy = mv_y(best);
 
-        int dx, dy;
-        unsigned cost;
+        // Sec. 3.2: pixel recursive search.
         int iters = 0;
         float lastx = 0.0f, lasty = 0.0f;
-        int diff;
-        if (cls == SME_BOUNDARY) {
-            // Fig. 1 boundary branch: alpha mismatch of the BABs.
-            unsigned part = 0;
-            if (tid < nc * 16) {
-                const int key = s_cand[tid >> 4];
-                const int fdx = mv_x(key) / h, fdy = mv_y(key) / h;  // trunc toward zero
-                part = shape_row(a.packed + (size_t)(k + a.rd) * g.H * g.Wp, a.packed + (size_t)k * g.H * g.Wp,
-                                 g, X0, Y0, tid & 15, fdx, fdy);
-            }
-            part += __shfl_xor_sync(kFull, part, 8);
-            part += __shfl_xor_sync(kFull, part, 4);
-            part += __shfl_xor_sync(kFull, part, 2);
-            part += __shfl_xor_sync(kFull, part, 1);
-            if (tid < nc * 16 && (tid & 15) == 0) s_cost[tid >> 4] = part;
-            __syncthreads();
-            int best = 0;
-            for (int c = 1; c < nc; ++c)
-                if (s_cost[c] < s_cost[best]) best = c;
-            dx = mv_x(s_cand[best]);
-            dy = mv_y(s_cand[best]);
-            cost = s_cost[best];
-            diff = ref_at(win, pitch, lx, ly, dx, dy, h) - cval;
-        } else {
-            // Fig. 1 opaque branch: texture SAD of the candidates.
-            unsigned sad[5];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                const int key = s_cand[c < nc ? c : 0];
-                sad[c] = c < nc ? (unsigned)abs(ref_at(win, pitch, lx, ly, mv_x(key), mv_y(key), h) - cval) : 0u;
-            }
-            block_sum<5>(sad, s_red[rb], lane, warp);
-            rb ^= 1;
-            int best = 0;
-            unsigned bestc = sad[0];
-#pragma unroll
-            for (int c = 1; c < 5; ++c)
-                if (c < nc && sad[c] < bestc) {
-                    best = c;
-                    bestc = sad[c];
-                }
-            dx = mv_x(s_cand[best]);
-            dy = mv_y(s_cand[best]);
-            cost = bestc;
-            diff = ref_at(win, pitch, lx, ly, dx, dy, h) - cval;
-
-            // Sec. 3.2: pixel recursive search.
-            while (iters < g.K) {
-                ++iters;
-                float sx = __fmul_rn((float)diff, ux), sy = __fmul_rn((float)diff, uy);
-                tree_sum2(sx, sy, s_fred[rb], lane, warp);
-                rb ^= 1;
-                lastx = update_of(sx, nx, g.eps);
-                lasty = update_of(sy, ny, g.eps);
-                const int qx = clampi(dx + (int)roundf(__fmul_rn((float)h, lastx)), V.lox, V.hix);
-                const int qy = clampi(dy + (int)roundf(__fmul_rn((float)h, lasty)), V.loy, V.hiy);
-                const bool qmove = (qx != dx) || (qy != dy);
-                unsigned val[9];
-                val[0] = qmove ? (unsigned)abs(ref_at(win, pitch, lx, ly, qx, qy, h) - cval) : 0u;
-#pragma unroll
-                for (int n = 1; n < 9; ++n) {
-                    const int e = n < 5 ? n - 1 : n;  // skip the centre of the 3x3 raster
-                    const int ii = e % 3 - 1, jj = e / 3 - 1;
-                    const int ex = clampi(dx + ii, V.lox, V.hix), ey = clampi(dy + jj, V.loy, V.hiy);
-                    val[n] = (ex != dx || ey != dy) ? (unsigned)abs(ref_at(win, pitch, lx, ly, ex, ey, h) - cval) : 0u;
-                }
-                block_sum<9>(val, s_red[rb], lane, warp);
-                rb ^= 1;
+        while (iters < m.K) {
+            ++iters;
+            float sx, sy;
+            grad_sums(r8, c8, ux, uy, sx, sy);
+            lastx = update_of(sx, nx, m.eps);
+            lasty = update_of(sy, ny, m.eps);
+            const int qx = clampi(dx + (int)roundf(__fmul_rn((float)h, lastx)), V.lox, V.hix);
+            const int qy = clampi(dy + (int)roundf(__fmul_rn((float)h, lasty)), V.loy, V.hiy);
+            const bool qmove = (qx != dx) || (qy != dy);
+            const bool qnear = qmove && abs(qx - dx) <= 1 && abs(qy - dy) <= 1;
+            const bool inner = dx > V.lox && dx < V.hix && dy > V.loy && dy < V.hiy;
+            if (inner) {
+                // The proposal (when it is a neighbour) and the eight
+                // neighbours from one neighbourhood; clamping is the identity.
+                P8 nb9[9];
+                block3x3(win, pitch, lx, ly, dx, dy, h, nb9);
+                unsigned sad9[9];
+                warp_sum2(sad8(nb9[0], c8), sad8(nb9[1], c8), sad9[0], sad9[1]);
+                warp_sum2(sad8(nb9[2], c8), sad8(nb9[3], c8), sad9[2], sad9[3]);
+                warp_sum2(sad8(nb9[5], c8), sad8(nb9[6], c8), sad9[5], sad9[6]);
+                warp_sum2(sad8(nb9[7], c8), sad8(nb9[8], c8), sad9[7], sad9[8]);
+                sad9[4] = cost;
                 if (qmove) {
-                    if (tid == 0) s_log[nlog] = pack_mv(qx, qy);
+                    unsigned cq;
+                    P8 q8;
+                    if (qnear) {
+                        const int qi = (qy - dy + 1) * 3 + (qx - dx + 1);
+                        cq = sad9[0];
+                        q8 = nb9[0];
+#pragma unroll
+                        for (int n = 1; n < 9; ++n)
+                            if (n == qi) {
+                                cq = sad9[n];
+                                q8 = nb9[n];
+                            }
+                    } else {
+                        q8 = ref8(win, pitch, lx, ly, qx, qy, h);
+                        cq = __reduce_add_sync(kFull, sad8(q8, c8));
+                    }
+                    if (lane == 0) slog[nlog] = pack_mv(qx, qy);
                     ++nlog;
-                    if (val[0] < cost) {
+                    if (cq < cost) {
                         dx = qx;
                         dy = qy;
-                        cost = val[0];
-                        diff = ref_at(win, pitch, lx, ly, dx, dy, h) - cval;
+                        cost = cq;
+                        r8 = q8;
                         continue;
                     }
                 }
                 // Fig. 4: eight directions at one MV unit, first strict minimum.
                 unsigned bc = cost;
-                int bx = dx, by = dy;
+                int bn = 4;
 #pragma unroll
-                for (int n = 1; n < 9; ++n) {
-                    const int e = n < 5 ? n - 1 : n;
-                    const int ii = e % 3 - 1, jj = e / 3 - 1;
-                    const int ex = clampi(dx + ii, V.lox, V.hix), ey = clampi(dy + jj, V.loy, V.hiy);
-                    if (ex != dx || ey != dy) {
-                        if (tid == 0) s_log[nlog] = pack_mv(ex, ey);
-                        ++nlog;
-                        if (val[n] < bc) {
-                            bc = val[n];
-                            bx = ex;
-                            by = ey;
-                        }
+                for (int n = 0; n < 9; ++n) {
+                    if (n == 4) continue;
+                    if (lane == 0) slog[nlog] = pack_mv(dx + n % 3 - 1, dy + n / 3 - 1);
+                    ++nlog;
+                    if (sad9[n] < bc) {
+                        bc = sad9[n];
+                        bn = n;
                     }
                 }
                 if (bc < cost) {
-                    dx = bx;
-                    dy = by;
+#pragma unroll
+                    for (int n = 0; n < 9; ++n)
+                        if (n == bn) r8 = nb9[n];
+                    dx += bn % 3 - 1;
+                    dy += bn / 3 - 1;
                     cost = bc;
-                    diff = ref_at(win, pitch, lx, ly, dx, dy, h) - cval;
                     continue;
                 }
                 break;
             }
+            // d on the edge of V: the clamped neighbours one by one.
+            if (qmove) {
+                const P8 q8 = ref8(win, pitch, lx, ly, qx, qy, h);
+                const unsigned cq = __reduce_add_sync(kFull, sad8(q8, c8));
+                if (lane == 0) slog[nlog] = pack_mv(qx, qy);
+                ++nlog;
+                if (cq < cost) {
+                    dx = qx;
+                    dy = qy;
+                    cost = cq;
+                    r8 = q8;
+                    continue;
+                }
+            }
+            unsigned bc = cost;
+            int bx = dx, by = dy;
+#pragma unroll
+            for (int n = 1; n < 9; ++n) {
+                const int e = n < 5 ? n - 1 : n;  // 3x3 raster without its centre
+                const int ex = clampi(dx + e % 3 - 1, V.lox, V.hix), ey = clampi(dy + e / 3 - 1, V.loy, V.hiy);
+                if (ex != dx || ey != dy) {
+                    const unsigned cn = __reduce_add_sync(kFull, sad8(ref8(win, pitch, lx, ly, ex, ey, h), c8));
+                    if (lane == 0) slog[nlog] = pack_mv(ex, ey);
+                    ++nlog;
+                    if (cn < bc) {
+                        bc = cn;
+                        bx = ex;
+                        by = ey;
+                    }
+                }
+            }
+            if (bc < cost) {
+                dx = bx;
+                dy = by;
+                cost = bc;
+                r8 = ref8(win, pitch, lx, ly, dx, dy, h);
+                continue;
+            }
+            break;
+        }
+        res.r8 = r8;
+        res.iters = iters;
+        res.lastx = lastx;
+        res.lasty = lasty;
+    }
+    res.dx = dx;
+    res.dy = dy;
+    res.cost = cost;
+    res.nlog = nlog;
+    return res;
+}
+
+// Off the dependency chain: per-MB outputs, the distinct evaluated positions
+// (Table 1 unit), and the motion-compensated prediction with its SSE (Sec. 4).
+__device__ __forceinline__ void finish_mb(const SeqDesc* sd, int idx, int k, int cls, const MbResult& r, const P8& c8,
+                                          const int* slog, int lane, size_t FS, int W, int y, int x0)
+{
+    if (lane == 1) {
+        if (sd->cost) sd->cost[idx] = r.cost;
+        if (sd->iters) sd->iters[idx] = (uint8_t)r.iters;
+        if (sd->out_cls) sd->out_cls[idx] = (uint8_t)cls;
+    }
+    if (lane == 2 && sd->disp) {
+        sd->disp[2 * idx] = r.lastx;
+        sd->disp[2 * idx + 1] = r.lasty;
+    }
+    __syncwarp();
+    unsigned first = 0;
+    if (r.nlog <= 32) {
+        // Lanes holding equal keys match; the lowest such lane counts once.
+        // Unused lanes hold keys no vector can have (|dy| <= 128).
+        const int kk = lane < r.nlog ? slog[lane] : (0x7fff0000 | lane);
+        const unsigned eq = __match_any_sync(kFull, kk);
+        first = (lane < r.nlog && (__ffs(eq) - 1) == lane) ? 1u : 0u;
+    } else {
+        for (int e = lane; e < r.nlog; e += 32) {
+            const int kk = slog[e];
+            bool f = true;
+            for (int j = 0; j < e; ++j)
+                if (slog[j] == kk) {
+                    f = false;
+                    break;
+                }
+            first += f;
+        }
+    }
+    // One reduction for both: the MB's SSE is below 2^24 (256 * 255^2) and the
+    // position count below 2^8.
+    const unsigned both = __reduce_add_sync(kFull, sq8(r.r8, c8) | (first << 24));
+    const unsigned sse = both & 0xffffffu;
+    if (lane == 0) {
+        if (sd->npos) sd->npos[idx] = (uint8_t)(both >> 24);
+        if (sd->sse) atomicAdd(sd->sse + k, (unsigned long long)sse);
+        if (sd->sse_mb) sd->sse_mb[idx] = sse;
+    }
+    if (sd->pred)
+        *reinterpret_cast<uint2*>(sd->pred + (size_t)k * FS + (size_t)y * W + x0) = make_uint2(r.r8.lo, r.r8.hi);
+    __syncwarp();
+}
+
+// Fig. 1: a transparent MB gets no vector; its outputs and its co-located
+// prediction error (Sec. 4).  The vector (0,0) is published by the caller.
+__device__ __forceinline__ void transparent_mb(const SeqDesc* sd, int idx, int k, const uint8_t* ref, const P8& c8,
+                                               int lane, size_t FS, int W, int y, int x0)
+{
+    if (lane == 0) {
+        sd->mv[idx] = sme_mv{0, 0};
+        if (sd->cost) sd->cost[idx] = 0;
+        if (sd->disp) {
+            sd->disp[2 * idx] = 0.0f;
+            sd->disp[2 * idx + 1] = 0.0f;
+        }
+        if (sd->iters) sd->iters[idx] = 0;
+        if (sd->npos) sd->npos[idx] = 0;
+        if (sd->out_cls) sd->out_cls[idx] = (uint8_t)SME_TRANSPARENT;
+    }
+    const uint2 t2 = __ldg(reinterpret_cast<const uint2*>(ref + (size_t)y * W + x0));
+    P8 r8;
+    r8.lo = t2.x;
+    r8.hi = t2.y;
+    if (sd->pred) *reinterpret_cast<uint2*>(sd->pred + (size_t)k * FS + (size_t)y * W + x0) = t2;
+    if (sd->sse || sd->sse_mb) {
+        const unsigned s = __reduce_add_sync(kFull, sq8(r8, c8));
+        if (lane == 0) {
+            if (sd->sse) atomicAdd(sd->sse + k, (unsigned long long)s);
+            if (sd->sse_mb) sd->sse_mb[idx] = s;
+        }
+    }
+    __syncwarp();
+}
+
+// Eq. 4 factors of the lane's pixels and their counts over the MB.
+__device__ __forceinline__ void mb_factors(const uint8_t* cur, int W, int H, int x0, int y, const P8& c8, float theta,
+                                           const float* rcp, float (&ux)[8], float (&uy)[8], int& nx, int& ny)
+{
+    grad_factors8(cur, W, H, x0, y, c8, theta, rcp, ux, uy);
+    int cx = 0, cy = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        cx += ux[q] != 0.0f;
+        cy += uy[q] != 0.0f;
+    }
+    nx = (int)__reduce_add_sync(kFull, (unsigned)cx);
+    ny = (int)__reduce_add_sync(kFull, (unsigned)cy);
+}
+
+__device__ __forceinline__ int seed_key(const SeqDesc* sd, int idx, int h, const VRange& V)
+{
+    const float sx = fminf(fmaxf(__fmul_rn((float)h, __ldg(sd->seed + 2 * (size_t)idx)), -1024.0f), 1024.0f);
+    const float sy = fminf(fmaxf(__fmul_rn((float)h, __ldg(sd->seed + 2 * (size_t)idx + 1)), -1024.0f), 1024.0f);
+    return pack_mv(clampi((int)roundf(sx), V.lox, V.hix), clampi((int)roundf(sy), V.loy, V.hiy));
+}
+
+__device__ __forceinline__ P8 load8(const uint8_t* p)
+{
+    const uint2 t2 = __ldg(reinterpret_cast<const uint2*>(p));
+    P8 r;
+    r.lo = t2.x;
+    r.hi = t2.y;
+    return r;
+}
+
+// ====================================================== ME, per-MB warps ==
+__global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const Method m = a.m;
+    const int h = m.h, pitch = win_pitch(m.S);
+    uint8_t* win = smem + (size_t)wid * warp_smem(m.S);
+    int* slog = reinterpret_cast<int*>(win + win_bytes(m.S));
+    const unsigned long long tag = (unsigned long long)a.epoch << 32;
+    __shared__ float s_rcp[512];
+    fill_rcp(s_rcp);
+    __syncthreads();
+
+    for (;;) {
+        int t = 0;
+        if (lane == 0) {
+            t = (int)atomicAdd(&a.status->ticket, 1u);
+            if (ld_relaxed(&a.status->abort)) t = a.total;
+        }
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= a.total) break;
+        const int gid = __ldg(a.sched + t);
+        const SeqDesc* sd = a.seqs + (a.sched_seq ? __ldg(a.sched_seq + t) : 0);
+        const int W = sd->W, H = sd->H, M = sd->M, MBW = sd->MBW, rd = sd->rd;
+        const int idx = gid - sd->gid_base;
+        const int k = idx / M, mb = idx - k * M;
+        const int u = mb % MBW, v = mb / MBW;
+        const int X0 = 16 * u, Y0 = 16 * v;
+        const int x0 = X0 + 8 * (lane & 1), y = Y0 + (lane >> 1);
+        const size_t FS = (size_t)W * H;
+        const uint8_t* ref = sd->luma + (size_t)k * FS;
+        const uint8_t* cur = sd->luma + (size_t)(k + rd) * FS;
+        const int cls = __ldg(sd->cls + (size_t)(k + rd) * M + mb);
+        const P8 c8 = load8(cur + (size_t)y * W + x0);
+
+        if (cls == SME_TRANSPARENT) {
+            if (lane == 0 && gid != a.fault_ticket) st_ready(a.ready + gid, tag);
+            transparent_mb(sd, idx, k, ref, c8, lane, FS, W, y, x0);
+            continue;
         }
 
+        // ---- work that does not depend on the neighbours: prefetch ----
+        int wx0, wy0;
+        stage_window(win, ref, W, H, m.S, X0, Y0, lane, wx0, wy0);
+        float ux[8], uy[8];
+        int nx = 0, ny = 0;
+        if (cls == SME_OPAQUE) mb_factors(cur, W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny);
+        const VRange V = valid_range(W, H, m, X0, Y0);
+
+        // ---- candidates A, B, C, T (Fig. 1, Fig. 3) + optional seed ----
+        int key = 0;
+        bool failed = false;
+        if (lane < 4) {
+            int dep = -1;
+            if (lane == 0 && u > 0) dep = gid - 1;                       // A
+            if (lane == 1 && v > 0) dep = gid - MBW;                     // B
+            if (lane == 2 && v > 0 && u < MBW - 1) dep = gid - MBW + 1;  // C
+            if (lane == 3 && k > 0) dep = gid - M;                       // T
+            if (dep >= 0) {
+                unsigned val = 0;
+                if (wait_ready(a.ready + dep, a.epoch, a.status, a.timeout_ns, val)) {
+                    key = (int)val;
+                } else {
+                    failed = true;
+                    if (!ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
+                }
+            } else if (lane == 3 && sd->temporal_in) {
+                key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
+            }
+            key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
+        } else if (lane == 4 && sd->seed) {
+            key = seed_key(sd, idx, h, V);
+        }
+        if (__any_sync(kFull, failed)) break;
+        const int nc = sd->seed ? 5 : 4;
+        int cand[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) cand[c] = __shfl_sync(kFull, key, c);
+        if (lane < nc) slog[lane] = key;
+
+        const MbResult r = search_mb(m, cls, win, pitch, x0 - wx0, y - wy0, c8, ux, uy, nx, ny, V, cand, nc,
+                                     sd->packed + (size_t)(k + rd) * H * sd->Wp, sd->packed + (size_t)k * H * sd->Wp,
+                                     sd->Wp, X0, Y0, slog, lane);
+
         // ---- publish the vector first: it is on the dependency chain ----
-        if (tid == 0) {
-            a.mv[idx] = sme_mv{(int16_t)dx, (int16_t)dy};
-            if (t != a.fault_ticket) st_release(a.ready + idx, a.epoch);
-            if (a.cost) a.cost[idx] = cost;
-            if (a.disp) { a.disp[2 * idx] = lastx; a.disp[2 * idx + 1] = lasty; }
-            if (a.iters) a.iters[idx] = (uint8_t)iters;
-            if (a.out_cls) a.out_cls[idx] = (uint8_t)cls;
+        if (lane == 0) {
+            const int key_out = pack_mv(r.dx, r.dy);
+            if (gid != a.fault_ticket) st_ready(a.ready + gid, tag | (unsigned)key_out);
+            sd->mv[idx] = sme_mv{(int16_t)r.dx, (int16_t)r.dy};
         }
-        // ---- distinct evaluated positions (Table 1 unit) ----
+        finish_mb(sd, idx, k, cls, r, c8, slog, lane, FS, W, y, x0);
+    }
+}
+
+// ================================================ ME, per-pair CTAs ==
+// One CTA processes one frame pair of one sequence at a time (tickets in
+// pair order, so the previous pair -- the T candidate -- was always taken
+// earlier).  Warp w handles MB rows w, w + nw, ... left to right: the A
+// candidate is the warp's own previous vector, B and C come from the row
+// above through a ring of nw + 1 row slots in shared memory (a row's slot is
+// reused only after the row below it -- this warp's previous row -- is done),
+// and T comes from the previous pair's ready words in global memory, loaded
+// one MB ahead.  Everything else an MB reads -- the reference window, the
+// current block with a one-pixel halo, and the packed alpha rows of both
+// frames -- is fetched by TMA into the warp's other buffer while the current
+// MB is searched, so the only wait on the row's path is the row above.
+
+__host__ __device__ __forceinline__ int ceil128(int v) { return (v + 127) & ~127; }
+
+// Packed-alpha words of the reference strip: enough for every full-pel
+// shift of V plus the funnel-shift word and the 4-word alignment of the box.
+__host__ __device__ __forceinline__ int aref_words(int S) { return (((2 * S + 15) >> 5) + 6 + 3) & ~3; }
+constexpr int kCurBoxW = 48, kCurBoxH = 18;  // current block + halo: x from X0-16, y from Y0-1
+constexpr int kAcurWords = 4;                // current BAB: 16 rows x 4 words from (X0>>5)&~3
+
+struct PairLayout {
+    int o_ref, o_cur, o_aref, o_acur, buf_bytes;  // one buffer (all sections 128-byte aligned)
+    int log_off, bar_off, warp_bytes;
+    int R;                                        // row slots
+    int rows_off, prog_off, unit_off, total;
+};
+
+__host__ __device__ __forceinline__ PairLayout pair_layout(int S, int nw, int mbw_max)
+{
+    PairLayout L;
+    L.o_ref = 0;
+    L.o_cur = L.o_ref + ceil128(win_rows(S) * win_pitch(S) + 32);
+    L.o_aref = L.o_cur + ceil128(kCurBoxW * kCurBoxH + 16);
+    L.o_acur = L.o_aref + ceil128(aref_words(S) * 4 * win_rows(S));
+    L.buf_bytes = L.o_acur + ceil128(kAcurWords * 4 * 16);
+    L.log_off = 2 * L.buf_bytes;
+    L.bar_off = L.log_off + ceil16(kMaxLog * 4);
+    L.warp_bytes = ceil128(L.bar_off + 16);
+    L.R = nw + 1;
+    L.rows_off = nw * L.warp_bytes;
+    L.prog_off = L.rows_off + ceil16(L.R * mbw_max * 4);
+    L.unit_off = L.prog_off + ceil16(L.R * 4);
+    L.total = L.unit_off + 16;
+    return L;
+}
+
+__host__ __device__ __forceinline__ unsigned pair_tx_bytes(int S)
+{
+    return (unsigned)(win_rows(S) * win_pitch(S) + kCurBoxW * kCurBoxH + aref_words(S) * 4 * win_rows(S) +
+                      kAcurWords * 4 * 16);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the TMA copies that fill a buffer.
+__device__ bool mbar_wait(uint64_t* bar, unsigned parity, long long timeout_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (unsigned it = 1; it < (1u << 24); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15u) == 0 && (long long)(globaltimer() - t0) > timeout_ns) return false;
+    }
+    return false;
+}
+// 3-D tiled TMA load of one box at (x, y, z) into dst, completing on bar.
+// x * element size is a multiple of 16 bytes; x and y may be negative or run
+// past the tensor, where the box is filled with zeros.
+__device__ __forceinline__ void tma_box(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// The four tensor maps of one sequence (luma window, current block, packed
+// alpha strips of the reference and current frames).
+struct alignas(128) PairMaps {
+    CUtensorMap ref, cur, aref, acur;
+};
+
+// Issue the four boxes of MB (X0, Y0) of pair k into buffer `buf`.
+__device__ __forceinline__ void issue_mb_boxes(uint8_t* buf, const PairLayout& L, const PairMaps* mp, int S, int X0,
+                                               int Y0, int k, int kc, uint64_t* bar, unsigned tx)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(tx) : "memory");
+    tma_box(buf + L.o_ref, &mp->ref, X0 - ceil16(S), Y0 - S, k, bar);
+    tma_box(buf + L.o_cur, &mp->cur, X0 - 16, Y0 - 1, kc, bar);
+    tma_box(buf + L.o_aref, &mp->aref, ((X0 - S) >> 5) & ~3, Y0 - S, k, bar);
+    tma_box(buf + L.o_acur, &mp->acur, (X0 >> 5) & ~3, Y0, kc, bar);
+}
+
+__device__ __forceinline__ int ld_acquire_cta(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(int* p, int v)
+{
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+// Bounded wait until the row slot's progress word reaches `target`.
+__device__ bool wait_progress(const int* prog, int target, const DevStatus* st, long long timeout_ns)
+{
+    if (ld_acquire_cta(prog) >= target) return true;
+    const unsigned long long t0 = globaltimer();
+    for (unsigned it = 1; it < (1u << 26); ++it) {
+        if (ld_acquire_cta(prog) >= target) return true;
+        if ((it & 63u) == 0) {
+            if (ld_relaxed(&st->abort)) return false;
+            if ((long long)(globaltimer() - t0) > timeout_ns) return false;
+        }
+    }
+    return false;
+}
+
+// Shape costs from the staged packed-alpha strips (same arithmetic as
+// shape_costs): lane l takes row l&15 of candidates (l>>4) + 2j.
+__device__ __forceinline__ void shape_costs_smem(const uint32_t* acur, const uint32_t* aref, int arw, int S, int X0,
+                                                 const int (&cand)[5], int nc, int h, int lane, unsigned (&cost)[5])
+{
+    const int r = lane & 15, half = lane >> 4;
+    const unsigned cb = (acur[r * kAcurWords + (X0 >> 5) - ((X0 >> 5) & ~3)] >> (X0 & 31)) & 0xffffu;
+    const int xw0 = ((X0 - S) >> 5) & ~3;
+    unsigned s[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int c = half + 2 * j;
+        if (c < nc) {
+            int key = cand[0];
+#pragma unroll
+            for (int q = 1; q < 5; ++q)
+                if (q == c) key = cand[q];
+            const int fdx = mv_x(key) / h, fdy = mv_y(key) / h;  // trunc toward zero
+            const int xr = X0 + fdx, wr = (xr >> 5) - xw0;
+            const uint32_t* row = aref + (r + fdy + S) * arw;
+            const unsigned rb = __funnelshift_r(row[wr], row[wr + 1], xr & 31) & 0xffffu;
+            s[j] = __popc(cb ^ rb);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        s[j] += __shfl_xor_sync(kFull, s[j], 8);
+        s[j] += __shfl_xor_sync(kFull, s[j], 4);
+        s[j] += __shfl_xor_sync(kFull, s[j], 2);
+        s[j] += __shfl_xor_sync(kFull, s[j], 1);
+    }
+    cost[0] = __shfl_sync(kFull, s[0], 0);
+    cost[1] = __shfl_sync(kFull, s[0], 16);
+    cost[2] = __shfl_sync(kFull, s[1], 0);
+    cost[3] = __shfl_sync(kFull, s[1], 16);
+    cost[4] = __shfl_sync(kFull, s[2], 0);
+}
+
+// Eq. 4 factors from the staged current block (box row 1 + (lane>>1), box
+// column 16 + 8*(lane&1) is the lane's first pixel).
+__device__ __forceinline__ void factors_smem(const uint8_t* cb, int W, int H, int x0, int y, const P8& c,
+                                             float theta, const float* rcp, float (&ux)[8], float (&uy)[8],
+                                             int& nx, int& ny, int lane)
+{
+    const float lim = 2.0f * theta;
+    const uint8_t* row = cb + (1 + (lane >> 1)) * kCurBoxW + 16 + 8 * (lane & 1);
+    const int left = row[-1], right = row[8];
+    P8 up, dn;
+    {
+        const uint2 t = *reinterpret_cast<const uint2*>(row - kCurBoxW);
+        up.lo = t.x;
+        up.hi = t.y;
+        const uint2 b = *reinterpret_cast<const uint2*>(row + kCurBoxW);
+        dn.lo = b.x;
+        dn.hi = b.y;
+    }
+    int cx = 0, cy = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int x = x0 + k;
+        ux[k] = 0.0f;
+        uy[k] = 0.0f;
+        if (x > 0 && x < W - 1) {
+            const int rr = k < 7 ? byte_of(c, k + 1) : right;
+            const int ll = k > 0 ? byte_of(c, k - 1) : left;
+            const int g = rr - ll;
+            if (fabsf((float)g) >= lim) ux[k] = rcp[g + 255];
+        }
+        if (y > 0 && y < H - 1) {
+            const int g = byte_of(dn, k) - byte_of(up, k);
+            if (fabsf((float)g) >= lim) uy[k] = rcp[g + 255];
+        }
+        cx += ux[k] != 0.0f;
+        cy += uy[k] != 0.0f;
+    }
+    nx = (int)__reduce_add_sync(kFull, (unsigned)cx);
+    ny = (int)__reduce_add_sync(kFull, (unsigned)cy);
+}
+
+__global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArgs a, const __grid_constant__ PairMaps maps0)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const Method m = a.m;
+    const int h = m.h, S = m.S, cs = ceil16(S), pitch = win_pitch(S), arw = aref_words(S);
+    const unsigned tx = pair_tx_bytes(S);
+    const PairLayout L = pair_layout(S, nw, a.mbw_max);
+    uint8_t* wbase = smem + (size_t)wid * L.warp_bytes;
+    int* slog = reinterpret_cast<int*>(wbase + L.log_off);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + L.bar_off);
+    int* rowmv = reinterpret_cast<int*>(smem + L.rows_off);
+    int* prog = reinterpret_cast<int*>(smem + L.prog_off);
+    int* s_unit = reinterpret_cast<int*>(smem + L.unit_off);
+    const unsigned long long tag = (unsigned long long)a.epoch << 32;
+    const int lx = cs + 8 * (lane & 1), ly = S + (lane >> 1);  // lane's first pixel in the window
+
+    __shared__ float s_rcp[512];
+    fill_rcp(s_rcp);
+    if (lane == 0) {
+        mbar_init(&bars[0]);
+        mbar_init(&bars[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned parity = 0;   // bit b: parity of the next completion of buffer b
+    unsigned pending = 0;  // bit b: copies into buffer b are in flight
+    int cur = 0;           // buffer of the MB being processed
+    bool failed = false;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int t = (int)atomicAdd(&a.status->ticket, 1u);
+            if (ld_relaxed(&a.status->abort)) t = a.total_units;
+            *s_unit = t;
+        }
+        for (int i = threadIdx.x; i < L.R; i += blockDim.x) prog[i] = -1;
         __syncthreads();
-        int first = 0;
-        if (tid < nlog) {
-            const int key = s_log[tid];
-            first = 1;
-            for (int j = 0; j < tid; ++j)
-                if (s_log[j] == key) { first = 0; break; }
-        }
-        const int np = __syncthreads_count(first);
-        if (tid == 0 && a.npos) a.npos[idx] = (uint8_t)np;
-        // ---- Sec. 4: motion-compensated prediction and its SSE ----
-        if (a.pred) a.pred[(size_t)k * FS + (size_t)y * g.W + x] = (uint8_t)(cval + diff);
-        if (a.sse || a.sse_mb) {
-            unsigned sq[1] = {(unsigned)(diff * diff)};
-            block_sum<1>(sq, s_red[rb], lane, warp);
-            rb ^= 1;
-            if (tid == 0) {
-                if (a.sse) atomicAdd(a.sse + k, (unsigned long long)sq[0]);
-                if (a.sse_mb) a.sse_mb[idx] = sq[0];
+        const int unit = *s_unit;
+        if (unit >= a.total_units) break;  // uniform: a failure raised the abort word
+        const int sid = a.unit_seq ? __ldg(a.unit_seq + unit) : 0;
+        const int k = a.unit_pair ? __ldg(a.unit_pair + unit) : unit;
+        const SeqDesc* sd = a.seqs + sid;
+        const PairMaps* mp = a.tmaps ? reinterpret_cast<const PairMaps*>(a.tmaps) + sid : &maps0;
+        const int W = sd->W, H = sd->H, M = sd->M, MBW = sd->MBW, MBH = sd->MBH, rd = sd->rd;
+        const size_t FS = (size_t)W * H;
+        const int base = sd->gid_base + k * M;
+
+        for (int v = wid; v < MBH && !failed; v += nw) {
+            const int slot = v % L.R, pslot = (v + L.R - 1) % L.R;
+            const int Y0 = 16 * v, y = Y0 + (lane >> 1);
+            int akey = 0;  // A: this row's previous vector
+            if (lane == 0) issue_mb_boxes(wbase + cur * L.buf_bytes, L, mp, S, 0, Y0, k, k + rd, &bars[cur], tx);
+            pending |= 1u << cur;
+            unsigned long long tnext = 0;
+            if (lane == 3 && k > 0) tnext = ld_ready(a.ready + base + v * MBW - M);
+            for (int u = 0; u < MBW; ++u) {
+                const int mb = v * MBW + u, idx = k * M + mb, gid = base + mb;
+                const int X0 = 16 * u, x0 = X0 + 8 * (lane & 1);
+                const int nb = cur ^ 1;
+                if (u + 1 < MBW) {
+                    if (lane == 0)
+                        issue_mb_boxes(wbase + nb * L.buf_bytes, L, mp, S, X0 + 16, Y0, k, k + rd, &bars[nb], tx);
+                    pending |= 1u << nb;
+                }
+                const unsigned long long tcur = tnext;
+                if (lane == 3 && k > 0 && u + 1 < MBW) tnext = ld_ready(a.ready + gid + 1 - M);
+
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait(&bars[cur], (parity >> cur) & 1u, a.timeout_ns);
+                ok = __shfl_sync(kFull, ok, 0);
+                parity ^= 1u << cur;
+                pending &= ~(1u << cur);
+                if (!ok) {
+                    if (lane == 0) raise_error(a.status, SME_ERR_TIMEOUT, true);
+                    failed = true;
+                    break;
+                }
+                const uint8_t* buf = wbase + cur * L.buf_bytes;
+                const uint8_t* win = buf + L.o_ref;
+                const uint32_t* acur = reinterpret_cast<const uint32_t*>(buf + L.o_acur);
+                // Fig. 1 Block_Type from the current BAB (16 rows of 16 bits).
+                unsigned ones = 0;
+                if (lane < 16) ones = __popc((acur[lane * kAcurWords + (X0 >> 5) - ((X0 >> 5) & ~3)] >> (X0 & 31)) & 0xffffu);
+                ones = __reduce_add_sync(kFull, ones);
+                const int cls = ones == 0 ? SME_TRANSPARENT : (ones == 256 ? SME_OPAQUE : SME_BOUNDARY);
+                P8 c8;
+                {
+                    const uint2 t2 = *reinterpret_cast<const uint2*>(buf + L.o_cur + (1 + (lane >> 1)) * kCurBoxW + 16 +
+                                                                     8 * (lane & 1));
+                    c8.lo = t2.x;
+                    c8.hi = t2.y;
+                }
+
+                if (cls == SME_TRANSPARENT) {
+                    // Fig. 1: (0,0) is final at once.
+                    if (lane == 0) {
+                        rowmv[slot * a.mbw_max + u] = 0;
+                        st_release_cta(&prog[slot], v * 1024 + u + 1);
+                        if (gid != a.fault_ticket) st_ready(a.ready + gid, tag);
+                        sd->mv[idx] = sme_mv{0, 0};
+                    }
+                    akey = 0;
+                    MbResult r;
+                    r.dx = r.dy = r.iters = r.nlog = 0;
+                    r.cost = 0;
+                    r.lastx = r.lasty = 0.0f;
+                    r.r8 = ref8(win, pitch, lx, ly, 0, 0, h);
+                    finish_mb(sd, idx, k, cls, r, c8, slog, lane, FS, W, y, x0);
+                } else {
+                    float ux[8], uy[8];
+                    int nx = 0, ny = 0;
+                    if (cls == SME_OPAQUE)
+                        factors_smem(buf + L.o_cur, W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny, lane);
+                    const VRange V = valid_range(W, H, m, X0, Y0);
+                    // ---- candidates A, B, C, T (Fig. 1, Fig. 3) + optional seed ----
+                    if (v > 0 && lane == 0)
+                        ok = wait_progress(&prog[pslot], (v - 1) * 1024 + min(u + 2, MBW), a.status, a.timeout_ns);
+                    int key = 0;
+                    if (lane == 3) {
+                        if (k > 0) {
+                            unsigned val = (unsigned)tcur;
+                            if ((unsigned)(tcur >> 32) != a.epoch)
+                                ok = wait_ready(a.ready + gid - M, a.epoch, a.status, a.timeout_ns, val);
+                            key = (int)val;
+                        } else if (sd->temporal_in) {
+                            key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
+                        }
+                    }
+                    if (__any_sync(kFull, !ok)) {
+                        if (lane == 0 && !ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
+                        failed = true;
+                        break;
+                    }
+                    __syncwarp();  // lane 0's acquire of the row above orders the reads below
+                    if (lane == 0) key = akey;
+                    if (lane == 1 && v > 0) key = rowmv[pslot * a.mbw_max + u];
+                    if (lane == 2 && v > 0 && u + 1 < MBW) key = rowmv[pslot * a.mbw_max + u + 1];
+                    if (lane < 4) key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
+                    if (lane == 4 && sd->seed) key = seed_key(sd, idx, h, V);
+                    const int nc = sd->seed ? 5 : 4;
+                    int cand[5];
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) cand[c] = __shfl_sync(kFull, key, c);
+                    if (lane < nc) slog[lane] = key;
+                    MbResult r;
+                    if (cls == SME_BOUNDARY) {
+                        unsigned sc[5];
+                        shape_costs_smem(acur, reinterpret_cast<const uint32_t*>(buf + L.o_aref), arw, S, X0, cand, nc,
+                                         h, lane, sc);
+                        int best = cand[0];
+                        unsigned cost = sc[0];
+#pragma unroll
+                        for (int c = 1; c < 5; ++c)
+                            if (c < nc && sc[c] < cost) {
+                                cost = sc[c];
+                                best = cand[c];
+                            }
+                        r.dx = mv_x(best);
+                        r.dy = mv_y(best);
+                        r.cost = cost;
+                        r.iters = 0;
+                        r.nlog = nc;
+                        r.lastx = r.lasty = 0.0f;
+                        r.r8 = ref8(win, pitch, lx, ly, r.dx, r.dy, h);
+                    } else {
+                        r = search_mb(m, cls, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, nc, nullptr, nullptr, 0,
+                                      X0, Y0, slog, lane);
+                    }
+                    // ---- publish: row slot for the row below, ready word for the next pair ----
+                    const int key_out = pack_mv(r.dx, r.dy);
+                    if (lane == 0) {
+                        rowmv[slot * a.mbw_max + u] = key_out;
+                        st_release_cta(&prog[slot], v * 1024 + u + 1);
+                        if (gid != a.fault_ticket) st_ready(a.ready + gid, tag | (unsigned)key_out);
+                        sd->mv[idx] = sme_mv{(int16_t)r.dx, (int16_t)r.dy};
+                    }
+                    akey = key_out;
+                    finish_mb(sd, idx, k, cls, r, c8, slog, lane, FS, W, y, x0);
+                }
+                cur = nb;
+            }
+            // A failing warp drains its own copies in flight before the CTA moves on.
+            if (failed) {
+                for (int b = 0; b < 2; ++b)
+                    if (pending & (1u << b)) {
+                        if (lane == 0) mbar_wait(&bars[b], (parity >> b) & 1u, a.timeout_ns);
+                        __syncwarp();
+                        parity ^= 1u << b;
+                    }
+                pending = 0;
             }
         }
         __syncthreads();
@@ -522,22 +1382,27 @@ __global__ void __launch_bounds__(kThreads) me_kernel(const Geom g, const MeArgs
 }
 
 // ========================================================== compensate ==
-__global__ void __launch_bounds__(kThreads) compensate_kernel(const Geom g, const CompArgs a)
+__global__ void __launch_bounds__(256) compensate_kernel(const Geom g, const Method mth, const CompArgs a)
 {
-    __shared__ unsigned s_red[1][8];
+    __shared__ unsigned s_red[8];
     const int mb = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int u = mb % g.MBW, v = mb / g.MBW, X0 = 16 * u, Y0 = 16 * v;
     const int x = X0 + (tid & 15), y = Y0 + (tid >> 4);
     const unsigned raw = __ldg(reinterpret_cast<const unsigned*>(a.mv + mb));
     const int dx = mv_x((int)raw), dy = mv_y((int)raw);
-    const VRange V = valid_range(g, X0, Y0);
+    const VRange V = valid_range(g.W, g.H, mth, X0, Y0);
     if (dx < V.lox || dx > V.hix || dy < V.loy || dy > V.hiy) {
         if (tid == 0) raise_error(a.status, SME_ERR_RANGE, false);
         return;
     }
-    // Same interpolation as ref_at, read straight from global memory.
+    // One pixel per thread, read straight from global memory.
     int ix = dx, iy = dy, fx = 0, fy = 0;
-    if (g.h == 2) { ix = dx >> 1; iy = dy >> 1; fx = dx & 1; fy = dy & 1; }
+    if (mth.h == 2) {
+        ix = dx >> 1;
+        iy = dy >> 1;
+        fx = dx & 1;
+        fy = dy & 1;
+    }
     const uint8_t* r = a.ref + (size_t)(y + iy) * g.W + (x + ix);
     int p = __ldg(r);
     if (fx && fy) p = (p + __ldg(r + 1) + __ldg(r + g.W) + __ldg(r + g.W + 1) + 2) >> 2;
@@ -545,111 +1410,180 @@ __global__ void __launch_bounds__(kThreads) compensate_kernel(const Geom g, cons
     else if (fy) p = (p + __ldg(r + g.W) + 1) >> 1;
     const int e = (int)__ldg(a.cur + (size_t)y * g.W + x) - p;
     if (a.pred) a.pred[(size_t)y * g.W + x] = (uint8_t)p;
-    unsigned sq[1] = {(unsigned)(e * e)};
-    block_sum<1>(sq, s_red, lane, warp);
-    if (tid == 0) atomicAdd(a.sse, (unsigned long long)sq[0]);
+    const unsigned s = __reduce_add_sync(kFull, (unsigned)(e * e));
+    if (lane == 0) s_red[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long tot = 0;
+        for (int w = 0; w < 8; ++w) tot += s_red[w];
+        atomicAdd(a.sse, tot);
+    }
 }
 
 // ============================================================= queries ==
-__global__ void __launch_bounds__(kThreads) query_kernel(const Geom g, const QueryArgs a)
+// One warp per (MB, d) query, through the ME kernel's device functions.
+constexpr int kQueryWarps = 4;
+
+__global__ void __launch_bounds__(32 * kQueryWarps) query_kernel(const Geom g, const Method m, const QueryArgs a)
 {
-    extern __shared__ __align__(16) uint8_t win[];
-    __shared__ unsigned s_red[1][16][8];
-    __shared__ float s_fred[2][8];
-    __shared__ unsigned s_shape;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int qi = blockIdx.x;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int qi = blockIdx.x * kQueryWarps + wid;
+    __shared__ float s_rcp[512];
+    fill_rcp(s_rcp);
+    __syncthreads();
+    if (qi >= a.n) return;
+    uint8_t* win = smem + (size_t)wid * warp_smem(m.S);
     const int mb = __ldg(a.q + 3 * qi), dx = __ldg(a.q + 3 * qi + 1), dy = __ldg(a.q + 3 * qi + 2);
     if (mb < 0 || mb >= g.M) {
-        if (tid == 0) raise_error(a.status, SME_ERR_ARG, false);
+        if (lane == 0) raise_error(a.status, SME_ERR_ARG, false);
         return;
     }
     const int u = mb % g.MBW, v = mb / g.MBW, X0 = 16 * u, Y0 = 16 * v;
-    const VRange V = valid_range(g, X0, Y0);
+    const VRange V = valid_range(g.W, g.H, m, X0, Y0);
     if (dx < V.lox || dx > V.hix || dy < V.loy || dy > V.hiy) {
-        if (tid == 0) raise_error(a.status, SME_ERR_RANGE, false);
+        if (lane == 0) raise_error(a.status, SME_ERR_RANGE, false);
         return;
     }
-    const int x = X0 + (tid & 15), y = Y0 + (tid >> 4);
+    const int x0 = X0 + 8 * (lane & 1), y = Y0 + (lane >> 1);
     int wx0, wy0;
-    stage_window(win, a.ref, g, X0, Y0, tid, wx0, wy0);
-    float ux, uy;
-    grad_factors(a.cur, g, x, y, ux, uy);
-    const int nx = __syncthreads_count(ux != 0.0f);
-    const int ny = __syncthreads_count(uy != 0.0f);
-    const int cval = __ldg(a.cur + (size_t)y * g.W + x);
-    const int diff = ref_at(win, win_pitch(g), x - wx0, y - wy0, dx, dy, g.h) - cval;
-    unsigned sad[1] = {(unsigned)abs(diff)};
-    block_sum<1>(sad, s_red[0], lane, warp);
-    float sx = __fmul_rn((float)diff, ux), sy = __fmul_rn((float)diff, uy);
-    tree_sum2(sx, sy, s_fred, lane, warp);
-    if (a.pcur && a.pref) {
-        unsigned part = 0;
-        if (tid < 16) part = shape_row(a.pcur, a.pref, g, X0, Y0, tid, dx / g.h, dy / g.h);
-        part += __shfl_xor_sync(kFull, part, 8);
-        part += __shfl_xor_sync(kFull, part, 4);
-        part += __shfl_xor_sync(kFull, part, 2);
-        part += __shfl_xor_sync(kFull, part, 1);
-        if (tid == 0) s_shape = part;
-        __syncthreads();
+    stage_window(win, a.ref, g.W, g.H, m.S, X0, Y0, lane, wx0, wy0);
+    P8 c8;
+    const uint2 t2 = __ldg(reinterpret_cast<const uint2*>(a.cur + (size_t)y * g.W + x0));
+    c8.lo = t2.x;
+    c8.hi = t2.y;
+    const P8 r8 = ref8(win, win_pitch(m.S), x0 - wx0, y - wy0, dx, dy, m.h);
+    const unsigned sad = __reduce_add_sync(kFull, sad8(r8, c8));
+    float ux[8], uy[8];
+    grad_factors8(a.cur, g.W, g.H, x0, y, c8, m.theta, s_rcp, ux, uy);
+    int cx = 0, cy = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        cx += ux[q] != 0.0f;
+        cy += uy[q] != 0.0f;
     }
-    if (tid == 0) {
-        if (a.tsad) a.tsad[qi] = sad[0];
-        if (a.ssad && a.pcur) a.ssad[qi] = s_shape;
+    const int nx = (int)__reduce_add_sync(kFull, (unsigned)cx);
+    const int ny = (int)__reduce_add_sync(kFull, (unsigned)cy);
+    float sx, sy;
+    grad_sums(r8, c8, ux, uy, sx, sy);
+    unsigned shp = 0;
+    if (a.pcur && a.pref) {
+        int cand[5] = {pack_mv(dx, dy), 0, 0, 0, 0};
+        unsigned sc[5];
+        shape_costs(a.pcur, a.pref, g.Wp, X0, Y0, cand, 1, m.h, lane, sc);
+        shp = sc[0];
+    }
+    if (lane == 0) {
+        if (a.tsad) a.tsad[qi] = sad;
+        if (a.ssad && a.pcur) a.ssad[qi] = shp;
         if (a.delta) {
-            a.delta[2 * qi] = update_of(sx, nx, g.eps);
-            a.delta[2 * qi + 1] = update_of(sy, ny, g.eps);
+            a.delta[2 * qi] = update_of(sx, nx, m.eps);
+            a.delta[2 * qi + 1] = update_of(sy, ny, m.eps);
         }
     }
 }
 
 }  // namespace
 
-size_t me_smem_bytes(const Geom& g)
-{
-    const int cs = (g.S + 15) & ~15;
-    return (size_t)(16 + 2 * g.S) * (size_t)(16 + 2 * cs);
-}
+size_t me_smem_bytes(int S) { return (size_t)kMeWarps * warp_smem(S); }
 
 cudaError_t launch_classify(const Geom& g, const ClassifyArgs& a, cudaStream_t s)
 {
     dim3 grid(g.MBH, a.n_frames);
-    classify_pack_kernel<<<grid, kThreads, 0, s>>>(g, a);
+    classify_pack_kernel<<<grid, 256, 0, s>>>(g, a);
     return cudaGetLastError();
 }
 
-cudaError_t me_occupancy(const Geom& g, int* blocks_per_sm)
+cudaError_t me_occupancy(int S, int* blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, me_kernel, kThreads, me_smem_bytes(g));
+    const size_t smem = me_smem_bytes(S);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(me_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, me_kernel, 32 * kMeWarps, smem);
 }
 
-cudaError_t launch_me(const Geom& g, const MeArgs& a, int grid, cudaStream_t s)
+cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s)
 {
-    // Blocks wait on results of other blocks of the same launch, so the
-    // launch is cooperative: every block is resident at once.
+    // Warps wait on results of other warps of the same launch, so the launch
+    // is cooperative: every block is resident at once.
+    const size_t smem = me_smem_bytes(m.S);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(me_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = me_smem_bytes(g);
+    cfg.blockDim = dim3(32 * kMeWarps);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, me_kernel, g, a);
+    return cudaLaunchKernelEx(&cfg, me_kernel, a);
 }
 
-cudaError_t launch_compensate(const Geom& g, const CompArgs& a, cudaStream_t s)
+void pair_boxes(int S, unsigned (&box)[4][2])
 {
-    compensate_kernel<<<g.M, kThreads, 0, s>>>(g, a);
+    box[0][0] = (unsigned)win_pitch(S);
+    box[0][1] = (unsigned)win_rows(S);
+    box[1][0] = kCurBoxW;
+    box[1][1] = kCurBoxH;
+    box[2][0] = (unsigned)aref_words(S);
+    box[2][1] = (unsigned)win_rows(S);
+    box[3][0] = kAcurWords;
+    box[3][1] = 16;
+}
+
+size_t me_pair_smem_bytes(int S, int nwarps, int mbw_max)
+{
+    return (size_t)pair_layout(S, nwarps, mbw_max).total + 128;  // + alignment slack
+}
+
+cudaError_t me_pair_occupancy(int S, int nwarps, int mbw_max, int* blocks_per_sm)
+{
+    const size_t smem = me_pair_smem_bytes(S, nwarps, mbw_max);
+    cudaError_t e = cudaFuncSetAttribute(me_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, me_pair_kernel, 32 * nwarps, smem);
+}
+
+cudaError_t launch_me_pair(const Method& m, const MeArgs& a, const void* maps, int nwarps, int grid, cudaStream_t s)
+{
+    const size_t smem = me_pair_smem_bytes(m.S, nwarps, a.mbw_max);
+    cudaError_t e = cudaFuncSetAttribute(me_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * nwarps);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, me_pair_kernel, a, *reinterpret_cast<const PairMaps*>(maps));
+}
+
+cudaError_t launch_compensate(const Geom& g, const Method& m, const CompArgs& a, cudaStream_t s)
+{
+    compensate_kernel<<<g.M, 256, 0, s>>>(g, m, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_queries(const Geom& g, const QueryArgs& a, cudaStream_t s)
+cudaError_t launch_queries(const Geom& g, const Method& m, const QueryArgs& a, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
-    query_kernel<<<a.n, kThreads, me_smem_bytes(g), s>>>(g, a);
+    const size_t smem = (size_t)kQueryWarps * warp_smem(m.S);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    query_kernel<<<(a.n + kQueryWarps - 1) / kQueryWarps, 32 * kQueryWarps, smem, s>>>(g, m, a);
     return cudaGetLastError();
 }
 

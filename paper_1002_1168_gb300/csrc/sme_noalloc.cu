@@ -134,22 +134,24 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
     g.MBW = p->width / 16;
     g.MBH = p->height / 16;
     g.M = g.MBW * g.MBH;
-    g.Wp = (p->width + 31) / 32 + 1;
-    g.S = p->search_range;
-    g.h = p->subpel;
-    g.K = p->max_iters;
-    g.theta = p->theta;
-    g.eps = p->epsilon;
+    g.Wp = (((p->width + 31) / 32 + 1) + 3) & ~3;
+    Method mth;
+    mth.S = p->search_range;
+    mth.h = p->subpel;
+    mth.K = p->max_iters;
+    mth.theta = p->theta;
+    mth.eps = p->epsilon;
     const int F = n_frames, P = n_frames - rd;
     const int T = (g.MBW - 1) + 2 * (g.MBH - 1) + P;  // wavefront steps
     const size_t PM = (size_t)P * g.M;
 
     // Layout of the fixed scratch; anything larger is rejected.
     const size_t o_status = 0;
-    const size_t o_packed = o_status + round256(sizeof(DevStatus));
+    const size_t o_desc = o_status + round256(sizeof(DevStatus));
+    const size_t o_packed = o_desc + round256(sizeof(SeqDesc));
     const size_t o_cls = o_packed + round256((size_t)F * g.H * g.Wp * sizeof(uint32_t));
     const size_t o_ready = o_cls + round256((size_t)F * g.M);
-    const size_t o_sched = o_ready + round256(PM * sizeof(unsigned));
+    const size_t o_sched = o_ready + round256(PM * sizeof(unsigned long long));
     const size_t o_offs = o_sched + round256(PM * sizeof(int));
     const size_t need = o_offs + round256(((size_t)T + 1) * sizeof(int));
     if (need > kScratchBytes) return SME_ERR_SCRATCH;
@@ -159,23 +161,49 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
     void* base = nullptr;
     if ((rc = setup(dev, &base, &sms))) return rc;
     int per_sm = 0;
-    if (me_occupancy(g, &per_sm) != cudaSuccess || per_sm < 1) return SME_ERR_CUDA;
+    if (me_occupancy(mth.S, &per_sm) != cudaSuccess || per_sm < 1) return SME_ERR_CUDA;
 
     unsigned char* s = (unsigned char*)base;
     DevStatus* status = (DevStatus*)(s + o_status);
+    SeqDesc* desc = (SeqDesc*)(s + o_desc);
     uint32_t* packed = (uint32_t*)(s + o_packed);
     uint8_t* cls = s + o_cls;
-    unsigned* ready = (unsigned*)(s + o_ready);
+    unsigned long long* ready = (unsigned long long*)(s + o_ready);
     int* sched = (int*)(s + o_sched);
     int* offs = (int*)(s + o_offs);
     const cudaStream_t st = (cudaStream_t)cuda_stream;
 
     // Clear what must start at zero: status words and ready stamps.
     if (cudaMemsetAsync(status, 0, sizeof(DevStatus), st) != cudaSuccess ||
-        cudaMemsetAsync(ready, 0, PM * sizeof(unsigned), st) != cudaSuccess)
+        cudaMemsetAsync(ready, 0, PM * sizeof(unsigned long long), st) != cudaSuccess)
         return SME_ERR_CUDA;
     noalloc_schedule_kernel<<<1, 256, 0, st>>>(g, P, T, offs, sched);
     if (cudaGetLastError() != cudaSuccess) return SME_ERR_CUDA;
+
+    SeqDesc d{};
+    d.luma = luma;
+    d.packed = packed;
+    d.cls = cls;
+    d.temporal_in = temporal_in;
+    d.seed = seed;
+    d.mv = out->mv;
+    d.cost = out->cost;
+    d.disp = out->disp;
+    d.iters = out->iters;
+    d.npos = out->npos;
+    d.out_cls = out->mb_class;
+    d.sse_mb = out->sse_mb;
+    d.sse = out->sse;
+    d.pred = out->pred;
+    d.W = g.W;
+    d.H = g.H;
+    d.MBW = g.MBW;
+    d.MBH = g.MBH;
+    d.M = g.M;
+    d.Wp = g.Wp;
+    d.P = P;
+    d.rd = rd;
+    d.gid_base = 0;
 
     ClassifyArgs ca{};
     ca.alpha = alpha;
@@ -185,35 +213,25 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
     ca.status = status;
     ca.sse = out->sse;
     ca.n_sse = P;
+    ca.desc_out = desc;
+    ca.desc = d;
     if (launch_classify(g, ca, st) != cudaSuccess) return SME_ERR_CUDA;
 
     MeArgs a{};
-    a.luma = luma;
-    a.packed = packed;
-    a.cls = cls;
-    a.temporal_in = temporal_in;
-    a.seed = seed;
-    a.mv = out->mv;
-    a.cost = out->cost;
-    a.disp = out->disp;
-    a.iters = out->iters;
-    a.npos = out->npos;
-    a.out_cls = out->mb_class;
-    a.sse_mb = out->sse_mb;
-    a.sse = out->sse;
-    a.pred = out->pred;
+    a.seqs = desc;
     a.sched = sched;
+    a.sched_seq = nullptr;
     a.ready = ready;
     a.status = status;
+    a.m = mth;
     a.epoch = 1;
-    a.P = P;
-    a.rd = rd;
     a.total = (int)PM;
     a.fault_ticket = -1;
     a.timeout_ns = kDefaultTimeoutNs;
     const long long cap = (long long)sms * per_sm;
-    const int grid = (int)(cap < (long long)PM ? cap : (long long)PM);
-    if (launch_me(g, a, grid, st) != cudaSuccess) return SME_ERR_CUDA;
+    const long long want = ((long long)PM + kMeWarps - 1) / kMeWarps;
+    const int grid = (int)(cap < want ? cap : want);
+    if (launch_me(mth, a, grid, st) != cudaSuccess) return SME_ERR_CUDA;
 
     // Report a device-side failure of this call (synchronises the stream).
     int err = 0;

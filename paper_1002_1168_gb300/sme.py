@@ -16,6 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsme.so")
 
 SME_TRANSPARENT, SME_OPAQUE, SME_BOUNDARY = 0, 1, 2
+SME_OPT_SCHEDULE, SME_OPT_PAIR_WARPS = 1, 2
+SCHEDULES = {"auto": 0, "mb": 1, "pair": 2}
 STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4: "SME_ERR_TIMEOUT",
           5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE", 8: "SME_ERR_SCRATCH"}
 
@@ -26,7 +28,7 @@ EXPORTS = [
     "sme_estimate_sequence_host", "sme_set_reference", "sme_set_current", "sme_estimate",
     "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field",
     "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
-    "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_debug_set_fault",
+    "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_debug_set_fault",
 ]
 
 
@@ -89,6 +91,7 @@ def _lib():
             "sme_profile_begin": (i, [vp, i]),
             "sme_profile_end": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "sme_estimate_sequence_noalloc": (i, [C.POINTER(Params), vp, vp, i, vp, vp, C.POINTER(Outputs), vp]),
+            "sme_set_option": (i, [vp, i, i]),
             "sme_debug_set_fault": (i, [vp, i, C.c_longlong]),
         }
         for name, (res, args) in sig.items():
@@ -274,6 +277,14 @@ class Estimator:
 
     def set_temporal_field(self, field):
         _check(_lib().sme_set_temporal_field(self._bind(), _ptr(field)), "sme_set_temporal_field")
+
+    def set_option(self, option, value):
+        _check(_lib().sme_set_option(self._h, int(option), int(value)), "sme_set_option")
+
+    def set_schedule(self, name, pair_warps=0):
+        """'auto', 'mb' (one warp per MB) or 'pair' (one CTA per frame pair)."""
+        self.set_option(SME_OPT_SCHEDULE, SCHEDULES[name])
+        self.set_option(SME_OPT_PAIR_WARPS, pair_warps)
 
     def profile_begin(self, max_calls):
         _check(_lib().sme_profile_begin(self._h, int(max_calls)), "sme_profile_begin")

@@ -44,7 +44,7 @@ def test_host_only_helpers(lib):
     assert lib.sme_psnr(0, 64, 64) == math.inf
     assert lib.sme_psnr(64 * 64, 64, 64) == pytest.approx(20 * math.log10(255.0), abs=1e-12)
     assert lib.sme_strerror(4).decode().startswith("a bounded device wait")
-    assert lib.sme_packed_words(176) == 7 and lib.sme_packed_words(352) == 12
+    assert lib.sme_packed_words(176) == 8 and lib.sme_packed_words(352) == 12 and lib.sme_packed_words(368) == 16
     p = sme.Params()
     lib.sme_default_params(C.byref(p), 352, 288)
     assert (p.search_range, p.subpel, p.theta, p.epsilon, p.max_iters, p.ref_distance) == (16, 1, 2.0, 1.0, 8, 1)

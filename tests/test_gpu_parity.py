@@ -30,11 +30,15 @@ def cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+SCHEDULES = ["pair", "mb"]
+
+
 def run_both(sme, luma, alpha, S=16, h=1, K=8, theta=2.0, eps=1.0, rd=1, temporal=None, seed=None,
-             want_pred=True):
+             want_pred=True, schedule="pair"):
     F, H, W = luma.shape
     est = sme.Estimator(W, H, search_range=S, subpel=h, theta=theta, epsilon=eps, max_iters=K,
                         ref_distance=rd)
+    est.set_schedule(schedule)
     want = ("cost", "disp", "iters", "npos", "mb_class", "sse_mb", "sse") + (("pred",) if want_pred else ())
     g = est.estimate_sequence(cuda(luma), cuda(alpha),
                               temporal_in=None if temporal is None else cuda(temporal.astype(np.int16)),
@@ -133,9 +137,10 @@ def test_gradient_step_bitwise(sme, h):
 
 
 # ------------------------------------------------------- whole sequences --
-def test_qcif_pair_fullpel(sme):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_qcif_pair_fullpel(sme, schedule):
     seq = synth.qcif_pair(seed=1001)
-    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=16, h=1)
+    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=16, h=1, schedule=schedule)
     assert_parity(g, o, p, seq.luma)
 
 
@@ -146,19 +151,21 @@ def test_qcif_pairs_various_shifts(sme, seed):
     assert_parity(g, o, p, seq.luma)
 
 
-def test_cif_30_frames_halfpel_full_size(sme):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_cif_30_frames_halfpel_full_size(sme, schedule):
     """The CIF 352x288, 30-frame, half-pel workload the benchmark times,
     compared on every MB of every pair."""
     seq = synth.cif_sequence(seed=1002, frames=30)
-    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2)
+    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, schedule=schedule)
     assert_parity(g, o, p, seq.luma)
     assert (o["mbclass"] == 1).sum() > 1000 and (o["mbclass"] == 2).sum() > 500
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("S,h,K", [(7, 1, 8), (32, 2, 16), (64, 1, 3), (1, 2, 8), (16, 2, 0), (16, 1, 1)])
-def test_parameters(sme, S, h, K):
+def test_parameters(sme, S, h, K, schedule):
     seq = synth.make_sequence(160, 96, 4, seed=31 + S + K, vmax=6.0, noise_sigma=2.0, obj_frac=0.4)
-    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=S, h=h, K=K)
+    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=S, h=h, K=K, schedule=schedule)
     assert_parity(g, o, p, seq.luma)
 
 
@@ -169,45 +176,51 @@ def test_theta_epsilon(sme, theta, eps):
     assert_parity(g, o, p, seq.luma)
 
 
-def test_ref_distance_two_temporal_and_seed(sme):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_ref_distance_two_temporal_and_seed(sme, schedule):
     seq = synth.make_sequence(176, 144, 6, seed=12, vmax=4.0, obj_frac=0.4)
     rng = np.random.default_rng(0)
     M = 99
     temporal = rng.integers(-12, 13, (M, 2)).astype(np.int16)
     seed = rng.normal(0, 4, (4, M, 2)).astype(np.float32)
     seed[0, :5] = [1e6, -1e6]  # saturates
-    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, rd=2, temporal=temporal, seed=seed)
+    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, rd=2, temporal=temporal, seed=seed,
+                       schedule=schedule)
     assert_parity(g, o, p, seq.luma, rd=2)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("W,H,F", [(16, 16, 2), (16, 512, 3), (512, 16, 3), (48, 48, 5)])
-def test_degenerate_sizes_random_content(sme, W, H, F):
+def test_degenerate_sizes_random_content(sme, W, H, F, schedule):
     luma, alpha = synth.random_frames(W, H, F, seed=W * 7 + H, alpha_blobs=False, alpha_density=0.97)
     alpha[:, :, : W // 2] = 255
-    g, o, p = run_both(sme, luma, alpha, S=8, h=2)
+    g, o, p = run_both(sme, luma, alpha, S=8, h=2, schedule=schedule)
     assert_parity(g, o, p, luma)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("fill", [0, 255])
-def test_all_transparent_or_all_opaque(sme, fill):
+def test_all_transparent_or_all_opaque(sme, fill, schedule):
     seq = synth.make_sequence(96, 64, 3, seed=4)
     alpha = np.full_like(seq.alpha[0], fill)
-    g, o, p = run_both(sme, seq.luma, alpha, S=16, h=2)
+    g, o, p = run_both(sme, seq.luma, alpha, S=16, h=2, schedule=schedule)
     assert_parity(g, o, p, seq.luma)
     if fill == 0:
         assert (g["mv"] == 0).all() and (g["npos"] == 0).all()
 
 
-def test_batch_shapes_each_sequence(sme):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_batch_shapes_each_sequence(sme, schedule):
     """Sequences of the uneven-size batch (one of each frame size, 4 frames)."""
     sizes = [(176, 144), (352, 288), (704, 576), (1920, 1088)]
     for seq in synth.batch_sequences(seed=1003, frames=4, sizes=sizes):
         for i in range(seq.alpha.shape[0]):
-            g, o, p = run_both(sme, seq.luma, seq.alpha[i], S=16, h=2, want_pred=False)
+            g, o, p = run_both(sme, seq.luma, seq.alpha[i], S=16, h=2, want_pred=False, schedule=schedule)
             assert_parity(g, o, p)
 
 
-def test_golden_propagation_on_gpu(sme):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_golden_propagation_on_gpu(sme, schedule):
     """The hand-derived candidate-propagation fixture, through the GPU."""
     from conftest import read_golden
 
@@ -215,7 +228,7 @@ def test_golden_propagation_on_gpu(sme):
     luma, alpha = synth.translated_pair(W, H, (0, -2), seed=11)
     temporal = np.zeros((24, 2), np.int16)
     temporal[2] = (0, 2)
-    g, o, p = run_both(sme, luma, alpha, S=16, h=1, K=0, temporal=temporal)
+    g, o, p = run_both(sme, luma, alpha, S=16, h=1, K=0, temporal=temporal, schedule=schedule)
     want = read_golden("candidate_propagation.txt")["scenario C"]
     want = np.array([[tok.split(",") for tok in r] for r in want], int).reshape(-1, 2)
     assert np.array_equal(g["mv"][0].astype(int), want)
@@ -291,7 +304,8 @@ def test_repeated_runs_identical(sme):
     est.close()
 
 
-def test_bounded_wait_reports_timeout_and_context_recovers(sme):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_bounded_wait_reports_timeout_and_context_recovers(sme, schedule):
     """A result that is never published: dependants give up after a short
     limit, the launch ends, the host reads SME_ERR_TIMEOUT, and the next
     estimate on the same context is correct."""
@@ -299,8 +313,13 @@ def test_bounded_wait_reports_timeout_and_context_recovers(sme):
 
     W, H = 64, 64
     luma, alpha = synth.translated_pair(W, H, (1, 0), seed=3)
+    luma = np.concatenate([luma, luma[:1]])
+    alpha = np.concatenate([alpha, alpha[:1]])
     est = sme.Estimator(W, H, search_range=8, subpel=1)
-    est.debug_set_fault(skip_ticket=0, timeout_ns=20_000_000)  # MB 0: A of MB 1, B of MB 4
+    est.set_schedule(schedule)
+    # MB 0 of pair 0 is A of MB 1 and B of MB 4 (per-MB schedule) and T of
+    # MB 0 of pair 1 (both schedules)
+    est.debug_set_fault(skip_ticket=0, timeout_ns=20_000_000)
     with pytest.raises(SmeError) as e:
         est.estimate_sequence(cuda(luma), cuda(alpha))
     assert e.value.status == 4

@@ -67,10 +67,10 @@ def test_noalloc_matches_regular_entry_point_on_two_calls(sme):
 def test_noalloc_rejects_problems_beyond_its_scratch(sme):
     W, H = 1920, 1088
     params = sme.Params(W, H, 16, 2, 2.0, 1.0, 8, 1)
-    luma = torch.zeros((13, H, W), dtype=torch.uint8, device="cuda")
-    out = {"mv": torch.empty((12, (W // 16) * (H // 16), 2), dtype=torch.int16, device="cuda")}
+    luma = torch.zeros((12, H, W), dtype=torch.uint8, device="cuda")
+    out = {"mv": torch.empty((11, (W // 16) * (H // 16), 2), dtype=torch.int16, device="cuda")}
     assert _noalloc(sme, params, luma, luma, out) == 8  # SME_ERR_SCRATCH
     assert sme._lib().sme_strerror(8).decode().startswith("problem exceeds the fixed 4 MiB")
-    # 12 frames fit
-    assert _noalloc(sme, params, luma[:12], luma[:12], {"mv": out["mv"][:11]}) == 0
-    assert (out["mv"][:11] == 0).all()
+    # 11 frames fit
+    assert _noalloc(sme, params, luma[:11], luma[:11], {"mv": out["mv"][:10]}) == 0
+    assert (out["mv"][:10] == 0).all()

@@ -197,8 +197,14 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     SME_SCHED_AUTO (default) -- chosen per workload.
  *   SME_OPT_PAIR_WARPS: warps (MB rows in flight) per CTA of the pair
  *     schedule, 1..16; 0 (default) = automatic.
+ *   SME_OPT_MB_CTAS_PER_SM: resident CTAs (8 MBs each) per SM of the per-MB
+ *     schedule, 1..32, capped by occupancy; 0 (default) = as many as fit.
+ *   SME_OPT_SPECULATE: 1 (default) = in the per-MB schedule, cost each
+ *     candidate as soon as its vector arrives and take the first
+ *     pixel-recursive step at the first costed position while the other
+ *     candidates are awaited; 0 = do all of it after the last arrival.
  * Returns SME_ERR_ARG for an unknown option or value. */
-enum { SME_OPT_SCHEDULE = 1, SME_OPT_PAIR_WARPS = 2 };
+enum { SME_OPT_SCHEDULE = 1, SME_OPT_PAIR_WARPS = 2, SME_OPT_MB_CTAS_PER_SM = 3, SME_OPT_SPECULATE = 4 };
 enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2 };
 int sme_set_option(sme_ctx* ctx, int option, int value);
 

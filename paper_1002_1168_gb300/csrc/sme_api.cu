@@ -38,7 +38,7 @@ struct sme_ctx {
     std::vector<int> sched_host;
     int sched_P = -1;
     unsigned epoch = 0;
-    int schedule = kSchedAuto, pair_warps = 0;
+    int schedule = kSchedAuto, pair_warps = 0, mb_ctas_per_sm = 0, speculate = 1;
     int fault_ticket = -1;
     long long timeout_ns = kDefaultTimeoutNs;
     // pair interface
@@ -294,6 +294,7 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     a.epoch = c->epoch;
     a.total = (int)total;
     a.fault_ticket = c->fault_ticket;
+    a.speculate = c->speculate;
     a.timeout_ns = c->timeout_ns;
     if (pair) {
         int nw = c->pair_warps > 0 ? c->pair_warps : std::min(kPairWarpsMax, g.MBH);
@@ -303,7 +304,8 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
         const int grid = std::max(1, std::min(c->num_sms * per_sm, P));
         if (launch_me_pair(c->m, a, &maps, nw, grid, c->stream) != cudaSuccess) return SME_ERR_CUDA;
     } else {
-        const long long cap = (long long)c->num_sms * c->me_blocks_per_sm;
+        const int per_sm = c->mb_ctas_per_sm > 0 ? std::min(c->mb_ctas_per_sm, c->me_blocks_per_sm) : c->me_blocks_per_sm;
+        const long long cap = (long long)c->num_sms * per_sm;
         const long long want = ((long long)total + kMeWarps - 1) / kMeWarps;
         const int grid = (int)std::max(1LL, std::min<long long>(cap, want));
         if (launch_me(c->m, a, grid, c->stream) != cudaSuccess) return SME_ERR_CUDA;
@@ -692,6 +694,14 @@ int sme_set_option(sme_ctx* c, int option, int value)
     case SME_OPT_PAIR_WARPS:
         if (value < 0 || value > kPairWarpsMax) return SME_ERR_ARG;
         c->pair_warps = value;
+        return SME_OK;
+    case SME_OPT_MB_CTAS_PER_SM:
+        if (value < 0 || value > 32) return SME_ERR_ARG;
+        c->mb_ctas_per_sm = value;
+        return SME_OK;
+    case SME_OPT_SPECULATE:
+        if (value != 0 && value != 1) return SME_ERR_ARG;
+        c->speculate = value;
         return SME_OK;
     default:
         return SME_ERR_ARG;

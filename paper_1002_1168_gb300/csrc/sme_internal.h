@@ -94,6 +94,7 @@ struct MeArgs {
     unsigned epoch;
     int total;
     int fault_ticket;
+    int speculate;
     long long timeout_ns;
 };
 

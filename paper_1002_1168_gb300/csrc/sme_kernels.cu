@@ -572,13 +572,134 @@ struct MbResult {
     P8 r8;  // reference samples of the lane's pixels at the final vector
 };
 
+// One pixel-recursive step at d (Sec. 3.2): the FP32 update (Eqs. 3-5), the
+// proposal q, and -- when d lies inside V, so that clamping is the identity --
+// the SADs of the eight neighbours (Fig. 4) from one 3x3 neighbourhood.
+struct PrsStep {
+    float lastx, lasty;
+    int qx, qy;
+    bool qmove, inner;
+    unsigned cq;      // SAD at q (when qmove)
+    P8 q8;            // samples at q (when qmove)
+    unsigned sad9[9]; // neighbour SADs, raster order (when inner)
+};
+
+__device__ __forceinline__ PrsStep prs_eval(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
+                                            const P8& c8, const float (&ux)[8], const float (&uy)[8], int nx, int ny,
+                                            const VRange& V, int dx, int dy, const P8& r8, unsigned cost)
+{
+    const int h = m.h;
+    PrsStep st;
+    float sx, sy;
+    grad_sums(r8, c8, ux, uy, sx, sy);
+    st.lastx = update_of(sx, nx, m.eps);
+    st.lasty = update_of(sy, ny, m.eps);
+    st.qx = clampi(dx + (int)roundf(__fmul_rn((float)h, st.lastx)), V.lox, V.hix);
+    st.qy = clampi(dy + (int)roundf(__fmul_rn((float)h, st.lasty)), V.loy, V.hiy);
+    st.qmove = (st.qx != dx) || (st.qy != dy);
+    st.inner = dx > V.lox && dx < V.hix && dy > V.loy && dy < V.hiy;
+    st.cq = 0u;
+    st.q8 = r8;
+    const bool qnear = st.qmove && abs(st.qx - dx) <= 1 && abs(st.qy - dy) <= 1;
+    if (st.inner) {
+        P8 nb9[9];
+        block3x3(win, pitch, lx, ly, dx, dy, h, nb9);
+        warp_sum2(sad8(nb9[0], c8), sad8(nb9[1], c8), st.sad9[0], st.sad9[1]);
+        warp_sum2(sad8(nb9[2], c8), sad8(nb9[3], c8), st.sad9[2], st.sad9[3]);
+        warp_sum2(sad8(nb9[5], c8), sad8(nb9[6], c8), st.sad9[5], st.sad9[6]);
+        warp_sum2(sad8(nb9[7], c8), sad8(nb9[8], c8), st.sad9[7], st.sad9[8]);
+        st.sad9[4] = cost;
+        if (qnear) {
+            const int qi = (st.qy - dy + 1) * 3 + (st.qx - dx + 1);
+#pragma unroll
+            for (int n = 0; n < 9; ++n)
+                if (n == qi) {
+                    st.cq = st.sad9[n];
+                    st.q8 = nb9[n];
+                }
+            return st;
+        }
+    }
+    if (st.qmove) {
+        st.q8 = ref8(win, pitch, lx, ly, st.qx, st.qy, h);
+        st.cq = __reduce_add_sync(kFull, sad8(st.q8, c8));
+    }
+    return st;
+}
+
+// The decision of one step in the paper's order: the proposal if it lowers
+// the SAD, else the first strict minimum of the eight clamped neighbours,
+// else stop.  Logs the evaluated positions.  Returns true when d moved.
+__device__ __forceinline__ bool prs_decide(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
+                                           const P8& c8, const VRange& V, const PrsStep& st, int& dx, int& dy,
+                                           unsigned& cost, P8& r8, int* slog, int& nlog, int lane)
+{
+    const int h = m.h;
+    if (st.qmove) {
+        if (lane == 0) slog[nlog] = pack_mv(st.qx, st.qy);
+        ++nlog;
+        if (st.cq < cost) {
+            dx = st.qx;
+            dy = st.qy;
+            cost = st.cq;
+            r8 = st.q8;
+            return true;
+        }
+    }
+    if (st.inner) {
+        unsigned bc = cost;
+        int bn = 4;
+#pragma unroll
+        for (int n = 0; n < 9; ++n) {
+            if (n == 4) continue;
+            if (lane == 0) slog[nlog] = pack_mv(dx + n % 3 - 1, dy + n / 3 - 1);
+            ++nlog;
+            if (st.sad9[n] < bc) {
+                bc = st.sad9[n];
+                bn = n;
+            }
+        }
+        if (bc < cost) {
+            dx += bn % 3 - 1;
+            dy += bn / 3 - 1;
+            cost = bc;
+            r8 = ref8(win, pitch, lx, ly, dx, dy, h);
+            return true;
+        }
+        return false;
+    }
+    // d on the edge of V: the clamped neighbours one by one.
+    unsigned bc = cost;
+    int bx = dx, by = dy;
+#pragma unroll
+    for (int n = 1; n < 9; ++n) {
+        const int e = n < 5 ? n - 1 : n;  // 3x3 raster without its centre
+        const int ex = clampi(dx + e % 3 - 1, V.lox, V.hix), ey = clampi(dy + e / 3 - 1, V.loy, V.hiy);
+        if (ex != dx || ey != dy) {
+            const unsigned cn = __reduce_add_sync(kFull, sad8(ref8(win, pitch, lx, ly, ex, ey, h), c8));
+            if (lane == 0) slog[nlog] = pack_mv(ex, ey);
+            ++nlog;
+            if (cn < bc) {
+                bc = cn;
+                bx = ex;
+                by = ey;
+            }
+        }
+    }
+    if (bc < cost) {
+        dx = bx;
+        dy = by;
+        cost = bc;
+        r8 = ref8(win, pitch, lx, ly, dx, dy, h);
+        return true;
+    }
+    return false;
+}
+
 // Fig. 1 from the candidate comparison on: shape cost (boundary) or texture
 // SAD (opaque) of the candidates, first strict minimum, and on opaque MBs the
 // pixel recursive search of Sec. 3.2.  The candidates are already logged in
-// slog[0..nc); the evaluated PRS positions are appended by lane 0.  The
-// neighbours of the eight-direction check are evaluated together with the
-// proposal from one 3x3 neighbourhood when d is inside V; the decisions
-// follow the paper's order (proposal first, then the neighbours).
+// slog[0..nc); the evaluated PRS positions are appended by lane 0.
 __device__ __forceinline__ MbResult search_mb(const Method& m, int cls, const uint8_t* win, int pitch, int lx,
                                               int ly, const P8& c8, const float (&ux)[8], const float (&uy)[8],
                                               int nx, int ny, const VRange& V, const int (&cand)[5], int nc,
@@ -639,116 +760,10 @@ __device__ __forceinline__ MbResult search_mb(const Method& m, int cls, const ui
         float lastx = 0.0f, lasty = 0.0f;
         while (iters < m.K) {
             ++iters;
-            float sx, sy;
-            grad_sums(r8, c8, ux, uy, sx, sy);
-            lastx = update_of(sx, nx, m.eps);
-            lasty = update_of(sy, ny, m.eps);
-            const int qx = clampi(dx + (int)roundf(__fmul_rn((float)h, lastx)), V.lox, V.hix);
-            const int qy = clampi(dy + (int)roundf(__fmul_rn((float)h, lasty)), V.loy, V.hiy);
-            const bool qmove = (qx != dx) || (qy != dy);
-            const bool qnear = qmove && abs(qx - dx) <= 1 && abs(qy - dy) <= 1;
-            const bool inner = dx > V.lox && dx < V.hix && dy > V.loy && dy < V.hiy;
-            if (inner) {
-                // The proposal (when it is a neighbour) and the eight
-                // neighbours from one neighbourhood; clamping is the identity.
-                P8 nb9[9];
-                block3x3(win, pitch, lx, ly, dx, dy, h, nb9);
-                unsigned sad9[9];
-                warp_sum2(sad8(nb9[0], c8), sad8(nb9[1], c8), sad9[0], sad9[1]);
-                warp_sum2(sad8(nb9[2], c8), sad8(nb9[3], c8), sad9[2], sad9[3]);
-                warp_sum2(sad8(nb9[5], c8), sad8(nb9[6], c8), sad9[5], sad9[6]);
-                warp_sum2(sad8(nb9[7], c8), sad8(nb9[8], c8), sad9[7], sad9[8]);
-                sad9[4] = cost;
-                if (qmove) {
-                    unsigned cq;
-                    P8 q8;
-                    if (qnear) {
-                        const int qi = (qy - dy + 1) * 3 + (qx - dx + 1);
-                        cq = sad9[0];
-                        q8 = nb9[0];
-#pragma unroll
-                        for (int n = 1; n < 9; ++n)
-                            if (n == qi) {
-                                cq = sad9[n];
-                                q8 = nb9[n];
-                            }
-                    } else {
-                        q8 = ref8(win, pitch, lx, ly, qx, qy, h);
-                        cq = __reduce_add_sync(kFull, sad8(q8, c8));
-                    }
-                    if (lane == 0) slog[nlog] = pack_mv(qx, qy);
-                    ++nlog;
-                    if (cq < cost) {
-                        dx = qx;
-                        dy = qy;
-                        cost = cq;
-                        r8 = q8;
-                        continue;
-                    }
-                }
-                // Fig. 4: eight directions at one MV unit, first strict minimum.
-                unsigned bc = cost;
-                int bn = 4;
-#pragma unroll
-                for (int n = 0; n < 9; ++n) {
-                    if (n == 4) continue;
-                    if (lane == 0) slog[nlog] = pack_mv(dx + n % 3 - 1, dy + n / 3 - 1);
-                    ++nlog;
-                    if (sad9[n] < bc) {
-                        bc = sad9[n];
-                        bn = n;
-                    }
-                }
-                if (bc < cost) {
-#pragma unroll
-                    for (int n = 0; n < 9; ++n)
-                        if (n == bn) r8 = nb9[n];
-                    dx += bn % 3 - 1;
-                    dy += bn / 3 - 1;
-                    cost = bc;
-                    continue;
-                }
-                break;
-            }
-            // d on the edge of V: the clamped neighbours one by one.
-            if (qmove) {
-                const P8 q8 = ref8(win, pitch, lx, ly, qx, qy, h);
-                const unsigned cq = __reduce_add_sync(kFull, sad8(q8, c8));
-                if (lane == 0) slog[nlog] = pack_mv(qx, qy);
-                ++nlog;
-                if (cq < cost) {
-                    dx = qx;
-                    dy = qy;
-                    cost = cq;
-                    r8 = q8;
-                    continue;
-                }
-            }
-            unsigned bc = cost;
-            int bx = dx, by = dy;
-#pragma unroll
-            for (int n = 1; n < 9; ++n) {
-                const int e = n < 5 ? n - 1 : n;  // 3x3 raster without its centre
-                const int ex = clampi(dx + e % 3 - 1, V.lox, V.hix), ey = clampi(dy + e / 3 - 1, V.loy, V.hiy);
-                if (ex != dx || ey != dy) {
-                    const unsigned cn = __reduce_add_sync(kFull, sad8(ref8(win, pitch, lx, ly, ex, ey, h), c8));
-                    if (lane == 0) slog[nlog] = pack_mv(ex, ey);
-                    ++nlog;
-                    if (cn < bc) {
-                        bc = cn;
-                        bx = ex;
-                        by = ey;
-                    }
-                }
-            }
-            if (bc < cost) {
-                dx = bx;
-                dy = by;
-                cost = bc;
-                r8 = ref8(win, pitch, lx, ly, dx, dy, h);
-                continue;
-            }
-            break;
+            const PrsStep st = prs_eval(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, dx, dy, r8, cost);
+            lastx = st.lastx;
+            lasty = st.lasty;
+            if (!prs_decide(m, win, pitch, lx, ly, c8, V, st, dx, dy, cost, r8, slog, nlog, lane)) break;
         }
         res.r8 = r8;
         res.iters = iters;
@@ -760,6 +775,19 @@ __device__ __forceinline__ MbResult search_mb(const Method& m, int cls, const ui
     res.cost = cost;
     res.nlog = nlog;
     return res;
+}
+
+// Shape cost of one candidate: lanes 0..15 take the 16 rows (lanes 16..31
+// repeat them); every lane gets the total.
+__device__ __forceinline__ unsigned shape_cost1(const uint32_t* pcur, const uint32_t* pref, int Wp, int X0, int Y0,
+                                                int key, int h, int lane)
+{
+    unsigned s = shape_row(pcur, pref, Wp, X0, Y0, lane & 15, mv_x(key) / h, mv_y(key) / h);
+    s += __shfl_xor_sync(kFull, s, 8);
+    s += __shfl_xor_sync(kFull, s, 4);
+    s += __shfl_xor_sync(kFull, s, 2);
+    s += __shfl_xor_sync(kFull, s, 1);
+    return s;
 }
 
 // Off the dependency chain: per-MB outputs, the distinct evaluated positions
@@ -923,39 +951,159 @@ __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
         const VRange V = valid_range(W, H, m, X0, Y0);
 
         // ---- candidates A, B, C, T (Fig. 1, Fig. 3) + optional seed ----
+        // Lanes 0..3 poll the ready words of A, B, C, T.  While the warp
+        // waits, every candidate whose vector has arrived is costed at once,
+        // and the first pixel-recursive step is taken speculatively at the
+        // first costed position; the results are exactly those the search
+        // computes after the wait, so nothing changes but the latency.
+        int dep = -1;
+        if (lane == 0 && u > 0) dep = gid - 1;                       // A
+        if (lane == 1 && v > 0) dep = gid - MBW;                     // B
+        if (lane == 2 && v > 0 && u < MBW - 1) dep = gid - MBW + 1;  // C
+        if (lane == 3 && k > 0) dep = gid - M;                       // T
         int key = 0;
-        bool failed = false;
-        if (lane < 4) {
-            int dep = -1;
-            if (lane == 0 && u > 0) dep = gid - 1;                       // A
-            if (lane == 1 && v > 0) dep = gid - MBW;                     // B
-            if (lane == 2 && v > 0 && u < MBW - 1) dep = gid - MBW + 1;  // C
-            if (lane == 3 && k > 0) dep = gid - M;                       // T
-            if (dep >= 0) {
-                unsigned val = 0;
-                if (wait_ready(a.ready + dep, a.epoch, a.status, a.timeout_ns, val)) {
-                    key = (int)val;
-                } else {
-                    failed = true;
-                    if (!ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
-                }
-            } else if (lane == 3 && sd->temporal_in) {
-                key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
-            }
-            key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
-        } else if (lane == 4 && sd->seed) {
-            key = seed_key(sd, idx, h, V);
-        }
-        if (__any_sync(kFull, failed)) break;
+        if (lane == 3 && k == 0 && sd->temporal_in)
+            key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
+        if (lane == 4 && sd->seed) key = seed_key(sd, idx, h, V);
+        if (lane < 4) key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
         const int nc = sd->seed ? 5 : 4;
+        bool res_l = dep < 0;
+        unsigned have = __ballot_sync(kFull, lane < nc && res_l) & ((1u << nc) - 1u);
+        const unsigned all = (1u << nc) - 1u;
+        unsigned costed = 0;
+        unsigned ccost[5] = {0u, 0u, 0u, 0u, 0u};
+        int ckey[5] = {0, 0, 0, 0, 0};
+        P8 cs8[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) cs8[c] = c8;
+        bool spec = false;
+        int spec_key = 0;
+        PrsStep sp;
+        const uint32_t* pcur = sd->packed + (size_t)(k + rd) * H * sd->Wp;
+        const uint32_t* pref = sd->packed + (size_t)k * H * sd->Wp;
+        const int lx = x0 - wx0, ly = y - wy0;
+        bool failed = false;
+        unsigned long long t_start = 0;
+        for (unsigned it = 0;; ++it) {
+            // The next poll is issued first, so its latency overlaps the
+            // costing below; its result is consumed at the end of the pass.
+            unsigned long long w = 0;
+            if (lane < 4 && !res_l) w = ld_ready(a.ready + dep);
+            const unsigned fresh = (a.speculate || have == all) ? (have & ~costed) : 0u;
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                if (fresh & (1u << c)) {
+                    const int kc = __shfl_sync(kFull, key, c);
+                    ckey[c] = kc;
+                    // A position already costed is not evaluated again.
+                    bool dup = false;
+#pragma unroll
+                    for (int e = 0; e < 5; ++e)
+                        if (e != c && !dup && (costed & (1u << e)) && ckey[e] == kc) {
+                            ccost[c] = ccost[e];
+                            cs8[c] = cs8[e];
+                            dup = true;
+                        }
+                    if (!dup) {
+                        if (cls == SME_BOUNDARY) {
+                            ccost[c] = shape_cost1(pcur, pref, sd->Wp, X0, Y0, kc, h, lane);
+                        } else {
+                            cs8[c] = ref8(win, pitch, lx, ly, mv_x(kc), mv_y(kc), h);
+                            ccost[c] = __reduce_add_sync(kFull, sad8(cs8[c], c8));
+                        }
+                    }
+                    costed |= 1u << c;
+                }
+            if (costed == all) break;
+            if (a.speculate && cls == SME_OPAQUE && costed && m.K > 0) {
+                // The first pixel-recursive step at the provisional winner
+                // (first strict minimum among the candidates costed so far).
+                int pb = -1;
+                unsigned pc = 0;
+#pragma unroll
+                for (int c = 0; c < 5; ++c)
+                    if ((costed & (1u << c)) && (pb < 0 || ccost[c] < pc)) {
+                        pb = c;
+                        pc = ccost[c];
+                    }
+                int pk = ckey[0];
+                P8 r0 = cs8[0];
+#pragma unroll
+                for (int c = 1; c < 5; ++c)
+                    if (c == pb) {
+                        pk = ckey[c];
+                        r0 = cs8[c];
+                    }
+                if (!spec || pk != spec_key) {
+                    sp = prs_eval(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, mv_x(pk), mv_y(pk), r0, pc);
+                    spec_key = pk;
+                    spec = true;
+                }
+            }
+            if (lane < 4 && !res_l && (unsigned)(w >> 32) == a.epoch) {
+                const int kk = (int)(unsigned)w;
+                key = pack_mv(clampi(mv_x(kk), V.lox, V.hix), clampi(mv_y(kk), V.loy, V.hiy));
+                res_l = true;
+            }
+            have = __ballot_sync(kFull, lane < nc && res_l) & all;
+            if ((it & 15u) == 15u) {
+                // Bounded wait: the launch's abort word, a time limit, an iteration cap.
+                int give_up = 0;
+                if (lane == 0) {
+                    const unsigned long long now = globaltimer();
+                    if (t_start == 0) t_start = now;
+                    give_up = ld_relaxed(&a.status->abort) || (long long)(now - t_start) > a.timeout_ns ||
+                              it > (1u << 24);
+                }
+                if (__shfl_sync(kFull, give_up, 0)) {
+                    if (lane == 0 && !ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
+                    failed = true;
+                    break;
+                }
+            }
+        }
+        if (failed) break;
         int cand[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) cand[c] = __shfl_sync(kFull, key, c);
         if (lane < nc) slog[lane] = key;
 
-        const MbResult r = search_mb(m, cls, win, pitch, x0 - wx0, y - wy0, c8, ux, uy, nx, ny, V, cand, nc,
-                                     sd->packed + (size_t)(k + rd) * H * sd->Wp, sd->packed + (size_t)k * H * sd->Wp,
-                                     sd->Wp, X0, Y0, slog, lane);
+        // First strict minimum in the order A, B, C, T (+ seed).
+        MbResult r;
+        int best = cand[0];
+        unsigned cost = ccost[0];
+        P8 r8 = cs8[0];
+#pragma unroll
+        for (int c = 1; c < 5; ++c)
+            if (c < nc && ccost[c] < cost) {
+                cost = ccost[c];
+                best = cand[c];
+                r8 = cs8[c];
+            }
+        int dx = mv_x(best), dy = mv_y(best), nlog = nc, iters = 0;
+        float lastx = 0.0f, lasty = 0.0f;
+        if (cls == SME_BOUNDARY) r8 = ref8(win, pitch, lx, ly, dx, dy, h);  // prediction at the shape winner
+        if (cls == SME_OPAQUE) {
+            // Sec. 3.2: pixel recursive search (the first step may be the
+            // speculative one, taken at the same position).
+            while (iters < m.K) {
+                PrsStep st;
+                if (iters == 0 && spec && best == spec_key) st = sp;
+                else st = prs_eval(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, dx, dy, r8, cost);
+                ++iters;
+                lastx = st.lastx;
+                lasty = st.lasty;
+                if (!prs_decide(m, win, pitch, lx, ly, c8, V, st, dx, dy, cost, r8, slog, nlog, lane)) break;
+            }
+        }
+        r.dx = dx;
+        r.dy = dy;
+        r.cost = cost;
+        r.iters = iters;
+        r.nlog = nlog;
+        r.lastx = lastx;
+        r.lasty = lasty;
+        r.r8 = r8;
 
         // ---- publish the vector first: it is on the dependency chain ----
         if (lane == 0) {

@@ -227,6 +227,7 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
     a.epoch = 1;
     a.total = (int)PM;
     a.fault_ticket = -1;
+    a.speculate = 1;
     a.timeout_ns = kDefaultTimeoutNs;
     const long long cap = (long long)sms * per_sm;
     const long long want = ((long long)PM + kMeWarps - 1) / kMeWarps;

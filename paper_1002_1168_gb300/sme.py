@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsme.so")
 
 SME_TRANSPARENT, SME_OPAQUE, SME_BOUNDARY = 0, 1, 2
-SME_OPT_SCHEDULE, SME_OPT_PAIR_WARPS = 1, 2
+SME_OPT_SCHEDULE, SME_OPT_PAIR_WARPS, SME_OPT_MB_CTAS_PER_SM, SME_OPT_SPECULATE = 1, 2, 3, 4
 SCHEDULES = {"auto": 0, "mb": 1, "pair": 2}
 STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4: "SME_ERR_TIMEOUT",
           5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE", 8: "SME_ERR_SCRATCH"}

@@ -208,6 +208,54 @@ enum { SME_OPT_SCHEDULE = 1, SME_OPT_PAIR_WARPS = 2, SME_OPT_MB_CTAS_PER_SM = 3,
 enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2 };
 int sme_set_option(sme_ctx* ctx, int option, int value);
 
+/* Autotuner for a context: runs the estimate on the given sequence once per
+ * candidate execution configuration (schedule, CTAs per SM, speculation,
+ * pair-schedule warps -- see sme_set_option), `trials` times each, and keeps
+ * the fastest by device time.  Every configuration computes bit-identical
+ * results, so the choice changes only speed.  Arguments as for
+ * sme_estimate_sequence; synchronises.  No counterpart in the paper. */
+int sme_autotune(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha, int n_frames,
+                 const sme_outputs* out, int trials);
+
+/* Batches: many independent sequences (each one VOP, Sec. 1: every object
+ * is coded as its own plane) of uneven frame size and length, estimated by
+ * one classification launch and one persistent ME launch whose tickets
+ * interleave all sequences by wavefront step.  The method parameters
+ * (search range, subpel, Theta, eps, max_iters, ref_distance) are shared;
+ * width/height come from each sequence.  Every pointer in sme_sequence is
+ * caller-owned device memory that must stay valid (and keep its address)
+ * for the life of the batch, because sme_batch_run replays the same work.
+ *   sme_batch_create   validates, allocates scratch, builds the schedule.
+ *   sme_batch_tune     times the candidate execution configurations
+ *                      (`trials` runs each), keeps the fastest, captures
+ *                      the launches in a CUDA graph; synchronises.
+ *   sme_batch_run      enqueues one pass over all sequences (graph replay
+ *                      once tuned) on the batch's stream.
+ *   sme_batch_synchronize  waits and reports a device-side failure.
+ *   sme_batch_config   the configuration in use (schedule SME_SCHED_*,
+ *                      its parameter: CTAs per SM for SME_SCHED_MB (0 = all
+ *                      that fit) or warps for SME_SCHED_PAIR, speculation)
+ *                      and the tuned time per run in ms (0 before tuning).
+ * Results per sequence are exactly those of sme_estimate_sequence on it. */
+typedef struct {
+    int width, height, n_frames;
+    const uint8_t* luma;        /* [n_frames][height][width] */
+    const uint8_t* alpha;       /* [n_frames][height][width] */
+    const sme_mv* temporal_in;  /* [M] or NULL */
+    const float* seed;          /* [P][M][2] or NULL */
+    sme_outputs out;
+} sme_sequence;
+
+typedef struct sme_batch sme_batch;
+
+int sme_batch_create(sme_batch** out, const sme_params* p, const sme_sequence* seqs, int n,
+                     void* cuda_stream);
+int sme_batch_tune(sme_batch* b, int trials);
+int sme_batch_run(sme_batch* b);
+int sme_batch_synchronize(sme_batch* b);
+int sme_batch_config(sme_batch* b, int* schedule, int* param, int* speculate, float* best_ms);
+int sme_batch_destroy(sme_batch* b);
+
 /* Stage timing (tracing).  sme_profile_begin makes every following
  * sme_estimate_sequence* call record CUDA events around its two launches on
  * the context's stream (classification, then the persistent ME launch), for

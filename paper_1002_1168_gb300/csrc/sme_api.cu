@@ -37,7 +37,6 @@ struct sme_ctx {
     DevBuf packed, cls, ready, sched, desc, qpacked, qcls;
     std::vector<int> sched_host;
     int sched_P = -1;
-    unsigned epoch = 0;
     int schedule = kSchedAuto, pair_warps = 0, mb_ctas_per_sm = 0, speculate = 1;
     int fault_ticket = -1;
     long long timeout_ns = kDefaultTimeoutNs;
@@ -236,6 +235,9 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
 
     SeqDesc d{};
     d.luma = luma;
+    d.alpha = alpha;
+    d.packed_w = (uint32_t*)c->packed.p;
+    d.cls_w = (uint8_t*)c->cls.p;
     d.packed = (const uint32_t*)c->packed.p;
     d.cls = (const uint8_t*)c->cls.p;
     d.temporal_in = temporal_in;
@@ -257,6 +259,7 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     d.Wp = g.Wp;
     d.P = P;
     d.rd = rd;
+    d.F = F;
     d.gid_base = 0;
 
     // The classify launch also stores the descriptor the ME launch reads.
@@ -278,7 +281,6 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     if (launch_classify(g, ca, c->stream) != cudaSuccess) return SME_ERR_CUDA;
     if (ev && cudaEventRecord(ev[1], c->stream) != cudaSuccess) return SME_ERR_CUDA;
 
-    if (++c->epoch == 0) c->epoch = 1;
     MeArgs a{};
     a.seqs = (const SeqDesc*)c->desc.p;
     a.sched = pair ? nullptr : (const int*)c->sched.p;
@@ -291,7 +293,6 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     a.ready = (unsigned long long*)c->ready.p;
     a.status = c->status;
     a.m = c->m;
-    a.epoch = c->epoch;
     a.total = (int)total;
     a.fault_ticket = c->fault_ticket;
     a.speculate = c->speculate;
@@ -331,6 +332,38 @@ int read_status(sme_ctx* c)
         return err;
     }
     return SME_OK;
+}
+
+struct ExecCfg {
+    int schedule, pair_warps, mb_ctas_per_sm, speculate;
+};
+const ExecCfg kTuneCandidates[] = {
+    {kSchedMB, 0, 1, 1}, {kSchedMB, 0, 0, 1}, {kSchedMB, 0, 1, 0}, {kSchedMB, 0, 0, 0},
+    {kSchedPair, 4, 0, 0}, {kSchedPair, 8, 0, 0}, {kSchedPair, 16, 0, 0},
+};
+
+// Device time of `trials` back-to-back runs of `enqueue` (the minimum), ms;
+// a negative value means the configuration failed.
+template <class F>
+float time_runs(cudaStream_t s, int trials, F enqueue)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0f;
+    float best = -1.0f;
+    for (int i = 0; i < trials; ++i) {
+        if (cudaEventRecord(e0, s) != cudaSuccess || enqueue() != SME_OK || cudaEventRecord(e1, s) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess) {
+            best = -1.0f;
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best < 0.0f || ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    return best;
 }
 
 }  // namespace
@@ -708,6 +741,36 @@ int sme_set_option(sme_ctx* c, int option, int value)
     }
 }
 
+int sme_autotune(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_frames, const sme_outputs* out,
+                 int trials)
+{
+    if (!c || trials < 1) return SME_ERR_ARG;
+    int rc = run_sequence(c, luma, alpha, n_frames, nullptr, nullptr, out);  // validates, allocates
+    if (rc) return rc;
+    if ((rc = sme_synchronize(c))) return rc;
+    float best = -1.0f;
+    ExecCfg pick = {c->schedule, c->pair_warps, c->mb_ctas_per_sm, c->speculate};
+    for (const ExecCfg& e : kTuneCandidates) {
+        c->schedule = e.schedule;
+        c->pair_warps = e.pair_warps;
+        c->mb_ctas_per_sm = e.mb_ctas_per_sm;
+        c->speculate = e.speculate;
+        const float ms = time_runs(c->stream, trials, [&] {
+            return run_sequence(c, luma, alpha, n_frames, nullptr, nullptr, out);
+        });
+        if (read_status(c) != SME_OK) continue;
+        if (ms > 0.0f && (best < 0.0f || ms < best)) {
+            best = ms;
+            pick = e;
+        }
+    }
+    c->schedule = pick.schedule;
+    c->pair_warps = pick.pair_warps;
+    c->mb_ctas_per_sm = pick.mb_ctas_per_sm;
+    c->speculate = pick.speculate;
+    return best > 0.0f ? SME_OK : SME_ERR_CUDA;
+}
+
 int sme_profile_begin(sme_ctx* c, int max_calls)
 {
     if (!c || max_calls < 1 || max_calls > (1 << 20)) return SME_ERR_ARG;
@@ -753,6 +816,330 @@ int sme_debug_set_fault(sme_ctx* c, int skip_ticket, long long timeout_ns)
     if (!c) return SME_ERR_ARG;
     c->fault_ticket = skip_ticket < 0 ? -1 : skip_ticket;
     c->timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
+    return SME_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================
+// Batches of sequences
+// ====================================================================
+struct sme_batch {
+    sme_params prm;
+    Method m;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    int device = 0, num_sms = 0, smem_optin = 0, me_blocks_per_sm = 0;
+    int n = 0, total_frames = 0, max_mbh = 0, mbw_max = 0, total_units = 0;
+    long long total_mbs = 0;
+    DevStatus* status = nullptr;
+    DevBuf descs, packed, cls, ready, sched, sched_seq, unit_seq, unit_pair, fseq, ffrm, maps;
+    ExecCfg cfg = {kSchedMB, 0, 0, 1};
+    float tuned_ms = 0.0f;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int batch_enqueue(sme_batch* b, cudaStream_t s)
+{
+    ClassifyBatchArgs ca{(const SeqDesc*)b->descs.p, (const int*)b->fseq.p, (const int*)b->ffrm.p, b->status};
+    if (launch_classify_batch(ca, b->max_mbh, b->total_frames, s) != cudaSuccess) return SME_ERR_CUDA;
+    MeArgs a{};
+    a.seqs = (const SeqDesc*)b->descs.p;
+    a.sched = (const int*)b->sched.p;
+    a.sched_seq = (const int*)b->sched_seq.p;
+    a.unit_seq = (const int*)b->unit_seq.p;
+    a.unit_pair = (const int*)b->unit_pair.p;
+    a.tmaps = (const CUtensorMap*)b->maps.p;
+    a.total_units = b->total_units;
+    a.mbw_max = b->mbw_max;
+    a.ready = (unsigned long long*)b->ready.p;
+    a.status = b->status;
+    a.m = b->m;
+    a.total = (int)b->total_mbs;
+    a.fault_ticket = -1;
+    a.speculate = b->cfg.speculate;
+    a.timeout_ns = kDefaultTimeoutNs;
+    if (b->cfg.schedule == kSchedPair) {
+        int nw = b->cfg.pair_warps > 0 ? b->cfg.pair_warps : kPairWarpsMax;
+        while (nw > 1 && me_pair_smem_bytes(b->m.S, nw, b->mbw_max) > (size_t)b->smem_optin) --nw;
+        int per_sm = 0;
+        if (me_pair_occupancy(b->m.S, nw, b->mbw_max, &per_sm) != cudaSuccess || per_sm < 1) return SME_ERR_CUDA;
+        const int grid = std::max(1, std::min(b->num_sms * per_sm, b->total_units));
+        MapSet unused;
+        memset(&unused, 0, sizeof(unused));
+        return cuda_status(launch_me_pair(b->m, a, &unused, nw, grid, s));
+    }
+    const int per_sm =
+        b->cfg.mb_ctas_per_sm > 0 ? std::min(b->cfg.mb_ctas_per_sm, b->me_blocks_per_sm) : b->me_blocks_per_sm;
+    const long long want = (b->total_mbs + kMeWarps - 1) / kMeWarps;
+    const int grid = (int)std::max(1LL, std::min<long long>((long long)b->num_sms * per_sm, want));
+    return cuda_status(launch_me(b->m, a, grid, s));
+}
+
+void batch_drop_graph(sme_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Capture one pass in a CUDA graph on the private stream; without a graph the
+// batch simply launches directly.
+void batch_capture(sme_batch* b)
+{
+    batch_drop_graph(b);
+    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const int rc = batch_enqueue(b, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (rc != SME_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return;
+    }
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        b->exec = nullptr;
+        cudaGetLastError();
+        return;
+    }
+    b->graph = g;
+}
+
+int batch_read_status(sme_batch* b)
+{
+    int err = 0;
+    if (cudaMemcpy(&err, &b->status->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SME_ERR_CUDA;
+    if (err && cudaMemset(&b->status->err, 0, sizeof(int)) != cudaSuccess) return SME_ERR_CUDA;
+    return err;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sme_batch_create(sme_batch** out, const sme_params* p, const sme_sequence* seqs, int n, void* stream)
+{
+    if (!out || !seqs || n < 1) return SME_ERR_ARG;
+    *out = nullptr;
+    sme_params q = p ? *p : sme_params{};
+    if (!p) return SME_ERR_ARG;
+    q.width = seqs[0].width;
+    q.height = seqs[0].height;
+    int rc = check_params(&q);
+    if (rc) return rc;
+    const int rd = p->ref_distance;
+    for (int i = 0; i < n; ++i) {
+        const sme_sequence& x = seqs[i];
+        if (x.width <= 0 || x.height <= 0 || x.width % 16 || x.height % 16 || x.width > kMaxDim ||
+            x.height > kMaxDim)
+            return SME_ERR_SIZE;
+        if (!x.luma || !x.alpha || !x.out.mv || x.n_frames <= rd || !aligned16(x.luma) || !aligned16(x.alpha))
+            return SME_ERR_ARG;
+    }
+    sme_batch* b = new (std::nothrow) sme_batch();
+    if (!b) return SME_ERR_NOMEM;
+    b->prm = *p;
+    b->m = make_method(*p);
+    b->stream = (cudaStream_t)stream;
+    b->n = n;
+    auto fail = [&](int code) {
+        sme_batch_destroy(b);
+        return code;
+    };
+    if (cudaGetDevice(&b->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess ||
+        me_occupancy(b->m.S, &b->me_blocks_per_sm) != cudaSuccess || b->me_blocks_per_sm < 1 ||
+        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SME_ERR_CUDA);
+    }
+    if (cudaMalloc(&b->status, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMemset(b->status, 0, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SME_ERR_NOMEM);
+    }
+    // Geometry, scratch offsets and descriptors.
+    std::vector<SeqDesc> d(n);
+    size_t packed_words = 0, cls_bytes = 0;
+    long long gid = 0;
+    int max_steps = 0;
+    std::vector<int> fseq, ffrm;
+    for (int i = 0; i < n; ++i) {
+        const sme_sequence& x = seqs[i];
+        SeqDesc& e = d[i];
+        e = SeqDesc{};
+        e.W = x.width;
+        e.H = x.height;
+        e.MBW = x.width / 16;
+        e.MBH = x.height / 16;
+        e.M = e.MBW * e.MBH;
+        e.Wp = (((x.width + 31) / 32 + 1) + 3) & ~3;
+        e.F = x.n_frames;
+        e.P = x.n_frames - rd;
+        e.rd = rd;
+        e.gid_base = (int)gid;
+        gid += (long long)e.P * e.M;
+        packed_words += (size_t)e.F * e.H * e.Wp;
+        cls_bytes += (size_t)e.F * e.M;
+        b->total_frames += e.F;
+        b->max_mbh = std::max(b->max_mbh, e.MBH);
+        b->mbw_max = std::max(b->mbw_max, e.MBW);
+        b->total_units += e.P;
+        max_steps = std::max(max_steps, (e.MBW - 1) + 2 * (e.MBH - 1) + e.P);
+        for (int f = 0; f < e.F; ++f) {
+            fseq.push_back(i);
+            ffrm.push_back(f);
+        }
+    }
+    if (gid > (long long)INT32_MAX) return fail(SME_ERR_SIZE);
+    b->total_mbs = gid;
+    if ((rc = ensure(b->packed, packed_words * 4)) || (rc = ensure(b->cls, cls_bytes)) ||
+        (rc = ensure(b->ready, (size_t)gid * 8, true, nullptr)) || (rc = ensure(b->descs, sizeof(SeqDesc) * n)) ||
+        (rc = ensure(b->fseq, fseq.size() * 4)) || (rc = ensure(b->ffrm, ffrm.size() * 4)) ||
+        (rc = ensure(b->maps, sizeof(MapSet) * n)))
+        return fail(rc);
+    size_t po = 0, co = 0;
+    std::vector<MapSet> maps(n);
+    for (int i = 0; i < n; ++i) {
+        const sme_sequence& x = seqs[i];
+        SeqDesc& e = d[i];
+        e.luma = x.luma;
+        e.alpha = x.alpha;
+        e.packed_w = (uint32_t*)b->packed.p + po;
+        e.cls_w = (uint8_t*)b->cls.p + co;
+        e.packed = e.packed_w;
+        e.cls = e.cls_w;
+        e.temporal_in = x.temporal_in;
+        e.seed = x.seed;
+        e.mv = x.out.mv;
+        e.cost = x.out.cost;
+        e.disp = x.out.disp;
+        e.iters = x.out.iters;
+        e.npos = x.out.npos;
+        e.out_cls = x.out.mb_class;
+        e.sse_mb = x.out.sse_mb;
+        e.sse = x.out.sse;
+        e.pred = x.out.pred;
+        po += (size_t)e.F * e.H * e.Wp;
+        co += (size_t)e.F * e.M;
+        Geom g{e.W, e.H, e.M, e.MBW, e.MBH, e.Wp};
+        if ((rc = encode_pair_maps(&maps[i], x.luma, e.packed_w, g, e.F, b->m.S))) return fail(rc);
+    }
+    // Per-MB schedule: every MB of every sequence by wavefront step.
+    std::vector<int> sched((size_t)gid), sseq((size_t)gid);
+    size_t k = 0;
+    for (int t = 0; t < max_steps; ++t)
+        for (int i = 0; i < n; ++i) {
+            const SeqDesc& e = d[i];
+            for (int pr = 0; pr < e.P && pr <= t; ++pr)
+                for (int v = 0; v < e.MBH; ++v) {
+                    const int u = t - 2 * v - pr;
+                    if (u < 0) break;
+                    if (u < e.MBW) {
+                        sched[k] = e.gid_base + pr * e.M + v * e.MBW + u;
+                        sseq[k] = i;
+                        ++k;
+                    }
+                }
+        }
+    if (k != (size_t)gid) return fail(SME_ERR_STATE);
+    // Per-pair schedule: pair k of every sequence before pair k+1 of any.
+    std::vector<int> useq, upair;
+    int max_p = 0;
+    for (const SeqDesc& e : d) max_p = std::max(max_p, e.P);
+    for (int pr = 0; pr < max_p; ++pr)
+        for (int i = 0; i < n; ++i)
+            if (pr < d[i].P) {
+                useq.push_back(i);
+                upair.push_back(pr);
+            }
+    if ((rc = ensure(b->sched, sched.size() * 4)) || (rc = ensure(b->sched_seq, sseq.size() * 4)) ||
+        (rc = ensure(b->unit_seq, useq.size() * 4)) || (rc = ensure(b->unit_pair, upair.size() * 4)))
+        return fail(rc);
+    if (cudaMemcpy(b->descs.p, d.data(), sizeof(SeqDesc) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->maps.p, maps.data(), sizeof(MapSet) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->fseq.p, fseq.data(), fseq.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->ffrm.p, ffrm.data(), ffrm.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->sched.p, sched.data(), sched.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->sched_seq.p, sseq.data(), sseq.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->unit_seq.p, useq.data(), useq.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->unit_pair.p, upair.data(), upair.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SME_ERR_CUDA);
+    }
+    *out = b;
+    return SME_OK;
+}
+
+int sme_batch_tune(sme_batch* b, int trials)
+{
+    if (!b || trials < 1) return SME_ERR_ARG;
+    batch_drop_graph(b);
+    float best = -1.0f;
+    ExecCfg pick = b->cfg;
+    for (const ExecCfg& e : kTuneCandidates) {
+        b->cfg = e;
+        if (batch_enqueue(b, b->stream) != SME_OK || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        const float ms = time_runs(b->stream, trials, [&] { return batch_enqueue(b, b->stream); });
+        if (batch_read_status(b) != SME_OK) continue;
+        if (ms > 0.0f && (best < 0.0f || ms < best)) {
+            best = ms;
+            pick = e;
+        }
+    }
+    b->cfg = pick;
+    b->tuned_ms = best > 0.0f ? best : 0.0f;
+    batch_capture(b);
+    return best > 0.0f ? SME_OK : SME_ERR_CUDA;
+}
+
+int sme_batch_run(sme_batch* b)
+{
+    if (!b) return SME_ERR_ARG;
+    if (b->exec) return cuda_status(cudaGraphLaunch(b->exec, b->stream));
+    return batch_enqueue(b, b->stream);
+}
+
+int sme_batch_synchronize(sme_batch* b)
+{
+    if (!b) return SME_ERR_ARG;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SME_ERR_CUDA;
+    return batch_read_status(b);
+}
+
+int sme_batch_config(sme_batch* b, int* schedule, int* param, int* speculate, float* best_ms)
+{
+    if (!b) return SME_ERR_ARG;
+    if (schedule) *schedule = b->cfg.schedule;
+    if (param) *param = b->cfg.schedule == kSchedPair ? b->cfg.pair_warps : b->cfg.mb_ctas_per_sm;
+    if (speculate) *speculate = b->cfg.speculate;
+    if (best_ms) *best_ms = b->tuned_ms;
+    return SME_OK;
+}
+
+int sme_batch_destroy(sme_batch* b)
+{
+    if (!b) return SME_ERR_ARG;
+    cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    DevBuf* bufs[] = {&b->descs, &b->packed, &b->cls, &b->ready, &b->sched, &b->sched_seq, &b->unit_seq,
+                      &b->unit_pair, &b->fseq, &b->ffrm, &b->maps};
+    for (DevBuf* x : bufs) release(*x);
+    if (b->status) cudaFree(b->status);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
     return SME_OK;
 }
 

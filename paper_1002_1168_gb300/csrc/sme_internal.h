@@ -31,7 +31,7 @@ struct DevStatus {
     unsigned ticket;
     unsigned abort;
     int err;
-    unsigned pad;
+    unsigned epoch;  // stamp of the current launch's ready words, bumped by classify
 };
 
 // Method parameters shared by every sequence of a launch.
@@ -49,6 +49,9 @@ struct Geom {
 // = gid_base + k*M + mb; ready words are indexed by global MB id.
 struct SeqDesc {
     const uint8_t* luma;      // [F][H][W]
+    const uint8_t* alpha;     // [F][H][W]
+    uint32_t* packed_w;       // [F][H][Wp] (written by the classify launch)
+    uint8_t* cls_w;           // [F][M]     (written by the classify launch)
     const uint32_t* packed;   // [F][H][Wp]
     const uint8_t* cls;       // [F][M]
     const sme_mv* temporal_in;
@@ -62,9 +65,8 @@ struct SeqDesc {
     uint32_t* sse_mb;
     unsigned long long* sse;  // [P]
     uint8_t* pred;
-    int W, H, MBW, MBH, M, Wp, P, rd;
+    int W, H, MBW, MBH, M, Wp, P, rd, F;
     int gid_base;
-    int pad;
 };
 
 struct ClassifyArgs {
@@ -79,6 +81,15 @@ struct ClassifyArgs {
     SeqDesc desc;
 };
 
+// Classification of many sequences in one launch: block (x, g) handles MB
+// row x of global frame g = (sequence fseq[g], frame ffrm[g]).
+struct ClassifyBatchArgs {
+    const SeqDesc* seqs;
+    const int* fseq;
+    const int* ffrm;
+    DevStatus* status;
+};
+
 struct MeArgs {
     const SeqDesc* seqs;      // [nseq] in device memory
     const int* sched;         // per-MB schedule: ticket -> global MB id, by wavefront step
@@ -91,7 +102,6 @@ struct MeArgs {
     unsigned long long* ready;  // [total] (epoch << 32) | packed vector
     DevStatus* status;
     Method m;
-    unsigned epoch;
     int total;
     int fault_ticket;
     int speculate;
@@ -122,6 +132,7 @@ struct QueryArgs {
 
 // Launchers (sme_kernels.cu).  Return cudaSuccess or the launch error.
 cudaError_t launch_classify(const Geom& g, const ClassifyArgs& a, cudaStream_t s);
+cudaError_t launch_classify_batch(const ClassifyBatchArgs& a, int max_mbh, int total_frames, cudaStream_t s);
 cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s);
 // `maps` points to 4 CUtensorMaps (128-byte aligned): luma window box, current
 // block box, packed-alpha reference strip, packed-alpha current BAB.

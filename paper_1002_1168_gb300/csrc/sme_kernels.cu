@@ -529,6 +529,8 @@ __global__ void __launch_bounds__(256) classify_pack_kernel(const Geom g, const 
         if (a.status && tid == 0) {
             a.status->ticket = 0;
             a.status->abort = 0;
+            const unsigned e = a.status->epoch + 1u;
+            a.status->epoch = e ? e : 1u;
         }
         if (a.desc_out && tid == 0) *a.desc_out = a.desc;
         if (a.sse)
@@ -560,6 +562,62 @@ __global__ void __launch_bounds__(256) classify_pack_kernel(const Geom g, const 
     for (int s = tid; s < segs; s += blockDim.x) {
         const unsigned n = cnt[s];
         a.cls[(size_t)f * g.M + v * g.MBW + s] =
+            (uint8_t)(n == 0 ? SME_TRANSPARENT : (n == 256 ? SME_OPAQUE : SME_BOUNDARY));
+    }
+}
+
+// One BAB row segment: 16 alpha bytes -> 16-bit mask.
+__device__ __forceinline__ unsigned bab_bits16(const uint8_t* p)
+{
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+    const unsigned w[4] = {q.x, q.y, q.z, q.w};
+    unsigned m = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const unsigned nz = __vcmpne4(w[b], 0u) & 0x01010101u;
+        m |= ((nz | (nz >> 7) | (nz >> 14) | (nz >> 21)) & 0xfu) << (4 * b);
+    }
+    return m;
+}
+
+// Fig. 1 "Block_Type" for every frame of every sequence of a batch (same
+// arithmetic as classify_pack_kernel, geometry from the descriptors).  Block
+// (0,0) also starts the launch (status words, epoch); the first row block of
+// each sequence's first frame zeroes that sequence's SSE outputs.
+__global__ void __launch_bounds__(256) classify_batch_kernel(const ClassifyBatchArgs a)
+{
+    __shared__ unsigned cnt[kMaxDim / 16];
+    const int v = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
+    if (v == 0 && g == 0 && tid == 0) {
+        a.status->ticket = 0;
+        a.status->abort = 0;
+        const unsigned e = a.status->epoch + 1u;
+        a.status->epoch = e ? e : 1u;
+    }
+    const SeqDesc* sd = a.seqs + a.fseq[g];
+    const int f = a.ffrm[g];
+    const int W = sd->W, H = sd->H, MBW = sd->MBW, Wp = sd->Wp;
+    if (v >= sd->MBH) return;
+    if (v == 0 && f == 0 && sd->sse)
+        for (int i = tid; i < sd->P; i += blockDim.x) sd->sse[i] = 0ull;
+    for (int i = tid; i < MBW; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const uint8_t* al = sd->alpha + (size_t)f * W * H + (size_t)v * 16 * W;
+    uint16_t* pk = reinterpret_cast<uint16_t*>(sd->packed_w + ((size_t)f * H + v * 16) * Wp);
+    const int hw = 2 * Wp;
+    for (int it = tid; it < 16 * hw; it += blockDim.x) {
+        const int r = it / hw, sg = it - r * hw;
+        unsigned m = 0;
+        if (sg < MBW) {
+            m = bab_bits16(al + (size_t)r * W + 16 * sg);
+            atomicAdd(&cnt[sg], (unsigned)__popc(m));
+        }
+        pk[(size_t)r * hw + sg] = (uint16_t)m;
+    }
+    __syncthreads();
+    for (int sg = tid; sg < MBW; sg += blockDim.x) {
+        const unsigned n = cnt[sg];
+        sd->cls_w[(size_t)f * sd->M + v * MBW + sg] =
             (uint8_t)(n == 0 ? SME_TRANSPARENT : (n == 256 ? SME_OPAQUE : SME_BOUNDARY));
     }
 }
@@ -909,7 +967,8 @@ __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
     const int h = m.h, pitch = win_pitch(m.S);
     uint8_t* win = smem + (size_t)wid * warp_smem(m.S);
     int* slog = reinterpret_cast<int*>(win + win_bytes(m.S));
-    const unsigned long long tag = (unsigned long long)a.epoch << 32;
+    const unsigned epoch = ld_relaxed(&a.status->epoch);
+    const unsigned long long tag = (unsigned long long)epoch << 32;
     __shared__ float s_rcp[512];
     fill_rcp(s_rcp);
     __syncthreads();
@@ -1040,7 +1099,7 @@ __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
                     spec = true;
                 }
             }
-            if (lane < 4 && !res_l && (unsigned)(w >> 32) == a.epoch) {
+            if (lane < 4 && !res_l && (unsigned)(w >> 32) == epoch) {
                 const int kk = (int)(unsigned)w;
                 key = pack_mv(clampi(mv_x(kk), V.lox, V.hix), clampi(mv_y(kk), V.loy, V.hiy));
                 res_l = true;
@@ -1346,7 +1405,8 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
     int* rowmv = reinterpret_cast<int*>(smem + L.rows_off);
     int* prog = reinterpret_cast<int*>(smem + L.prog_off);
     int* s_unit = reinterpret_cast<int*>(smem + L.unit_off);
-    const unsigned long long tag = (unsigned long long)a.epoch << 32;
+    const unsigned epoch = ld_relaxed(&a.status->epoch);
+    const unsigned long long tag = (unsigned long long)epoch << 32;
     const int lx = cs + 8 * (lane & 1), ly = S + (lane >> 1);  // lane's first pixel in the window
 
     __shared__ float s_rcp[512];
@@ -1454,8 +1514,8 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
                     if (lane == 3) {
                         if (k > 0) {
                             unsigned val = (unsigned)tcur;
-                            if ((unsigned)(tcur >> 32) != a.epoch)
-                                ok = wait_ready(a.ready + gid - M, a.epoch, a.status, a.timeout_ns, val);
+                            if ((unsigned)(tcur >> 32) != epoch)
+                                ok = wait_ready(a.ready + gid - M, epoch, a.status, a.timeout_ns, val);
                             key = (int)val;
                         } else if (sd->temporal_in) {
                             key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
@@ -1639,6 +1699,12 @@ cudaError_t launch_classify(const Geom& g, const ClassifyArgs& a, cudaStream_t s
 {
     dim3 grid(g.MBH, a.n_frames);
     classify_pack_kernel<<<grid, 256, 0, s>>>(g, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_batch(const ClassifyBatchArgs& a, int max_mbh, int total_frames, cudaStream_t s)
+{
+    classify_batch_kernel<<<dim3(max_mbh, total_frames), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -182,6 +182,9 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
 
     SeqDesc d{};
     d.luma = luma;
+    d.alpha = alpha;
+    d.packed_w = packed;
+    d.cls_w = cls;
     d.packed = packed;
     d.cls = cls;
     d.temporal_in = temporal_in;
@@ -203,6 +206,7 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
     d.Wp = g.Wp;
     d.P = P;
     d.rd = rd;
+    d.F = F;
     d.gid_base = 0;
 
     ClassifyArgs ca{};
@@ -224,7 +228,6 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
     a.ready = ready;
     a.status = status;
     a.m = mth;
-    a.epoch = 1;
     a.total = (int)PM;
     a.fault_ticket = -1;
     a.speculate = 1;

@@ -28,7 +28,9 @@ EXPORTS = [
     "sme_estimate_sequence_host", "sme_set_reference", "sme_set_current", "sme_estimate",
     "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field",
     "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
-    "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_debug_set_fault",
+    "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_autotune",
+    "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
+    "sme_batch_destroy", "sme_debug_set_fault",
 ]
 
 
@@ -50,6 +52,11 @@ class Outputs(C.Structure):
     _fields_ = [("mv", C.c_void_p), ("cost", C.c_void_p), ("disp", C.c_void_p),
                 ("iters", C.c_void_p), ("npos", C.c_void_p), ("mb_class", C.c_void_p),
                 ("sse_mb", C.c_void_p), ("sse", C.c_void_p), ("pred", C.c_void_p)]
+
+
+class Sequence(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("n_frames", C.c_int), ("luma", C.c_void_p),
+                ("alpha", C.c_void_p), ("temporal_in", C.c_void_p), ("seed", C.c_void_p), ("out", Outputs)]
 
 
 _LIB = None
@@ -92,6 +99,14 @@ def _lib():
             "sme_profile_end": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "sme_estimate_sequence_noalloc": (i, [C.POINTER(Params), vp, vp, i, vp, vp, C.POINTER(Outputs), vp]),
             "sme_set_option": (i, [vp, i, i]),
+            "sme_autotune": (i, [vp, vp, vp, i, C.POINTER(Outputs), i]),
+            "sme_batch_create": (i, [ip, C.POINTER(Params), C.POINTER(Sequence), i, vp]),
+            "sme_batch_tune": (i, [vp, i]),
+            "sme_batch_run": (i, [vp]),
+            "sme_batch_synchronize": (i, [vp]),
+            "sme_batch_config": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_float)]),
+            "sme_batch_destroy": (i, [vp]),
             "sme_debug_set_fault": (i, [vp, i, C.c_longlong]),
         }
         for name, (res, args) in sig.items():
@@ -286,6 +301,16 @@ class Estimator:
         self.set_option(SME_OPT_SCHEDULE, SCHEDULES[name])
         self.set_option(SME_OPT_PAIR_WARPS, pair_warps)
 
+    def autotune(self, luma, alpha, out=None, trials=3, want=("cost", "disp", "iters", "npos", "mb_class", "sse")):
+        """Pick the fastest execution configuration for this sequence shape."""
+        F = luma.shape[0]
+        if out is None:
+            out = self._alloc_outputs(F - self.ref_distance, want, luma.device)
+        st = self._outputs_struct(out)
+        _check(_lib().sme_autotune(self._bind(), _ptr(luma), _ptr(alpha), F, C.byref(st), int(trials)),
+               "sme_autotune")
+        return out
+
     def profile_begin(self, max_calls):
         _check(_lib().sme_profile_begin(self._h, int(max_calls)), "sme_profile_begin")
 
@@ -297,3 +322,69 @@ class Estimator:
 
     def debug_set_fault(self, skip_ticket=-1, timeout_ns=0):
         _check(_lib().sme_debug_set_fault(self._h, int(skip_ticket), int(timeout_ns)), "sme_debug_set_fault")
+
+
+class Batch:
+    """Many sequences (luma, alpha CUDA tensors [F, H, W], uneven sizes) in one
+    persistent launch.  Outputs are allocated per sequence and reused by every
+    run (the work is replayed from a CUDA graph once tuned)."""
+
+    def __init__(self, luma_list, alpha_list, search_range=16, subpel=2, theta=2.0, epsilon=1.0,
+                 max_iters=8, ref_distance=1, want=("cost", "disp", "iters", "npos", "mb_class", "sse"),
+                 temporal_list=None, seed_list=None):
+        import torch
+
+        self.torch = torch
+        lib = _lib()
+        W0, H0 = luma_list[0].shape[2], luma_list[0].shape[1]
+        self.params = Params(W0, H0, search_range, subpel, theta, epsilon, max_iters, ref_distance)
+        self.inputs = list(zip(luma_list, alpha_list))
+        self.outputs = []
+        n = len(luma_list)
+        seqs = (Sequence * n)()
+        self._keep = []
+        for i, (l, a) in enumerate(self.inputs):
+            F, H, W = l.shape
+            est_like = Estimator.__new__(Estimator)
+            est_like.torch, est_like.M, est_like.height, est_like.width = torch, (W // 16) * (H // 16), H, W
+            out = Estimator._alloc_outputs(est_like, F - ref_distance, want, l.device)
+            self.outputs.append(out)
+            tmp = None if temporal_list is None else temporal_list[i]
+            sd = None if seed_list is None else seed_list[i]
+            self._keep += [tmp, sd]
+            seqs[i] = Sequence(W, H, F, l.data_ptr(), a.data_ptr(), None if tmp is None else tmp.data_ptr(),
+                               None if sd is None else sd.data_ptr(), Estimator._outputs_struct(out))
+        h = C.c_void_p()
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        _check(lib.sme_batch_create(C.byref(h), C.byref(self.params), seqs, n, stream), "sme_batch_create")
+        self._h = h
+
+    def tune(self, trials=3):
+        _check(_lib().sme_batch_tune(self._h, int(trials)), "sme_batch_tune")
+
+    def run(self, sync=True):
+        _check(_lib().sme_batch_run(self._h), "sme_batch_run")
+        if sync:
+            self.synchronize()
+        return self.outputs
+
+    def synchronize(self):
+        _check(_lib().sme_batch_synchronize(self._h), "sme_batch_synchronize")
+
+    def config(self):
+        s_, p_, sp_, ms = C.c_int(), C.c_int(), C.c_int(), C.c_float()
+        _check(_lib().sme_batch_config(self._h, C.byref(s_), C.byref(p_), C.byref(sp_), C.byref(ms)),
+               "sme_batch_config")
+        name = {v: k for k, v in SCHEDULES.items()}[s_.value]
+        return {"schedule": name, "param": p_.value, "speculate": sp_.value, "tuned_ms": ms.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().sme_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

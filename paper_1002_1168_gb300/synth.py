@@ -42,6 +42,19 @@ class Texture:
             s += self.amp[i] * np.sin(self.kx[i] * x + self.ky[i] * y + self.phase[i])
         return 127.5 + 127.5 * s / self.amp.sum()
 
+    def grid(self, xs, ys, ca=1.0, sa=0.0, scale=1.0):
+        """The texture at local coordinates q = R(-angle) (p - origin) / scale
+        for the grid p = (xs[i], ys[j]) given relative to the origin; each
+        wave sin(kx qx + ky qy + phase) = sin(al x + ph) cos(be y) +
+        cos(al x + ph) sin(be y) is built from 1-D tables."""
+        al = (self.kx * ca + self.ky * sa) / scale
+        be = (self.ky * ca - self.kx * sa) / scale
+        ax = np.outer(al, xs) + self.phase[:, None]           # [n, W]
+        by = np.outer(be, ys)                                 # [n, H]
+        left = np.concatenate([(self.amp[:, None] * np.cos(by)).T, (self.amp[:, None] * np.sin(by)).T], axis=1)
+        right = np.concatenate([np.sin(ax), np.cos(ax)], axis=0)
+        return 127.5 + (127.5 / self.amp.sum()) * (left @ right)
+
 
 @dataclass
 class MovingObject:
@@ -99,18 +112,31 @@ class Sequence:
 
 
 def render(W, H, F, background: Texture, bg_offsets, objects, noise_sigma, rng) -> tuple:
-    """Composite background + objects per frame, add noise, return (luma, alpha)."""
-    Y, X = np.mgrid[0:H, 0:W].astype(np.float64)
+    """Composite background + objects per frame, add noise, return (luma, alpha).
+    Object masks and textures are evaluated inside each object's bounding box."""
+    xs, ys = np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64)
     luma = np.empty((F, H, W), np.uint8)
     alpha = np.zeros((len(objects), F, H, W), np.uint8)
     for t in range(F):
         ox, oy = bg_offsets[t]
-        img = background(X - ox, Y - oy)
+        img = background.grid(xs - ox, ys - oy)
         for i, ob in enumerate(objects):
-            qx, qy = ob.local(t, X, Y)
+            cx, cy = ob.centers[t]
+            ang, sc = ob.angles[t], ob.scales[t]
+            rad = max(ob.a, ob.b) * (1.0 + float(np.abs(ob.harm_c).sum())) * sc + 2.0
+            x0, x1 = max(0, int(np.floor(cx - rad))), min(W, int(np.ceil(cx + rad)) + 1)
+            y0, y1 = max(0, int(np.floor(cy - rad))), min(H, int(np.ceil(cy + rad)) + 1)
+            if x0 >= x1 or y0 >= y1:
+                continue
+            bx, by = xs[x0:x1] - cx, ys[y0:y1] - cy
+            ca, sa = np.cos(-ang), np.sin(-ang)
+            qx = (ca * bx[None, :] - sa * by[:, None]) / sc
+            qy = (sa * bx[None, :] + ca * by[:, None]) / sc
             m = ob.inside(qx, qy)
-            img = np.where(m, ob.texture(qx, qy), img)
-            alpha[i, t] = np.where(m, 255, 0).astype(np.uint8)
+            tex = ob.texture.grid(bx, by, ca, sa, sc)
+            sub = img[y0:y1, x0:x1]
+            img[y0:y1, x0:x1] = np.where(m, tex, sub)
+            alpha[i, t, y0:y1, x0:x1] = np.where(m, 255, 0).astype(np.uint8)
         if noise_sigma > 0:
             img = img + rng.normal(0.0, noise_sigma, img.shape)
         luma[t] = np.clip(np.rint(img), 0, 255).astype(np.uint8)

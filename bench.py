@@ -113,6 +113,12 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# DRAM bytes (read + write) of one me_kernel launch on this workload, from the
+# ncu capture summarised in profiles/me_kernel_cif30_halfpel.md (set to None
+# whenever the kernel changes until it is captured again).
+ME_KERNEL_TRAFFIC_BYTES = 3502592 + 15872
+
+
 def algorithmic_bytes(P, M, F):
     """Minimum DRAM bytes of one ME launch: every luma frame once (each frame
     is the current frame of one pair and the reference of the next), the packed
@@ -168,6 +174,79 @@ def cpu_baseline(seq, budget_s=10.0):
             "sample": f"{n} full passes over the workload ({n * P * p.mbs} MBs, {dt:.1f} s), single-threaded C"}, res
 
 
+def measure_batch(sme, torch, args, rank, dist):
+    """Secondary measurement: 64 sequences of uneven size (16 QCIF, 24 CIF,
+    16 4CIF, 8 1920x1088), 10 frames, 1-4 objects each (one VOP per object),
+    |v| <= 16, S=16, half-pel, estimated in one persistent launch replayed
+    from a CUDA graph.  Inputs (0.9 GB) exceed L2, so no flush is needed."""
+    import oracle as O
+    from paper_1002_1168_gb300 import synth
+
+    t0 = time.perf_counter()
+    sizes = {"full": None, "hd8": [(1920, 1088)] * 8}[args.batch_preset]
+    seqs = synth.batch_sequences(seed=1003 + 100 * rank, frames=10, sizes=sizes)
+    gen_s = time.perf_counter() - t0
+    lumas, alphas, host = [], [], []
+    for sq in seqs:
+        lt = torch.from_numpy(sq.luma).cuda()
+        for j in range(sq.alpha.shape[0]):
+            lumas.append(lt)
+            alphas.append(torch.from_numpy(sq.alpha[j]).cuda())
+            host.append((sq, j))
+    b = sme.Batch(lumas, alphas, search_range=16, subpel=2, want=("cost", "iters", "npos", "mb_class", "sse"))
+    b.tune(trials=3)
+    cfg = b.config()
+    total = sum((l.shape[0] - 1) * (l.shape[1] // 16) * (l.shape[2] // 16) for l in lumas)
+    steps = max(3, args.steps // 5)
+    for _ in range(2):
+        b.run(sync=False)
+    b.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(steps):
+        starts[i].record()
+        b.run(sync=False)
+        ends[i].record()
+    torch.cuda.synchronize()
+    b.synchronize()
+    ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)) / steps
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ws = dist.get_world_size() if dist else 1
+    # parity on a sample of VOP sequences (every 7th, all frame sizes), about
+    # args.cpu_seconds of oracle time; the CPU baseline is that same sample
+    exact, cpu_mbs, cpu_s, sample = True, 0, 0.0, []
+    for i in list(range(0, len(host), 7)) + list(range(1, len(host), 7)):
+        if cpu_s >= args.cpu_seconds:
+            break
+        sq, j = host[i]
+        tc = time.perf_counter()
+        o = O.estimate_sequence(O.OracleParams(sq.width, sq.height, 16, 2), sq.luma, sq.alpha[j])
+        cpu_s += time.perf_counter() - tc
+        cpu_mbs += o["mv"].shape[0] * o["mv"].shape[1]
+        sample.append(i)
+        g = b.outputs[i]
+        exact &= bool(np.array_equal(g["mv"].cpu().numpy(), o["mv"]) and
+                      np.array_equal(g["sse"].cpu().numpy().view(np.uint64), o["sse"]) and
+                      np.array_equal(g["cost"].cpu().numpy().view(np.uint32), o["cost"]))
+    nt = sum(int((o_["mb_class"] > 0).sum().item()) for o_ in b.outputs)
+    b.close()
+    name = {"full": "64 sequences (16 QCIF, 24 CIF, 16 4CIF, 8 1920x1088)",
+            "hd8": "8 sequences of 1920x1088"}[args.batch_preset]
+    return {"workload": f"{name}, 10 frames, {len(lumas)} VOPs, half-pel, S=16", "mb_per_run": total,
+            "value": ws * total / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "runs": steps,
+            "non_transparent_frac": nt / total, "config": cfg, "generation_s": gen_s,
+            "bit_exact_vs_oracle_sample": exact, "sample_sequences": len(sample),
+            "cpu_baseline": {"value": cpu_mbs / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(sample)} of the batch's VOP sequences (every 7th), "
+                                       f"{cpu_mbs} MBs, {cpu_s:.1f} s, single-threaded C"}}
+
+
 def run_ours(args):
     import torch
 
@@ -185,11 +264,14 @@ def run_ours(args):
     seq = workload(rank)
     P, M = FRAMES - 1, (W // 16) * (H // 16)
     est = sme.Estimator(W, H, search_range=S, subpel=SUBPEL)
-    est.set_schedule(args.schedule)
     luma = torch.from_numpy(seq.luma).cuda()
     alpha = torch.from_numpy(seq.alpha[0]).cuda()
     out = est._alloc_outputs(P, OUT_FIELDS, luma.device)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=luma.device)
+    if args.schedule == "auto":
+        est.autotune(luma, alpha, out=out, trials=5)  # outside the timed region
+    else:
+        est.set_schedule(args.schedule)
 
     for _ in range(max(args.warmup, 3)):
         est.estimate_sequence(luma, alpha, out=out, sync=False)
@@ -244,6 +326,10 @@ def run_ours(args):
     h2d = int(hl.numel() + ha.numel())
     d2h = int(sum(v.numel() * v.element_size() for v in hout.values()))
 
+    batched = None
+    if not args.no_batch:
+        batched = measure_batch(sme, torch, args, rank, dist)
+
     if rank != 0:
         est.close()
         if dist:
@@ -278,7 +364,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "me_kernel",
+                     "frac": achieved / hbm, "traffic": ME_KERNEL_TRAFFIC_BYTES, "kernel": "me_kernel",
                      "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg,
                      "avg_launch_ms": me_avg_s * 1e3, "classify_avg_ms": cls_ms / max(calls, 1),
                      "critical_path_steps": (W // 16 - 1) + 2 * (H // 16 - 1) + P},
@@ -289,6 +375,7 @@ def run_ours(args):
                     "positions_per_mb": float(res["npos"][cls > 0].mean()),
                     "psnr_db_mean": float(np.mean(psnr)), "learned_seeded": None},
         "wall_s_timed": wall,
+        "batched": batched,
     }
     print(json.dumps(line))
     est.close()
@@ -304,9 +391,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--schedule", default="auto", choices=["auto", "pair", "mb"])
+    ap.add_argument("--no-batch", action="store_true", help="skip the secondary batched measurement")
+    ap.add_argument("--batch-only", action="store_true", help="only the batched measurement (profiling)")
+    ap.add_argument("--batch-preset", default="full", choices=["full", "hd8"],
+                    help="batched workload: the 64-sequence batch, or 8 HD sequences (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch_only:
+        import torch
+        from paper_1002_1168_gb300 import build as cuda_build
+        from paper_1002_1168_gb300 import sme
+
+        cuda_build.build()
+        print(json.dumps({"batched": measure_batch(sme, torch, args, 0, None)}))
     else:
         run_ours(args)
 

@@ -236,7 +236,56 @@ static uint32_t mb_cost(const orc_params* P, int cls, const uint8_t* ref, const 
     return orc_texture_sad(ref, cur, P->width, P->subpel, X0, Y0, dx, dy);
 }
 
-/* One frame pair, Fig. 1: raster scan over the MB grid (Sec. 3.1). */
+/* Sec. 3.2 pixel recursive search from (dx, dy) with SAD c: gradient step,
+ * proposal, eight directions (Fig. 4), repeated while the SAD drops, at most
+ * max_iters steps.  Updates the vector and SAD, returns the steps taken and
+ * the last update in last[2]; evaluated positions go to ps. */
+static int prs_search(const orc_params* P, const uint8_t* ref, const uint8_t* cur, int X0, int Y0,
+                      int lox, int hix, int loy, int hiy, int* pdx, int* pdy, uint32_t* pc,
+                      float last[2], pos_set* ps)
+{
+    const int W = P->width, h = P->subpel;
+    int dx = *pdx, dy = *pdy, k = 0;
+    uint32_t c = *pc;
+    last[0] = last[1] = 0.0f;
+    while (k < P->max_iters) {
+        ++k;
+        orc_gradient_step(P, ref, cur, X0, Y0, dx, dy, last);
+        int qx = iclamp(dx + (int)roundf((float)h * last[0]), lox, hix);
+        int qy = iclamp(dy + (int)roundf((float)h * last[1]), loy, hiy);
+        if (qx != dx || qy != dy) {
+            uint32_t cq = orc_texture_sad(ref, cur, W, h, X0, Y0, qx, qy);
+            pos_note(ps, qx, qy);
+            if (cq < c) { dx = qx; dy = qy; c = cq; continue; }
+        }
+        /* Fig. 4: the eight directions at one MV unit */
+        int bx = dx, by = dy;
+        uint32_t bcost = c;
+        for (int jj = -1; jj <= 1; ++jj)
+            for (int ii = -1; ii <= 1; ++ii) {
+                if (!ii && !jj) continue;
+                int nx = iclamp(dx + ii, lox, hix), ny = iclamp(dy + jj, loy, hiy);
+                if (nx == dx && ny == dy) continue;
+                uint32_t cn = orc_texture_sad(ref, cur, W, h, X0, Y0, nx, ny);
+                pos_note(ps, nx, ny);
+                if (cn < bcost) { bcost = cn; bx = nx; by = ny; }
+            }
+        if (bcost < c) { dx = bx; dy = by; c = bcost; continue; }
+        break;
+    }
+    *pdx = dx;
+    *pdy = dy;
+    *pc = c;
+    return k;
+}
+
+/* One frame pair, Fig. 1: raster scan over the MB grid (Sec. 3.1).
+ * With seeds (the learned proposal), the seed is a fifth candidate after T;
+ * on an opaque MB whose seed strictly wins the candidate comparison, the
+ * pixel recursive search runs from the seed and from the best of A, B, C, T,
+ * and the seeded result is kept only if its final SAD is strictly lower (the
+ * plain search stays the fallback).  Steps and update are those of the kept
+ * search; the evaluated positions of both count. */
 int orc_estimate_pair(const orc_params* P, const uint8_t* ref, const uint8_t* cur,
                       const uint8_t* aref, const uint8_t* acur,
                       const orc_mv* temporal, const float* seed,
@@ -276,11 +325,12 @@ int orc_estimate_pair(const orc_params* P, const uint8_t* ref, const uint8_t* cu
             pos_set ps;
             ps.n = 0;
             int best = -1;
-            uint32_t bc = 0;
+            uint32_t bc = 0, costs[5] = {0, 0, 0, 0, 0};
             for (int k = 0; k < nc; ++k) {
                 cx[k] = iclamp(cx[k], lox, hix);
                 cy[k] = iclamp(cy[k], loy, hiy);
                 uint32_t c = mb_cost(P, cls, ref, cur, aref, acur, X0, Y0, cx[k], cy[k]);
+                costs[k] = c;
                 pos_note(&ps, cx[k], cy[k]);
                 if (best < 0 || c < bc) { best = k; bc = c; }
             }
@@ -288,32 +338,22 @@ int orc_estimate_pair(const orc_params* P, const uint8_t* ref, const uint8_t* cu
             uint32_t c = bc;
             float last[2] = {0.0f, 0.0f};
             int k = 0;
-            if (cls == ORC_OPAQUE) {
-                while (k < P->max_iters) {
-                    ++k;
-                    orc_gradient_step(P, ref, cur, X0, Y0, dx, dy, last);
-                    int qx = iclamp(dx + (int)roundf((float)h * last[0]), lox, hix);
-                    int qy = iclamp(dy + (int)roundf((float)h * last[1]), loy, hiy);
-                    if (qx != dx || qy != dy) {
-                        uint32_t cq = orc_texture_sad(ref, cur, W, h, X0, Y0, qx, qy);
-                        pos_note(&ps, qx, qy);
-                        if (cq < c) { dx = qx; dy = qy; c = cq; continue; }
-                    }
-                    /* Fig. 4: the eight directions at one MV unit */
-                    int bx = dx, by = dy;
-                    uint32_t bcost = c;
-                    for (int jj = -1; jj <= 1; ++jj)
-                        for (int ii = -1; ii <= 1; ++ii) {
-                            if (!ii && !jj) continue;
-                            int nx = iclamp(dx + ii, lox, hix), ny = iclamp(dy + jj, loy, hiy);
-                            if (nx == dx && ny == dy) continue;
-                            uint32_t cn = orc_texture_sad(ref, cur, W, h, X0, Y0, nx, ny);
-                            pos_note(&ps, nx, ny);
-                            if (cn < bcost) { bcost = cn; bx = nx; by = ny; }
-                        }
-                    if (bcost < c) { dx = bx; dy = by; c = bcost; continue; }
-                    break;
+            if (cls == ORC_OPAQUE && best == 4) {
+                /* the seed won: search from it and from the plain winner */
+                int pb = 0;
+                for (int q = 1; q < 4; ++q)
+                    if (costs[q] < costs[pb]) pb = q;
+                int pdx = cx[pb], pdy = cy[pb];
+                uint32_t pc = costs[pb];
+                float plast[2];
+                int pk = prs_search(P, ref, cur, X0, Y0, lox, hix, loy, hiy, &pdx, &pdy, &pc, plast, &ps);
+                k = prs_search(P, ref, cur, X0, Y0, lox, hix, loy, hiy, &dx, &dy, &c, last, &ps);
+                if (!(c < pc)) { /* the plain search is kept unless the seeded one is strictly better */
+                    dx = pdx; dy = pdy; c = pc; k = pk;
+                    last[0] = plast[0]; last[1] = plast[1];
                 }
+            } else if (cls == ORC_OPAQUE) {
+                k = prs_search(P, ref, cur, X0, Y0, lox, hix, loy, hiy, &dx, &dy, &c, last, &ps);
             }
             mv[m].dx = (int16_t)dx;
             mv[m].dy = (int16_t)dy;

@@ -754,6 +754,99 @@ __device__ __forceinline__ bool prs_decide(const Method& m, const uint8_t* win, 
     return false;
 }
 
+// Sec. 3.2 pixel recursive search from (dx, dy): steps until neither the
+// proposal nor a neighbour lowers the SAD, at most K.  When use_first is set,
+// `first` is the already computed first step at the starting position.
+// Returns the steps taken; the last update goes to lastx/lasty.
+__device__ __forceinline__ int prs_run(const Method& m, const uint8_t* win, int pitch, int lx, int ly, const P8& c8,
+                                       const float (&ux)[8], const float (&uy)[8], int nx, int ny, const VRange& V,
+                                       int& dx, int& dy, unsigned& cost, P8& r8, float& lastx, float& lasty,
+                                       int* slog, int& nlog, int lane, bool use_first, const PrsStep& first)
+{
+    int iters = 0;
+    lastx = 0.0f;
+    lasty = 0.0f;
+    while (iters < m.K) {
+        const PrsStep st = (iters == 0 && use_first) ? first
+                                                     : prs_eval(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, dx, dy, r8, cost);
+        ++iters;
+        lastx = st.lastx;
+        lasty = st.lasty;
+        if (!prs_decide(m, win, pitch, lx, ly, c8, V, st, dx, dy, cost, r8, slog, nlog, lane)) break;
+    }
+    return iters;
+}
+
+// Opaque MB after the candidate comparison: the pixel recursive search from
+// the winner; when a learned seed (candidate 4) won strictly, the search runs
+// from it and from the best plain candidate, and the plain result is kept
+// unless the seeded one ends strictly lower.  cand/costs/cs8 are the
+// candidates in order A, B, C, T(, seed); best is the winning index.
+__device__ __forceinline__ void opaque_search(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
+                                              const P8& c8, const float (&ux)[8], const float (&uy)[8], int nx,
+                                              int ny, const VRange& V, const int (&cand)[5],
+                                              const unsigned (&costs)[5], const P8 (&cs8)[5], int nc, int best,
+                                              int* slog, int& nlog, int lane, bool spec, int spec_key,
+                                              const PrsStep& sp, MbResult& res)
+{
+    int dx = mv_x(cand[0]), dy = mv_y(cand[0]);
+    unsigned cost = costs[0];
+    P8 r8 = cs8[0];
+#pragma unroll
+    for (int c = 1; c < 5; ++c)
+        if (c == best) {
+            dx = mv_x(cand[c]);
+            dy = mv_y(cand[c]);
+            cost = costs[c];
+            r8 = cs8[c];
+        }
+    float lastx, lasty;
+    int iters;
+    if (nc == 5 && best == 4) {
+        int pb = 0;
+        unsigned pc = costs[0];
+#pragma unroll
+        for (int c = 1; c < 4; ++c)
+            if (costs[c] < pc) {
+                pb = c;
+                pc = costs[c];
+            }
+        int px = mv_x(cand[0]), py = mv_y(cand[0]);
+        P8 pr8 = cs8[0];
+#pragma unroll
+        for (int c = 1; c < 4; ++c)
+            if (c == pb) {
+                px = mv_x(cand[c]);
+                py = mv_y(cand[c]);
+                pr8 = cs8[c];
+            }
+        float plx, ply;
+        const int pit = prs_run(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, px, py, pc, pr8, plx, ply, slog, nlog,
+                                lane, spec && pack_mv(px, py) == spec_key, sp);
+        iters = prs_run(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, dx, dy, cost, r8, lastx, lasty, slog, nlog,
+                        lane, spec && pack_mv(dx, dy) == spec_key, sp);
+        if (!(cost < pc)) {
+            dx = px;
+            dy = py;
+            cost = pc;
+            r8 = pr8;
+            iters = pit;
+            lastx = plx;
+            lasty = ply;
+        }
+    } else {
+        iters = prs_run(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, dx, dy, cost, r8, lastx, lasty, slog, nlog,
+                        lane, spec && pack_mv(dx, dy) == spec_key, sp);
+    }
+    res.dx = dx;
+    res.dy = dy;
+    res.cost = cost;
+    res.r8 = r8;
+    res.iters = iters;
+    res.lastx = lastx;
+    res.lasty = lasty;
+}
+
 // Fig. 1 from the candidate comparison on: shape cost (boundary) or texture
 // SAD (opaque) of the candidates, first strict minimum, and on opaque MBs the
 // pixel recursive search of Sec. 3.2.  The candidates are already logged in
@@ -800,33 +893,19 @@ __device__ __forceinline__ MbResult search_mb(const Method& m, int cls, const ui
         warp_sum2(part[0], part[1], sad[0], sad[1]);
         warp_sum2(part[2], part[3], sad[2], sad[3]);
         sad[4] = nc > 4 ? __reduce_add_sync(kFull, part[4]) : 0u;
-        int best = cand[0];
+        int best = 0;
         cost = sad[0];
-        P8 r8 = cs8[0];
 #pragma unroll
         for (int c = 1; c < 5; ++c)
             if (c < nc && sad[c] < cost) {
                 cost = sad[c];
-                best = cand[c];
-                r8 = cs8[c];
+                best = c;
             }
-        dx = mv_x(best);
-        dy = mv_y(best);
-
-        // Sec. 3.2: pixel recursive search.
-        int iters = 0;
-        float lastx = 0.0f, lasty = 0.0f;
-        while (iters < m.K) {
-            ++iters;
-            const PrsStep st = prs_eval(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, dx, dy, r8, cost);
-            lastx = st.lastx;
-            lasty = st.lasty;
-            if (!prs_decide(m, win, pitch, lx, ly, c8, V, st, dx, dy, cost, r8, slog, nlog, lane)) break;
-        }
-        res.r8 = r8;
-        res.iters = iters;
-        res.lastx = lastx;
-        res.lasty = lasty;
+        PrsStep none;
+        opaque_search(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, sad, cs8, nc, best, slog, nlog, lane, false,
+                      0, none, res);
+        res.nlog = nlog;
+        return res;
     }
     res.dx = dx;
     res.dy = dy;
@@ -1129,40 +1208,33 @@ __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
 
         // First strict minimum in the order A, B, C, T (+ seed).
         MbResult r;
-        int best = cand[0];
-        unsigned cost = ccost[0];
-        P8 r8 = cs8[0];
+        int bi = 0;
+        unsigned bcost = ccost[0];
 #pragma unroll
         for (int c = 1; c < 5; ++c)
-            if (c < nc && ccost[c] < cost) {
-                cost = ccost[c];
-                best = cand[c];
-                r8 = cs8[c];
+            if (c < nc && ccost[c] < bcost) {
+                bcost = ccost[c];
+                bi = c;
             }
-        int dx = mv_x(best), dy = mv_y(best), nlog = nc, iters = 0;
-        float lastx = 0.0f, lasty = 0.0f;
-        if (cls == SME_BOUNDARY) r8 = ref8(win, pitch, lx, ly, dx, dy, h);  // prediction at the shape winner
+        int nlog = nc;
         if (cls == SME_OPAQUE) {
-            // Sec. 3.2: pixel recursive search (the first step may be the
-            // speculative one, taken at the same position).
-            while (iters < m.K) {
-                PrsStep st;
-                if (iters == 0 && spec && best == spec_key) st = sp;
-                else st = prs_eval(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, dx, dy, r8, cost);
-                ++iters;
-                lastx = st.lastx;
-                lasty = st.lasty;
-                if (!prs_decide(m, win, pitch, lx, ly, c8, V, st, dx, dy, cost, r8, slog, nlog, lane)) break;
-            }
+            // Sec. 3.2 (the first step may be the speculative one, taken at
+            // the same position).
+            opaque_search(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, ccost, cs8, nc, bi, slog, nlog, lane,
+                          spec, spec_key, sp, r);
+        } else {
+            int bk = cand[0];
+#pragma unroll
+            for (int c = 1; c < 5; ++c)
+                if (c == bi) bk = cand[c];
+            r.dx = mv_x(bk);
+            r.dy = mv_y(bk);
+            r.cost = bcost;
+            r.iters = 0;
+            r.lastx = r.lasty = 0.0f;
+            r.r8 = ref8(win, pitch, lx, ly, r.dx, r.dy, h);  // prediction at the shape winner
         }
-        r.dx = dx;
-        r.dy = dy;
-        r.cost = cost;
-        r.iters = iters;
         r.nlog = nlog;
-        r.lastx = lastx;
-        r.lasty = lasty;
-        r.r8 = r8;
 
         // ---- publish the vector first: it is on the dependency chain ----
         if (lane == 0) {

@@ -348,3 +348,17 @@ def test_argument_errors(sme):
                                      None, None, C.byref(out)) == 1  # no pair
     assert lib.sme_estimate(est._h, None) == 5  # no frames set
     est.close()
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_learned_seed_fallback_paths(sme, schedule):
+    """Seeds near the plain result (noisy): they win the candidate comparison
+    on some MBs, so both pixel-recursive searches and the fallback run."""
+    seq = synth.cif_sequence(seed=1002, frames=8)
+    p = O.OracleParams(352, 288, 16, 2)
+    plain = O.estimate_sequence(p, seq.luma, seq.alpha[0])
+    rng = np.random.default_rng(1)
+    seed = (plain["mv"].astype(np.float32) / 2 + rng.normal(0, 1.0, plain["mv"].shape)).astype(np.float32)
+    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, seed=seed, schedule=schedule)
+    assert_parity(g, o, p, seq.luma)
+    assert (o["mv"] != plain["mv"]).any(axis=-1).sum() > 0  # the seeds changed some results

@@ -308,3 +308,53 @@ def test_sequence_equals_chained_pairs_and_is_deterministic():
                             temporal=tmp)
         assert np.array_equal(r["mv"], o1["mv"][k])
         tmp = r["mv"]
+
+
+# ------------------------------------------------- learned-proposal seeds --
+def test_seed_at_a_plain_candidate_changes_nothing():
+    """A seed equal to the temporal candidate can never win strictly, so the
+    seeded run equals the plain one (same vectors, costs, steps, positions)."""
+    seq = synth.cif_sequence(frames=4)
+    p = O.OracleParams(352, 288, 16, 2)
+    plain = O.estimate_sequence(p, seq.luma, seq.alpha[0])
+    P, M = plain["mv"].shape[:2]
+    seed = np.zeros((P, M, 2), np.float32)
+    seed[1:] = plain["mv"][:-1].astype(np.float32) / 2  # T of pairs 1.. in pixels
+    seeded = O.estimate_sequence(p, seq.luma, seq.alpha[0], seed=seed)
+    for k in ("mv", "cost", "iters", "npos", "disp", "sse"):
+        assert np.array_equal(plain[k][1:], seeded[k][1:]), k
+
+
+def test_seeded_result_never_worse_on_an_isolated_mb():
+    """One MB per frame (no neighbours): whatever the seed, the kept search
+    ends with a SAD no larger than the plain search's."""
+    rng = np.random.default_rng(9)
+    worse = better = 0
+    for trial in range(60):
+        luma, alpha = synth.translated_pair(48, 48, rng.integers(-5, 6, 2), seed=trial, noise_sigma=2.0)
+        ref, cur = luma[0, 16:32, 16:32].copy(), luma[1, 16:32, 16:32].copy()
+        # a 16x16 frame has V = {0}; use 48x48 frames with the middle MB only opaque
+        a = np.zeros((2, 48, 48), np.uint8)
+        a[:, 16:32, 16:32] = 255
+        p = O.OracleParams(48, 48, 16, 2)
+        plain = O.estimate_pair(p, luma[0], luma[1], a[0], a[1])
+        seed = rng.normal(0, 6, (9, 2)).astype(np.float32)
+        s = O.estimate_pair(p, luma[0], luma[1], a[0], a[1], seed=seed)
+        assert s["cost"][4] <= plain["cost"][4]
+        better += s["cost"][4] < plain["cost"][4]
+    assert better > 0  # the seed path is taken sometimes
+
+
+def test_perfect_seed_recovers_translation():
+    """With a seed at the true vector every MB whose window contains it ends
+    at SAD 0 there, with no plain candidate in reach."""
+    W, H, sh = 128, 96, np.array([5, -6])
+    luma, alpha = synth.translated_pair(W, H, sh, seed=4)
+    p = O.OracleParams(W, H, 16, 2, max_iters=1)
+    seed = np.tile(-sh.astype(np.float32), (p.mbs, 1))
+    o = O.estimate_pair(p, luma[0], luma[1], alpha[0], alpha[1], seed=seed)
+    tgt = -sh * 2
+    for m in range(p.mbs):
+        lox, hix, loy, hiy = O.valid_range(W, H, 16, 16, 2, 16 * (m % 8), 16 * (m // 8))
+        if lox <= tgt[0] <= hix and loy <= tgt[1] <= hiy:
+            assert (o["mv"][m] == tgt).all() and o["cost"][m] == 0

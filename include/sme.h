@@ -256,6 +256,48 @@ int sme_batch_synchronize(sme_batch* b);
 int sme_batch_config(sme_batch* b, int* schedule, int* param, int* speculate, float* best_ms);
 int sme_batch_destroy(sme_batch* b);
 
+/* Learned seed proposal (no counterpart in the paper, whose seeds are the
+ * neighbour and temporal vectors of Sec. 3.1): a 5-layer 3x3 convolutional
+ * network, 32 channels, bfloat16 weights and activations with FP32
+ * accumulation on tensor cores, on a quarter-resolution grid (cell = 4x4
+ * pixels, MB = 4x4 cells).  Inputs per cell (16 channels, bfloat16): current
+ * and reference mean luma /255 - 0.5, their difference, the temporal
+ * candidate of the cell's MB in pixels / 16, zeros.  Output per MB: a seed
+ * (dx, dy) in pixels = 8 x the mean of output channels 0, 1 over its cells;
+ * pass the seeds to sme_estimate_sequence (`seed`), where they are a fifth
+ * candidate with the plain search as fallback.
+ *   Parameters (FP32, sme_seednet_param_count() floats): per layer the
+ *   weights [cout][3][3][cin] then the biases [cout]; channels
+ *   16, 32, 32, 32, 32, 16.  Training: Huber loss (1 px) between the seeds and
+ *   labels (pixels) over the MBs with mask != 0, averaged; Adam (0.9, 0.999,
+ *   1e-8) on FP32 master weights.
+ *   sme_seednet_create    max_cells = largest n * (W/4) * (H/4) used later.
+ *   sme_seednet_features  one frame pair of a [F][H][W] luma sequence (device)
+ *                         -> feat [(H/4)][(W/4)][16] bfloat16 (device, as uint16).
+ *   sme_seednet_forward   n stacked feature grids -> seeds [n][M][2] FP32
+ *                         pixels (device, optional) and the raw cell outputs
+ *                         [n][H/4][W/4][16] FP32 (device, optional).
+ *   sme_seednet_gradients loss and parameter gradients (host out), no update.
+ *   sme_seednet_train_step forward, loss, backward, one Adam step with rate lr;
+ *                         loss (host out, optional) synchronises.
+ * Sizes must be multiples of 16; SME_ERR_SIZE beyond max_cells. */
+typedef struct sme_seednet sme_seednet;
+int sme_seednet_param_count(void);
+int sme_seednet_create(sme_seednet** out, int max_cells, void* cuda_stream);
+int sme_seednet_destroy(sme_seednet* net);
+int sme_seednet_set_params(sme_seednet* net, const float* params /* host */);
+int sme_seednet_get_params(sme_seednet* net, float* params /* host */);
+int sme_seednet_features(sme_seednet* net, const uint8_t* luma, int width, int height, int ref_frame,
+                         int cur_frame, const sme_mv* temporal /* [M] device or NULL */, int subpel,
+                         uint16_t* feat);
+int sme_seednet_forward(sme_seednet* net, const uint16_t* feat, int n, int width, int height, float* seeds,
+                        float* out_cells);
+int sme_seednet_gradients(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
+                          const float* labels /* [n][M][2] device */, const uint8_t* mask /* [n][M] device */,
+                          float* grads /* host, param layout */, float* loss /* host */);
+int sme_seednet_train_step(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
+                           const float* labels, const uint8_t* mask, float lr, float* loss /* host */);
+
 /* Stage timing (tracing).  sme_profile_begin makes every following
  * sme_estimate_sequence* call record CUDA events around its two launches on
  * the context's stream (classification, then the persistent ME launch), for

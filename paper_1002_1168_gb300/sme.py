@@ -30,7 +30,9 @@ EXPORTS = [
     "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
     "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_autotune",
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
-    "sme_batch_destroy", "sme_debug_set_fault",
+    "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
+    "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_forward",
+    "sme_seednet_gradients", "sme_seednet_train_step", "sme_debug_set_fault",
 ]
 
 
@@ -107,6 +109,15 @@ def _lib():
             "sme_batch_config": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_float)]),
             "sme_batch_destroy": (i, [vp]),
+            "sme_seednet_param_count": (i, []),
+            "sme_seednet_create": (i, [ip, i, vp]),
+            "sme_seednet_destroy": (i, [vp]),
+            "sme_seednet_set_params": (i, [vp, vp]),
+            "sme_seednet_get_params": (i, [vp, vp]),
+            "sme_seednet_features": (i, [vp, vp, i, i, i, i, vp, i, vp]),
+            "sme_seednet_forward": (i, [vp, vp, i, i, i, vp, vp]),
+            "sme_seednet_gradients": (i, [vp, vp, i, i, i, vp, vp, vp, C.POINTER(C.c_float)]),
+            "sme_seednet_train_step": (i, [vp, vp, i, i, i, vp, vp, C.c_float, C.POINTER(C.c_float)]),
             "sme_debug_set_fault": (i, [vp, i, C.c_longlong]),
         }
         for name, (res, args) in sig.items():
@@ -388,3 +399,90 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class SeedNet:
+    """The learned seed proposal network (device weights, FP32 master copy)."""
+
+    def __init__(self, max_cells):
+        import torch
+
+        self.torch = torch
+        lib = _lib()
+        self.n_params = lib.sme_seednet_param_count()
+        h = C.c_void_p()
+        _check(lib.sme_seednet_create(C.byref(h), int(max_cells), C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+               "sme_seednet_create")
+        self._h = h
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        assert flat.size == self.n_params
+        _check(_lib().sme_seednet_set_params(self._h, flat.ctypes.data_as(C.c_void_p)), "sme_seednet_set_params")
+
+    def get_params(self):
+        out = np.zeros(self.n_params, np.float32)
+        _check(_lib().sme_seednet_get_params(self._h, out.ctypes.data_as(C.c_void_p)), "sme_seednet_get_params")
+        return out
+
+    def features(self, luma, ref_frame, cur_frame, temporal=None, subpel=2, out=None):
+        t = self.torch
+        F, H, W = luma.shape
+        if out is None:
+            out = t.empty((H // 4, W // 4, 16), dtype=t.int16, device=luma.device)
+        _check(_lib().sme_seednet_features(self._h, _ptr(luma), W, H, int(ref_frame), int(cur_frame),
+                                           _ptr(temporal), int(subpel), _ptr(out)), "sme_seednet_features")
+        return out
+
+    def forward(self, feat, want_cells=False):
+        """feat [n, H/4, W/4, 16] (int16 view of bfloat16) -> seeds [n, M, 2] FP32 px."""
+        t = self.torch
+        n, Hc, Wc, _ = feat.shape
+        seeds = t.empty((n, (Hc // 4) * (Wc // 4), 2), dtype=t.float32, device=feat.device)
+        cells = t.empty((n, Hc, Wc, 16), dtype=t.float32, device=feat.device) if want_cells else None
+        _check(_lib().sme_seednet_forward(self._h, _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(seeds), _ptr(cells)),
+               "sme_seednet_forward")
+        return (seeds, cells) if want_cells else seeds
+
+    def gradients(self, feat, labels, mask):
+        n, Hc, Wc, _ = feat.shape
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_float()
+        _check(_lib().sme_seednet_gradients(self._h, _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(labels), _ptr(mask),
+                                            g.ctypes.data_as(C.c_void_p), C.byref(loss)), "sme_seednet_gradients")
+        return loss.value, g
+
+    def train_step(self, feat, labels, mask, lr, want_loss=False):
+        n, Hc, Wc, _ = feat.shape
+        loss = C.c_float()
+        _check(_lib().sme_seednet_train_step(self._h, _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(labels), _ptr(mask),
+                                             float(lr), C.byref(loss) if want_loss else None),
+               "sme_seednet_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().sme_seednet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_params(params):
+    """Flatten [(w [cout,3,3,cin], b [cout]), ...] into the library's layout."""
+    return np.concatenate([np.concatenate([np.asarray(w, np.float32).ravel(), np.asarray(b, np.float32)])
+                           for w, b in params])
+
+
+def unpack_params(flat, channels=(16, 32, 32, 32, 32, 16)):
+    out, o = [], 0
+    for li in range(5):
+        cin, cout = channels[li], channels[li + 1]
+        nw = cout * 9 * cin
+        out.append((flat[o:o + nw].reshape(cout, 3, 3, cin), flat[o + nw:o + nw + cout]))
+        o += nw + cout
+    return out

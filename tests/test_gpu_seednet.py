@@ -1,0 +1,99 @@
+"""GPU parity of the learned seed network against its CPU oracle.
+
+Hidden activations and gradients are bfloat16 on both sides at the same
+points; the GPU accumulates in FP32 on tensor cores, the oracle in float64, so
+an element can land one bfloat16 step apart.  The comparisons are therefore
+relative-norm tolerances: 1e-2 for the forward outputs, 3e-2 for the
+gradients, and one bfloat16 step (2^-7 relative) for the input features."""
+import numpy as np
+import pytest
+
+from oracle import seednet as SN
+from paper_1002_1168_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sme():
+    from paper_1002_1168_gb300 import build as cuda_build
+    from paper_1002_1168_gb300 import sme as m
+
+    cuda_build.build()
+    return m
+
+
+def as_float(t16):
+    return t16.view(torch.bfloat16).float().cpu().numpy().astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_features_match_oracle(sme):
+    seq = synth.cif_sequence(seed=1002, frames=3)
+    rng = np.random.default_rng(2)
+    tmp = rng.integers(-20, 21, (396, 2)).astype(np.int16)
+    net = sme.SeedNet(max_cells=88 * 72)
+    luma = torch.from_numpy(seq.luma).cuda()
+    f = as_float(net.features(luma, 1, 2, temporal=torch.from_numpy(tmp).cuda(), subpel=2))
+    o = SN.features(seq.luma[1], seq.luma[2], tmp, 2)
+    assert f.shape == o.shape == (72, 88, 16)
+    assert np.all(np.abs(f - o) <= 2.0 ** -7 * np.abs(o) + 1e-12)
+    assert np.mean(f == o) > 0.99
+    net.close()
+
+
+def _setup(sme, N=2, W=96, H=64, seed=5):
+    rng = np.random.default_rng(seed)
+    params = SN.init_params(seed)
+    params = [(w * (3.0 if li == 4 else 1.0), rng.normal(0, 0.05, b.shape)) for li, (w, b) in enumerate(params)]
+    x = SN.bf16(rng.normal(0, 0.5, (N, H // 4, W // 4, 16)))
+    net = sme.SeedNet(max_cells=N * (H // 4) * (W // 4))
+    net.set_params(sme.pack_params(params))
+    xt = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).view(torch.int16).cuda()
+    return rng, params, x, net, xt
+
+
+def test_forward_matches_oracle(sme):
+    _, params, x, net, xt = _setup(sme)
+    seeds, cells = net.forward(xt, want_cells=True)
+    acts = SN.forward(x, params)
+    assert rel(cells.cpu().numpy(), acts[-1]) < 1e-2
+    assert rel(seeds.cpu().numpy(), SN.pool_seeds(acts[-1])) < 1e-2
+    net.close()
+
+
+def test_gradients_match_oracle(sme):
+    rng, params, x, net, xt = _setup(sme, seed=6)
+    N, Hc, Wc, _ = x.shape
+    M = (Hc // 4) * (Wc // 4)
+    labels = rng.normal(0, 2, (N, M, 2))
+    mask = (rng.random((N, M)) < 0.8).astype(np.uint8)
+    loss_g, g = net.gradients(xt, torch.from_numpy(labels.astype(np.float32)).cuda(), torch.from_numpy(mask).cuda())
+    acts = SN.forward(x, params)
+    loss_o, d = SN.loss_and_grad(acts[-1], labels, mask)
+    grads = SN.backward(acts, params, d)
+    assert loss_g == pytest.approx(loss_o, rel=1e-2)
+    gg = sme.unpack_params(g)
+    for li in range(5):
+        assert rel(gg[li][0], grads[li][0]) < 3e-2, li
+        assert rel(gg[li][1], grads[li][1]) < 3e-2, li
+    net.close()
+
+
+def test_training_reduces_loss(sme):
+    rng, params, x, net, xt = _setup(sme, N=4, seed=7)
+    N, Hc, Wc, _ = x.shape
+    M = (Hc // 4) * (Wc // 4)
+    # a learnable target: the seed is a fixed linear function of the inputs
+    tgt = 8 * x[..., :2].reshape(N, Hc // 4, 4, Wc // 4, 4, 2).mean(axis=(2, 4)).reshape(N, M, 2)
+    labels = torch.from_numpy(tgt.astype(np.float32)).cuda()
+    mask = torch.ones((N, M), dtype=torch.uint8, device="cuda")
+    first = net.train_step(xt, labels, mask, 1e-3, want_loss=True)
+    for _ in range(150):
+        last = net.train_step(xt, labels, mask, 1e-3, want_loss=True)
+    assert last < 0.5 * first
+    net.close()

@@ -272,8 +272,13 @@ int sme_batch_destroy(sme_batch* b);
  *   labels (pixels) over the MBs with mask != 0, averaged; Adam (0.9, 0.999,
  *   1e-8) on FP32 master weights.
  *   sme_seednet_create    max_cells = largest n * (W/4) * (H/4) used later.
- *   sme_seednet_features  one frame pair of a [F][H][W] luma sequence (device)
- *                         -> feat [(H/4)][(W/4)][16] bfloat16 (device, as uint16).
+ *   sme_seednet_features  n_pairs frame pairs (ref_frame + q, cur_frame + q) of a
+ *                         [F][H][W] luma sequence (device) -> feat
+ *                         [n_pairs][H/4][W/4][16] bfloat16 (device, as uint16);
+ *                         a temporal field is accepted only with n_pairs = 1.
+ *                         The caller guarantees that frames ref_frame +
+ *                         n_pairs - 1 and cur_frame + n_pairs - 1 exist (the
+ *                         library does not know F); n_pairs <= 65535.
  *   sme_seednet_forward   n stacked feature grids -> seeds [n][M][2] FP32
  *                         pixels (device, optional) and the raw cell outputs
  *                         [n][H/4][W/4][16] FP32 (device, optional).
@@ -288,8 +293,8 @@ int sme_seednet_destroy(sme_seednet* net);
 int sme_seednet_set_params(sme_seednet* net, const float* params /* host */);
 int sme_seednet_get_params(sme_seednet* net, float* params /* host */);
 int sme_seednet_features(sme_seednet* net, const uint8_t* luma, int width, int height, int ref_frame,
-                         int cur_frame, const sme_mv* temporal /* [M] device or NULL */, int subpel,
-                         uint16_t* feat);
+                         int cur_frame, int n_pairs, const sme_mv* temporal /* [M] device or NULL */,
+                         int subpel, uint16_t* feat);
 int sme_seednet_forward(sme_seednet* net, const uint16_t* feat, int n, int width, int height, float* seeds,
                         float* out_cells);
 int sme_seednet_gradients(sme_seednet* net, const uint16_t* feat, int n, int width, int height,

@@ -41,12 +41,15 @@ __device__ __forceinline__ float bf2f(__nv_bfloat16 v) { return __bfloat162float
 // ------------------------------------------------------------ features --
 // Per 4x4 cell: current and reference mean luma (/255 - 0.5), their
 // difference, the temporal candidate of the cell's MB (pixels / 16).
-__global__ void features_kernel(const uint8_t* luma, int W, int H, int ref_f, int cur_f, const sme_mv* temporal,
-                                int subpel, __nv_bfloat16* out)
+// Pair q of the launch (blockIdx.y) uses frames ref_f + q and cur_f + q.
+__global__ void features_kernel(const uint8_t* luma, int W, int H, int ref_f0, int cur_f0, const sme_mv* temporal,
+                                int subpel, __nv_bfloat16* out_all)
 {
     const int Wc = W / 4, Hc = H / 4;
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= Wc * Hc) return;
+    const int q = blockIdx.y, ref_f = ref_f0 + q, cur_f = cur_f0 + q;
+    __nv_bfloat16* out = out_all + (size_t)q * Wc * Hc * 16;
     const int ci = cell / Wc, cj = cell - ci * Wc;
     const uint8_t* r = luma + (size_t)ref_f * W * H + (size_t)(4 * ci) * W + 4 * cj;
     const uint8_t* c = luma + (size_t)cur_f * W * H + (size_t)(4 * ci) * W + 4 * cj;
@@ -89,7 +92,7 @@ __device__ __forceinline__ unsigned pack_bf2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 // one row per warp), N = COUT, K = 9 taps x CIN.  y = conv(x, w) (+ bias)
 // (ReLU) (* [mask > 0]) stored as bfloat16 or FP32.  Zero padding.
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16* __restrict__ x,
+__global__ void __launch_bounds__(256) conv3x3_kernel(const __nv_bfloat16* __restrict__ x,
                                                       const __nv_bfloat16* __restrict__ w,
                                                       const float* __restrict__ bias,
                                                       const __nv_bfloat16* __restrict__ mask, int relu, int N,
@@ -103,11 +106,11 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16* __res
         ws[o * WST + k] = reinterpret_cast<const unsigned*>(w)[i];
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, tq = lane & 3;
-    const int segs = (Wc + 15) / 16;
-    const int seg = blockIdx.x * 4 + warp;
-    if (seg >= N * Hc * segs) return;
+    const int segs = (Wc + 15) / 16, nseg = N * Hc * segs;
+    // Persistent CTAs: each warp walks row segments, the weights staged once.
+    for (int seg = blockIdx.x * nwarps + warp; seg < nseg; seg += gridDim.x * nwarps) {
     const int n = seg / (Hc * segs), rem = seg - n * Hc * segs;
     const int i = rem / segs, j0 = (rem - i * segs) * 16;
     float acc[COUT / 8][4];
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16* __res
                     pack_bf2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
             }
         }
+    }
     }
 }
 
@@ -329,12 +333,16 @@ __global__ void convert_kernel(const float* p, __nv_bfloat16* w16, __nv_bfloat16
     wt16[woff + ((size_t)c * 9 + (8 - tap)) * cout + o] = b;
 }
 
+int g_conv_sms = 148;  // CTAs per launch scale with the SM count (set at create)
+
 template <int CIN, int COUT>
 cudaError_t conv(const __nv_bfloat16* x, const __nv_bfloat16* w, const float* b, const __nv_bfloat16* mask, int relu,
                  int N, int Hc, int Wc, __nv_bfloat16* y16, float* y32, cudaStream_t s)
 {
     const int segs = N * Hc * ((Wc + 15) / 16);
-    conv3x3_kernel<CIN, COUT><<<(segs + 3) / 4, 128, 0, s>>>(x, w, b, mask, relu, N, Hc, Wc, y16, y32);
+    int grid = (segs + 7) / 8;
+    if (grid > 4 * g_conv_sms) grid = 4 * g_conv_sms;
+    conv3x3_kernel<CIN, COUT><<<grid, 256, 0, s>>>(x, w, b, mask, relu, N, Hc, Wc, y16, y32);
     return cudaGetLastError();
 }
 
@@ -465,6 +473,7 @@ int sme_seednet_create(sme_seednet** out, int max_cells, void* stream)
     int dev = 0;
     bool ok = cudaGetDevice(&dev) == cudaSuccess &&
               cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+    if (ok) g_conv_sms = s->sms;
     const size_t P = kParams, C = (size_t)max_cells;
     int wtot = woff_of(kLayers);
     ok = ok && cudaMalloc(&s->master, P * 4) == cudaSuccess && cudaMalloc(&s->grad, P * 4) == cudaSuccess &&
@@ -522,14 +531,14 @@ int sme_seednet_get_params(sme_seednet* s, float* params)
 }
 
 int sme_seednet_features(sme_seednet* s, const uint8_t* luma, int width, int height, int ref_frame,
-                         int cur_frame, const sme_mv* temporal, int subpel, uint16_t* feat)
+                         int cur_frame, int n_pairs, const sme_mv* temporal, int subpel, uint16_t* feat)
 {
     if (!s || !luma || !feat || width % 16 || height % 16 || width <= 0 || height <= 0 || ref_frame < 0 ||
-        cur_frame < 0 || (subpel != 1 && subpel != 2))
+        cur_frame < 0 || n_pairs < 1 || n_pairs > 65535 || (subpel != 1 && subpel != 2) || (temporal && n_pairs != 1))
         return SME_ERR_ARG;
     const int cells = (width / 4) * (height / 4);
-    features_kernel<<<(cells + 127) / 128, 128, 0, s->stream>>>(luma, width, height, ref_frame, cur_frame, temporal,
-                                                               subpel, reinterpret_cast<__nv_bfloat16*>(feat));
+    features_kernel<<<dim3((cells + 127) / 128, n_pairs), 128, 0, s->stream>>>(
+        luma, width, height, ref_frame, cur_frame, temporal, subpel, reinterpret_cast<__nv_bfloat16*>(feat));
     return cudaGetLastError() == cudaSuccess ? SME_OK : SME_ERR_CUDA;
 }
 

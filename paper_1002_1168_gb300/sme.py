@@ -114,7 +114,7 @@ def _lib():
             "sme_seednet_destroy": (i, [vp]),
             "sme_seednet_set_params": (i, [vp, vp]),
             "sme_seednet_get_params": (i, [vp, vp]),
-            "sme_seednet_features": (i, [vp, vp, i, i, i, i, vp, i, vp]),
+            "sme_seednet_features": (i, [vp, vp, i, i, i, i, i, vp, i, vp]),
             "sme_seednet_forward": (i, [vp, vp, i, i, i, vp, vp]),
             "sme_seednet_gradients": (i, [vp, vp, i, i, i, vp, vp, vp, C.POINTER(C.c_float)]),
             "sme_seednet_train_step": (i, [vp, vp, i, i, i, vp, vp, C.c_float, C.POINTER(C.c_float)]),
@@ -425,12 +425,18 @@ class SeedNet:
         _check(_lib().sme_seednet_get_params(self._h, out.ctypes.data_as(C.c_void_p)), "sme_seednet_get_params")
         return out
 
-    def features(self, luma, ref_frame, cur_frame, temporal=None, subpel=2, out=None):
+    def features(self, luma, ref_frame, cur_frame, temporal=None, subpel=2, out=None, n_pairs=1):
+        """Input grid(s) of n_pairs frame pairs (ref_frame + q, cur_frame + q);
+        [H/4, W/4, 16] for one pair, else [n_pairs, H/4, W/4, 16]."""
         t = self.torch
         F, H, W = luma.shape
+        last = max(int(ref_frame), int(cur_frame)) + int(n_pairs) - 1
+        if min(int(ref_frame), int(cur_frame)) < 0 or last >= F:
+            raise ValueError(f"frames {ref_frame}/{cur_frame} + {n_pairs} pairs outside a {F}-frame sequence")
         if out is None:
-            out = t.empty((H // 4, W // 4, 16), dtype=t.int16, device=luma.device)
-        _check(_lib().sme_seednet_features(self._h, _ptr(luma), W, H, int(ref_frame), int(cur_frame),
+            shape = (H // 4, W // 4, 16) if n_pairs == 1 else (n_pairs, H // 4, W // 4, 16)
+            out = t.empty(shape, dtype=t.int16, device=luma.device)
+        _check(_lib().sme_seednet_features(self._h, _ptr(luma), W, H, int(ref_frame), int(cur_frame), int(n_pairs),
                                            _ptr(temporal), int(subpel), _ptr(out)), "sme_seednet_features")
         return out
 

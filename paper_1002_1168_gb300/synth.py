@@ -287,3 +287,15 @@ def random_frames(W, H, F, seed, alpha_density=0.5, alpha_blobs=True):
     else:
         alpha = np.where(rng.random((F, H, W)) < alpha_density, 255, 0).astype(np.uint8)
     return luma, alpha
+
+
+def seednet_init(seed, channels=(16, 32, 32, 32, 32, 16)):
+    """Initial weights of the seed network: He-normal (std sqrt(2 / (9 cin))),
+    the last layer at a tenth of that, zero biases; numpy PCG64."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for li in range(5):
+        cin, cout = channels[li], channels[li + 1]
+        std = np.sqrt(2.0 / (9 * cin)) * (0.1 if li == 4 else 1.0)
+        out.append((rng.normal(0.0, std, (cout, 3, 3, cin)), np.zeros(cout)))
+    return out

@@ -46,6 +46,23 @@ def test_features_match_oracle(sme):
     net.close()
 
 
+def test_features_batched_pairs_match_single(sme):
+    # one launch over P pairs (ref frame q, current frame q + 2) equals P
+    # single-pair launches, bit for bit, and the oracle within one bf16 step
+    seq = synth.cif_sequence(seed=1002, frames=6)
+    net = sme.SeedNet(max_cells=4 * 88 * 72)
+    luma = torch.from_numpy(seq.luma).cuda()
+    many = net.features(luma, 0, 2, subpel=2, n_pairs=4).cpu()
+    assert many.shape == (4, 72, 88, 16)
+    for q in range(4):
+        one = net.features(luma, q, q + 2, subpel=2).cpu()
+        assert torch.equal(many[q], one)
+        o = SN.features(seq.luma[q], seq.luma[q + 2], None, 2)
+        f = as_float(many[q])
+        assert np.all(np.abs(f - o) <= 2.0 ** -7 * np.abs(o) + 1e-12)
+    net.close()
+
+
 def _setup(sme, N=2, W=96, H=64, seed=5):
     rng = np.random.default_rng(seed)
     params = SN.init_params(seed)

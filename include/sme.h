@@ -282,6 +282,14 @@ int sme_batch_destroy(sme_batch* b);
  *   sme_seednet_forward   n stacked feature grids -> seeds [n][M][2] FP32
  *                         pixels (device, optional) and the raw cell outputs
  *                         [n][H/4][W/4][16] FP32 (device, optional).
+ *   sme_seednet_forward_active  seeds [n][M][2] (device) of the MBs that
+ *                         use one, the non-transparent ones (mb_class [n][M]
+ *                         device, as sme_classify writes it), equal bit for
+ *                         bit to those of sme_seednet_forward; transparent MBs
+ *                         get (0, 0).  The layers are evaluated only on MBs
+ *                         within one MB of a non-transparent MB (five 3x3
+ *                         layers reach 5 cells, one MB is 4 cells and the
+ *                         MB's own cells are the fifth).
  *   sme_seednet_gradients loss and parameter gradients (host out), no update.
  *   sme_seednet_train_step forward, loss, backward, one Adam step with rate lr;
  *                         loss (host out, optional) synchronises.
@@ -297,6 +305,8 @@ int sme_seednet_features(sme_seednet* net, const uint8_t* luma, int width, int h
                          int subpel, uint16_t* feat);
 int sme_seednet_forward(sme_seednet* net, const uint16_t* feat, int n, int width, int height, float* seeds,
                         float* out_cells);
+int sme_seednet_forward_active(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
+                               const uint8_t* mb_class, float* seeds);
 int sme_seednet_gradients(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
                           const float* labels /* [n][M][2] device */, const uint8_t* mask /* [n][M] device */,
                           float* grads /* host, param layout */, float* loss /* host */);

@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const __nv_bfloat16* __res
                                                       const __nv_bfloat16* __restrict__ w,
                                                       const float* __restrict__ bias,
                                                       const __nv_bfloat16* __restrict__ mask, int relu, int N,
-                                                      int Hc, int Wc, __nv_bfloat16* y16, float* y32)
+                                                      int Hc, int Wc, const int* __restrict__ units,
+                                                      __nv_bfloat16* y16, float* y32)
 {
     constexpr int KT = 9 * CIN;        // K per output channel
     constexpr int WST = KT / 2 + 4;    // smem row stride in 32-bit words (padded against bank conflicts)
@@ -108,11 +109,17 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const __nv_bfloat16* __res
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, tq = lane & 3;
-    const int segs = (Wc + 15) / 16, nseg = N * Hc * segs;
-    // Persistent CTAs: each warp walks row segments, the weights staged once.
-    for (int seg = blockIdx.x * nwarps + warp; seg < nseg; seg += gridDim.x * nwarps) {
-    const int n = seg / (Hc * segs), rem = seg - n * Hc * segs;
-    const int i = rem / segs, j0 = (rem - i * segs) * 16;
+    const int mbw = Wc >> 2, per = mbw * (Hc >> 2);
+    // A warp's tile is the 4x4 cells of one MB: tile row r is cell (r / 4, r % 4),
+    // so this lane's rows g and g + 8 are cells (g/4, g%4) and (g/4 + 2, g%4).
+    // units = NULL: every MB of the N grids; else units[0] MBs listed in units[1..].
+    const int total = units ? units[0] : N * per;
+    // Persistent CTAs: each warp walks MBs, the weights staged once.
+    for (int k = blockIdx.x * nwarps + warp; k < total; k += gridDim.x * nwarps) {
+    const int u = units ? units[1 + k] : k;
+    const int n = u / per, mb = u - n * per;
+    const int mv = mb / mbw, mu = mb - mv * mbw;
+    const int i0 = 4 * mv + (g >> 2), j = 4 * mu + (g & 3);
     float acc[COUT / 8][4];
 #pragma unroll
     for (int t = 0; t < COUT / 8; ++t)
@@ -121,11 +128,10 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const __nv_bfloat16* __res
     const unsigned* xw = reinterpret_cast<const unsigned*>(x);
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-        const int ii = i + tap / 3 - 1;
-        const bool row_ok = ii >= 0 && ii < Hc;
-        const int jj0 = j0 + g + tap % 3 - 1, jj1 = jj0 + 8;
-        const bool ok0 = row_ok && jj0 >= 0 && jj0 < Wc, ok1 = row_ok && jj1 >= 0 && jj1 < Wc;
-        const size_t p0 = ((size_t)n * Hc + ii) * Wc + jj0, p1 = p0 + 8;
+        const int ii0 = i0 + tap / 3 - 1, ii1 = ii0 + 2, jj = j + tap % 3 - 1;
+        const bool col_ok = jj >= 0 && jj < Wc;
+        const bool ok0 = col_ok && ii0 >= 0 && ii0 < Hc, ok1 = col_ok && ii1 >= 0 && ii1 < Hc;
+        const size_t p0 = ((size_t)n * Hc + ii0) * Wc + jj, p1 = p0 + 2 * (size_t)Wc;
 #pragma unroll
         for (int cb = 0; cb < CIN / 16; ++cb) {
             const int c0 = cb * 16 + 2 * tq;
@@ -142,12 +148,10 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const __nv_bfloat16* __res
             }
         }
     }
-    // epilogue: rows g and g+8 of the tile, channels t*8 + 2*tq (+1)
+    // epilogue: tile rows g and g+8 (cells (i0, j), (i0 + 2, j)), channels t*8 + 2*tq (+1)
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-        const int j = j0 + g + 8 * half;
-        if (j >= Wc) continue;
-        const size_t p = ((size_t)n * Hc + i) * Wc + j;
+        const size_t p = ((size_t)n * Hc + i0 + 2 * half) * Wc + j;
 #pragma unroll
         for (int t = 0; t < COUT / 8; ++t) {
             const int ch = t * 8 + 2 * tq;
@@ -174,6 +178,30 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const __nv_bfloat16* __res
         }
     }
     }
+}
+
+// The MBs the seeds of the non-transparent MBs (the only ones that use a
+// seed) depend on.  A seed reads layer 5 on its MB's cells; layer l (1..5) is
+// needed on those cells dilated by 5 - l cells, at most 4 cells = one MB.  So
+// every layer is evaluated only on the MBs within one MB (Chebyshev) of a
+// non-transparent MB; each needed value then reads only needed (hence
+// evaluated) values of the layer before, and the seeds equal those of the
+// dense pass bit for bit.
+// units[0] = count (zeroed by the caller), units[1..] = MB indices n * M + mb
+// in no particular order (each MB's arithmetic does not depend on it).
+__global__ void active_units_kernel(const uint8_t* __restrict__ cls, int N, int mbw, int mbh, int* units)
+{
+    const int M = mbw * mbh;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= N * M) return;
+    const int n = id / M, mb = id - n * M, v = mb / mbw, u = mb - v * mbw;
+    bool act = false;
+    for (int dv = -1; dv <= 1; ++dv)
+        for (int du = -1; du <= 1; ++du) {
+            const int vv = v + dv, uu = u + du;
+            if (vv >= 0 && vv < mbh && uu >= 0 && uu < mbw && cls[(size_t)n * M + vv * mbw + uu] != 0) act = true;
+        }
+    if (act) units[1 + atomicAdd(units, 1)] = id;
 }
 
 // Weight and bias gradients: dW[o][tap][c] = sum_p dY[p][o] x[p + tap][c],
@@ -253,12 +281,20 @@ __global__ void __launch_bounds__(288) conv3x3_wgrad_kernel(const __nv_bfloat16*
 // Per-MB seeds (SEED_SCALE x mean of output channels 0, 1 over the MB's 4x4
 // cells) and, with labels, the Huber loss over the masked MBs (mean) and its
 // gradient w.r.t. the cell outputs (bfloat16, channels 0, 1; others 0).
+// With cls (seeds only): transparent MBs (class 0) get seed 0 and their cells
+// are not read.
 __global__ void pool_loss_kernel(const float* out, int N, int Hc, int Wc, float* seeds, const float* labels,
-                                 const uint8_t* mask, const int* count, float* loss, __nv_bfloat16* dout)
+                                 const uint8_t* mask, const int* count, float* loss, __nv_bfloat16* dout,
+                                 const uint8_t* cls = nullptr)
 {
     const int MBW = Wc / 4, MBH = Hc / 4, M = MBW * MBH;
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= N * M) return;
+    if (cls && cls[id] == 0) {
+        seeds[2 * (size_t)id] = 0.0f;
+        seeds[2 * (size_t)id + 1] = 0.0f;
+        return;
+    }
     const int n = id / M, mb = id - n * M, u = mb % MBW, v = mb / MBW;
     float s[2] = {0.0f, 0.0f};
     for (int y = 0; y < 4; ++y)
@@ -335,14 +371,21 @@ __global__ void convert_kernel(const float* p, __nv_bfloat16* w16, __nv_bfloat16
 
 int g_conv_sms = 148;  // CTAs per launch scale with the SM count (set at create)
 
+// units: NULL for every MB of the N grids, else a device list (count first)
+// of at most N * MBs entries.
 template <int CIN, int COUT>
 cudaError_t conv(const __nv_bfloat16* x, const __nv_bfloat16* w, const float* b, const __nv_bfloat16* mask, int relu,
-                 int N, int Hc, int Wc, __nv_bfloat16* y16, float* y32, cudaStream_t s)
+                 int N, int Hc, int Wc, const int* units, __nv_bfloat16* y16, float* y32, cudaStream_t s)
 {
-    const int segs = N * Hc * ((Wc + 15) / 16);
-    int grid = (segs + 7) / 8;
-    if (grid > 4 * g_conv_sms) grid = 4 * g_conv_sms;
-    conv3x3_kernel<CIN, COUT><<<grid, 256, 0, s>>>(x, w, b, mask, relu, N, Hc, Wc, y16, y32);
+    static int per_sm = 0;  // resident CTAs per SM of this instance
+    if (per_sm == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv3x3_kernel<CIN, COUT>, 256, 0) != cudaSuccess ||
+         per_sm < 1))
+        per_sm = 1;
+    const int mbs = N * (Hc / 4) * (Wc / 4);
+    int grid = (mbs + 7) / 8;
+    if (grid > per_sm * g_conv_sms) grid = per_sm * g_conv_sms;
+    conv3x3_kernel<CIN, COUT><<<grid, 256, 0, s>>>(x, w, b, mask, relu, N, Hc, Wc, units, y16, y32);
     return cudaGetLastError();
 }
 
@@ -375,6 +418,7 @@ struct sme_seednet {
     __nv_bfloat16* d0 = nullptr;       // gradient ping-pong buffers
     __nv_bfloat16* d1 = nullptr;
     float* scal = nullptr;             // loss (float) + count (int)
+    int* units = nullptr;              // active MB list of the sparse forward (count first)
 };
 
 namespace {
@@ -386,7 +430,7 @@ int woff_of(int l)
     return o;
 }
 
-int forward(sme_seednet* s, const __nv_bfloat16* feat, int N, int Hc, int Wc)
+int forward(sme_seednet* s, const __nv_bfloat16* feat, int N, int Hc, int Wc, const int* units = nullptr)
 {
     cudaStream_t st = s->stream;
     const float* b[kLayers];
@@ -395,11 +439,11 @@ int forward(sme_seednet* s, const __nv_bfloat16* feat, int N, int Hc, int Wc)
         w[l] = s->w16 + woff_of(l);
         b[l] = s->master + loff(l) + wsize(l);
     }
-    if (conv<16, 32>(feat, w[0], b[0], nullptr, 1, N, Hc, Wc, s->act[1], nullptr, st) ||
-        conv<32, 32>(s->act[1], w[1], b[1], nullptr, 1, N, Hc, Wc, s->act[2], nullptr, st) ||
-        conv<32, 32>(s->act[2], w[2], b[2], nullptr, 1, N, Hc, Wc, s->act[3], nullptr, st) ||
-        conv<32, 32>(s->act[3], w[3], b[3], nullptr, 1, N, Hc, Wc, s->act[4], nullptr, st) ||
-        conv<32, 16>(s->act[4], w[4], b[4], nullptr, 0, N, Hc, Wc, nullptr, s->out32, st))
+    if (conv<16, 32>(feat, w[0], b[0], nullptr, 1, N, Hc, Wc, units, s->act[1], nullptr, st) ||
+        conv<32, 32>(s->act[1], w[1], b[1], nullptr, 1, N, Hc, Wc, units, s->act[2], nullptr, st) ||
+        conv<32, 32>(s->act[2], w[2], b[2], nullptr, 1, N, Hc, Wc, units, s->act[3], nullptr, st) ||
+        conv<32, 32>(s->act[3], w[3], b[3], nullptr, 1, N, Hc, Wc, units, s->act[4], nullptr, st) ||
+        conv<32, 16>(s->act[4], w[4], b[4], nullptr, 0, N, Hc, Wc, units, nullptr, s->out32, st))
         return SME_ERR_CUDA;
     return SME_OK;
 }
@@ -433,13 +477,13 @@ int backward(sme_seednet* s, const __nv_bfloat16* feat, int N, int Hc, int Wc, c
     }
     // layer 4 (32 -> 16): weights from act[4] and d0; input gradient into d1 (masked by act[4])
     if (wgrad<32, 16>(s->act[4], s->d0, N, Hc, Wc, dw[4], db[4], s->sms, st) ||
-        conv<16, 32>(s->d0, wt[4], nullptr, s->act[4], 0, N, Hc, Wc, s->d1, nullptr, st) ||
+        conv<16, 32>(s->d0, wt[4], nullptr, s->act[4], 0, N, Hc, Wc, nullptr, s->d1, nullptr, st) ||
         wgrad<32, 32>(s->act[3], s->d1, N, Hc, Wc, dw[3], db[3], s->sms, st) ||
-        conv<32, 32>(s->d1, wt[3], nullptr, s->act[3], 0, N, Hc, Wc, s->d0, nullptr, st) ||
+        conv<32, 32>(s->d1, wt[3], nullptr, s->act[3], 0, N, Hc, Wc, nullptr, s->d0, nullptr, st) ||
         wgrad<32, 32>(s->act[2], s->d0, N, Hc, Wc, dw[2], db[2], s->sms, st) ||
-        conv<32, 32>(s->d0, wt[2], nullptr, s->act[2], 0, N, Hc, Wc, s->d1, nullptr, st) ||
+        conv<32, 32>(s->d0, wt[2], nullptr, s->act[2], 0, N, Hc, Wc, nullptr, s->d1, nullptr, st) ||
         wgrad<32, 32>(s->act[1], s->d1, N, Hc, Wc, dw[1], db[1], s->sms, st) ||
-        conv<32, 32>(s->d1, wt[1], nullptr, s->act[1], 0, N, Hc, Wc, s->d0, nullptr, st) ||
+        conv<32, 32>(s->d1, wt[1], nullptr, s->act[1], 0, N, Hc, Wc, nullptr, s->d0, nullptr, st) ||
         wgrad<16, 32>(feat, s->d0, N, Hc, Wc, dw[0], db[0], s->sms, st))
         return SME_ERR_CUDA;
     if (loss_host) {
@@ -480,7 +524,8 @@ int sme_seednet_create(sme_seednet** out, int max_cells, void* stream)
          cudaMalloc(&s->adam_m, P * 4) == cudaSuccess && cudaMalloc(&s->adam_v, P * 4) == cudaSuccess &&
          cudaMalloc(&s->w16, wtot * 2) == cudaSuccess && cudaMalloc(&s->wt16, wtot * 2) == cudaSuccess &&
          cudaMalloc(&s->out32, C * 16 * 4) == cudaSuccess && cudaMalloc(&s->d0, C * 32 * 2) == cudaSuccess &&
-         cudaMalloc(&s->d1, C * 32 * 2) == cudaSuccess && cudaMalloc(&s->scal, 16) == cudaSuccess;
+         cudaMalloc(&s->d1, C * 32 * 2) == cudaSuccess && cudaMalloc(&s->scal, 16) == cudaSuccess &&
+         cudaMalloc(&s->units, (C / 16 + 1) * sizeof(int)) == cudaSuccess;
     for (int l = 1; l < kLayers && ok; ++l) ok = cudaMalloc(&s->act[l], C * 32 * 2) == cudaSuccess;
     ok = ok && cudaMemset(s->master, 0, P * 4) == cudaSuccess && cudaMemset(s->adam_m, 0, P * 4) == cudaSuccess &&
          cudaMemset(s->adam_v, 0, P * 4) == cudaSuccess;
@@ -499,7 +544,8 @@ int sme_seednet_destroy(sme_seednet* s)
 {
     if (!s) return SME_ERR_ARG;
     cudaStreamSynchronize(s->stream);
-    void* ptrs[] = {s->master, s->grad, s->adam_m, s->adam_v, s->w16, s->wt16, s->out32, s->d0, s->d1, s->scal};
+    void* ptrs[] = {s->master, s->grad, s->adam_m, s->adam_v, s->w16,  s->wt16,
+                    s->out32,  s->d0,   s->d1,     s->scal,   s->units};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int l = 1; l < kLayers; ++l)
@@ -560,6 +606,22 @@ int sme_seednet_forward(sme_seednet* s, const uint16_t* feat, int n, int width, 
                         s->stream) != cudaSuccess)
         return SME_ERR_CUDA;
     return SME_OK;
+}
+
+int sme_seednet_forward_active(sme_seednet* s, const uint16_t* feat, int n, int width, int height,
+                               const uint8_t* mb_class, float* seeds)
+{
+    int rc = check_geom(s, feat, n, width, height);
+    if (rc) return rc;
+    if (!mb_class || !seeds) return SME_ERR_ARG;
+    const int Hc = height / 4, Wc = width / 4, M = n * (Hc / 4) * (Wc / 4);
+    if (cudaMemsetAsync(s->units, 0, sizeof(int), s->stream) != cudaSuccess) return SME_ERR_CUDA;
+    active_units_kernel<<<(M + 127) / 128, 128, 0, s->stream>>>(mb_class, n, Wc / 4, Hc / 4, s->units);
+    if (cudaGetLastError() != cudaSuccess) return SME_ERR_CUDA;
+    if ((rc = forward(s, reinterpret_cast<const __nv_bfloat16*>(feat), n, Hc, Wc, s->units))) return rc;
+    pool_loss_kernel<<<(M + 127) / 128, 128, 0, s->stream>>>(s->out32, n, Hc, Wc, seeds, nullptr, nullptr, nullptr,
+                                                             nullptr, nullptr, mb_class);
+    return cudaGetLastError() == cudaSuccess ? SME_OK : SME_ERR_CUDA;
 }
 
 int sme_seednet_gradients(sme_seednet* s, const uint16_t* feat, int n, int width, int height, const float* labels,

@@ -76,15 +76,18 @@ def train(net, feats, labels, mask, steps=600, batch=32, lr=1e-3, seed=0, log_ev
     return hist
 
 
-def sequence_seeds(net, luma, subpel=2, ref_distance=1):
-    """Seeds [P, M, 2] (pixels) for every pair of a sequence, one forward."""
-    import torch
-
+def sequence_seeds(net, luma, subpel=2, ref_distance=1, mb_class=None, out=None):
+    """Seeds [P, M, 2] (pixels) for every pair of a sequence, one forward.
+    With the frames' MB classes (mb_class [F, M]) only the non-transparent
+    MBs (the ones that use a seed) get seeds and the network runs only
+    around them."""
     F, H, W = luma.shape
     P = F - ref_distance
     feats = net.features(luma, 0, ref_distance, temporal=None, subpel=subpel, n_pairs=P)
     if P == 1:
         feats = feats[None]
+    if mb_class is not None:
+        return net.forward_active(feats, mb_class[ref_distance:], out=out)
     return net.forward(feats)
 
 
@@ -100,7 +103,9 @@ def evaluate(net, seq_luma, seq_alpha, search_range=16, subpel=2, runs=20):
     est = sme.Estimator(W, H, search_range=search_range, subpel=subpel)
     want = ("cost", "iters", "npos", "mb_class", "sse")
     plain = est.estimate_sequence(luma, alpha, want=want)
-    seeds = sequence_seeds(net, luma, subpel)
+    cls = torch.empty((F, est.M), dtype=torch.uint8, device=luma.device)
+    est.classify(alpha, want_packed=False, out=cls)
+    seeds = sequence_seeds(net, luma, subpel, mb_class=cls)
     learned = est.estimate_sequence(luma, alpha, seed=seeds, want=want)
 
     def timed(fn):
@@ -118,8 +123,14 @@ def evaluate(net, seq_luma, seq_alpha, search_range=16, subpel=2, runs=20):
     po = est._alloc_outputs(F - 1, want, luma.device)
     lo = est._alloc_outputs(F - 1, want, luma.device)
     ms_plain = timed(lambda: est.estimate_sequence(luma, alpha, out=po, sync=False))
-    ms_learned = timed(lambda: est.estimate_sequence(luma, alpha, seed=sequence_seeds(net, luma, subpel), out=lo,
-                                                     sync=False))
+    def learned_pass():
+        # the whole learned-seeded pass: classes, network near the object, estimation
+        est.classify(alpha, want_packed=False, out=cls, sync=False)
+        sequence_seeds(net, luma, subpel, mb_class=cls, out=seeds)
+        est.estimate_sequence(luma, alpha, seed=seeds, out=lo, sync=False)
+
+    ms_learned = timed(learned_pass)
+    ms_seeded_me = timed(lambda: est.estimate_sequence(luma, alpha, seed=seeds, out=lo, sync=False))
     est.synchronize()
     P, M = plain["mv"].shape[:2]
     res, raw = {}, {}
@@ -133,6 +144,7 @@ def evaluate(net, seq_luma, seq_alpha, search_range=16, subpel=2, runs=20):
                      "positions_per_mb": float(o["npos"][cls > 0].mean()),
                      "psnr_db": float(np.mean([sme.psnr(int(s_), W, H) for s_ in sse])),
                      "opaque_cost_sum": int(o["cost"].view(np.uint32)[cls == 1].sum())}
+    res["learned"]["ms_estimation_only"] = ms_seeded_me
     res["seed_changed_mbs"] = int((raw["plain"]["mv"] != raw["learned"]["mv"]).any(axis=-1).sum())
     est.close()
     return res, raw

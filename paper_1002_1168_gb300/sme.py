@@ -32,6 +32,7 @@ EXPORTS = [
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_forward",
+    "sme_seednet_forward_active",
     "sme_seednet_gradients", "sme_seednet_train_step", "sme_debug_set_fault",
 ]
 
@@ -116,6 +117,7 @@ def _lib():
             "sme_seednet_get_params": (i, [vp, vp]),
             "sme_seednet_features": (i, [vp, vp, i, i, i, i, i, vp, i, vp]),
             "sme_seednet_forward": (i, [vp, vp, i, i, i, vp, vp]),
+            "sme_seednet_forward_active": (i, [vp, vp, i, i, i, vp, vp]),
             "sme_seednet_gradients": (i, [vp, vp, i, i, i, vp, vp, vp, C.POINTER(C.c_float)]),
             "sme_seednet_train_step": (i, [vp, vp, i, i, i, vp, vp, C.c_float, C.POINTER(C.c_float)]),
             "sme_debug_set_fault": (i, [vp, i, C.c_longlong]),
@@ -234,14 +236,17 @@ class Estimator:
         _check(rc, "sme_estimate_sequence_host")
         return out
 
-    def classify(self, alpha, want_packed=True):
+    def classify(self, alpha, want_packed=True, out=None, sync=True):
+        """MB classes [F, M] uint8 (into out if given) and, optionally, the
+        packed alpha rows."""
         t = self.torch
         F = alpha.shape[0]
-        cls = t.empty((F, self.M), dtype=t.uint8, device=alpha.device)
+        cls = out if out is not None else t.empty((F, self.M), dtype=t.uint8, device=alpha.device)
         wp = _lib().sme_packed_words(self.width)
         packed = t.empty((F, self.height, wp), dtype=t.int32, device=alpha.device) if want_packed else None
         _check(_lib().sme_classify(self._bind(), _ptr(alpha), F, _ptr(cls), _ptr(packed)), "sme_classify")
-        self.synchronize()
+        if sync:
+            self.synchronize()
         return cls, packed
 
     def compensate(self, ref, cur, mv, want_pred=True):
@@ -449,6 +454,17 @@ class SeedNet:
         _check(_lib().sme_seednet_forward(self._h, _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(seeds), _ptr(cells)),
                "sme_seednet_forward")
         return (seeds, cells) if want_cells else seeds
+
+    def forward_active(self, feat, mb_class, out=None):
+        """Seeds of the non-transparent MBs (mb_class [n, M] uint8 != 0),
+        (0, 0) on transparent ones; the layers run only near those MBs."""
+        t = self.torch
+        n, Hc, Wc, _ = feat.shape
+        if out is None:
+            out = t.empty((n, (Hc // 4) * (Wc // 4), 2), dtype=t.float32, device=feat.device)
+        _check(_lib().sme_seednet_forward_active(self._h, _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(mb_class), _ptr(out)),
+               "sme_seednet_forward_active")
+        return out
 
     def gradients(self, feat, labels, mask):
         n, Hc, Wc, _ = feat.shape

@@ -63,6 +63,26 @@ def test_features_batched_pairs_match_single(sme):
     net.close()
 
 
+def test_forward_active_equals_dense(sme):
+    # the layers run only near non-transparent MBs; their seeds are those of
+    # the dense pass bit for bit, transparent MBs get (0, 0)
+    _, params, x, net, xt = _setup(sme, N=3, W=160, H=128, seed=8)
+    N, Hc, Wc, _ = x.shape
+    M = (Hc // 4) * (Wc // 4)
+    rng = np.random.default_rng(9)
+    cls = np.zeros((N, M), np.uint8)
+    cls[0, 0] = 1                                   # corner
+    cls[1, rng.choice(M, 6, replace=False)] = 1     # scattered
+    cls[1, rng.choice(M, 6, replace=False)] = 2     # boundary MBs use seeds too
+    cls[2, :] = 1                                   # all opaque
+    dense = net.forward(xt).cpu().numpy()
+    sparse = net.forward_active(xt, torch.from_numpy(cls).cuda()).cpu().numpy()
+    op = cls != 0
+    assert np.array_equal(sparse[op], dense[op])
+    assert np.all(sparse[~op] == 0)
+    net.close()
+
+
 def _setup(sme, N=2, W=96, H=64, seed=5):
     rng = np.random.default_rng(seed)
     params = SN.init_params(seed)

@@ -8,6 +8,12 @@ macroblocks per second over all frame-grid MBs of all pairs.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The same line carries the learned-seeded form: a seed network trained here
+on the GPU (2000 CIF VOP pairs, labelled by the plain method), then the
+learned-seeded pass on the same workload (quality.learned_seeded) and on the
+batched workload (batched.learned_seeded), each checked against the oracle
+given the same seeds.
+
 --impl reference times the CPU oracle (single-threaded C) on the same workload.
 Under torchrun (N > 1) every rank runs an independent replica (its own
 sequence); the data path has no collective, so scaling is weak.
@@ -174,7 +180,128 @@ def cpu_baseline(seq, budget_s=10.0):
             "sample": f"{n} full passes over the workload ({n * P * p.mbs} MBs, {dt:.1f} s), single-threaded C"}, res
 
 
-def measure_batch(sme, torch, args, rank, dist):
+def train_seednet(sme, torch, args):
+    """The learned proposal, trained here on the GPU by the library's own
+    forward/backward kernels: args.learn_pairs CIF VOP frame pairs (1-2
+    objects, rotation <= 5 deg, scale 0.95-1.05) labelled by the plain method,
+    args.learn_steps Adam steps of 32 pairs."""
+    from paper_1002_1168_gb300 import seedtrain, synth
+
+    t0 = time.perf_counter()
+    pairs = seedtrain.training_pairs(args.learn_pairs, seed=11, workers=min(os.cpu_count() or 1, 16))
+    gen_s = time.perf_counter() - t0
+    net = sme.SeedNet(max_cells=len(pairs) * (H // 4) * (W // 4))
+    net.set_params(sme.pack_params(synth.seednet_init(3)))
+    feats, labels, mask = seedtrain.build_dataset(pairs, net, search_range=S, subpel=SUBPEL)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = seedtrain.train(net, feats, labels, mask, steps=args.learn_steps, batch=32, lr=1e-3, seed=0,
+                           log_every=max(args.learn_steps // 4, 1))
+    torch.cuda.synchronize()
+    info = {"pairs": len(pairs), "labelled_mbs": int(mask.sum().item()), "steps": args.learn_steps, "batch": 32,
+            "lr": 1e-3, "generation_s": gen_s, "train_s": time.perf_counter() - t1,
+            "loss": [[st, round(float(l), 4)] for st, l in hist]}
+    del feats, labels, mask
+    return net, info
+
+
+def measure_learned(sme, torch, args, net, est, luma, alpha, flush):
+    """The learned-seeded pass on the headline workload, timed like the plain
+    one (L2 flushed between steps): classification, features of all pairs,
+    the sparse network forward near the object, estimation with the seeds as
+    fifth candidate (plain search as fallback)."""
+    P, M = FRAMES - 1, (W // 16) * (H // 16)
+    dev = luma.device
+    cls = torch.empty((FRAMES, M), dtype=torch.uint8, device=dev)
+    feat = torch.empty((P, H // 4, W // 4, 16), dtype=torch.int16, device=dev)
+    seeds = torch.empty((P, M, 2), dtype=torch.float32, device=dev)
+    out = est._alloc_outputs(P, OUT_FIELDS, dev)
+
+    def seed_pass():
+        est.classify(alpha, want_packed=False, out=cls, sync=False)
+        net.features(luma, 0, 1, subpel=SUBPEL, n_pairs=P, out=feat)
+        net.forward_active(feat, cls[1:], out=seeds)
+
+    def full_pass():
+        seed_pass()
+        est.estimate_sequence(luma, alpha, seed=seeds, out=out, sync=False)
+
+    def timed(fn, steps):
+        for _ in range(3):
+            fn()
+        est.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i, (e0, e1) in enumerate(ev):
+            flush.fill_(i & 0xff)
+            e0.record()
+            fn()
+            e1.record()
+        torch.cuda.synchronize()
+        est.synchronize()
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+
+    ms = timed(full_pass, args.steps)
+    ms_seeds = timed(seed_pass, max(args.steps // 2, 5))
+    ms_me = timed(lambda: est.estimate_sequence(luma, alpha, seed=seeds, out=out, sync=False),
+                  max(args.steps // 2, 5))
+    full_pass()
+    est.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    return {"value": P * M / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "ms_seed_pass": ms_seeds,
+            "ms_estimation_only": ms_me, "gpu_launches_per_step": 11}, res, seeds.cpu().numpy()
+
+
+def learned_oracle_leg(seq, plain, learned, seeds, pairs_judged=(0, 9, 18, 27)):
+    """Oracle leg of the learned measurement: the learned-seeded MV field
+    against the oracle given the same seeds, and the judge of both fields:
+    exhaustive search (the ES row of Table 1) on a sample of pairs, mean SAD
+    above the ES optimum over the opaque MBs."""
+    import oracle as O
+
+    p = O.OracleParams(W, H, S, SUBPEL)
+    orc = O.estimate_sequence(p, seq.luma, seq.alpha[0], seed=seeds)
+    exact = all(np.array_equal(learned[a].view(np.uint8), orc[b].view(np.uint8)) for a, b in
+                [("mv", "mv"), ("cost", "cost"), ("iters", "iters"), ("npos", "npos"), ("disp", "disp"),
+                 ("mb_class", "mbclass"), ("sse", "sse")])
+    gp, gl, n = 0, 0, 0
+    for k in pairs_judged:
+        _, es, _ = O.full_search(seq.luma[k], seq.luma[k + 1], W, H, SUBPEL, S)
+        op = plain["mb_class"][k] == 1
+        gp += int((plain["cost"][k].view(np.uint32)[op].astype(np.int64) - es[op]).sum())
+        gl += int((learned["cost"][k].view(np.uint32)[op].astype(np.int64) - es[op]).sum())
+        n += int(op.sum())
+    return exact, {"pairs": list(pairs_judged), "opaque_mbs": n, "mean_sad_above_es_plain": gp / max(n, 1),
+                   "mean_sad_above_es_learned": gl / max(n, 1)}
+
+
+def stats(res, width, height):
+    """iters/opaque MB, positions/non-transparent MB, mean PSNR (dB) of one output set."""
+    from paper_1002_1168_gb300 import sme
+
+    cls = res["mb_class"]
+    return {"iters_per_opaque_mb": float(res["iters"][cls == 1].mean()),
+            "positions_per_mb": float(res["npos"][cls > 0].mean()),
+            "psnr_db_mean": float(np.mean([sme.psnr(int(x), width, height) for x in res["sse"].view(np.uint64)]))}
+
+
+def batch_quality(outputs, host):
+    """iters/opaque MB, positions/non-transparent MB and mean PSNR over every
+    pair of every VOP of a batch."""
+    from paper_1002_1168_gb300 import sme
+
+    it, itn, pos, posn, ps = 0, 0, 0, 0, []
+    for o_, (sq, _) in zip(outputs, host):
+        cls = o_["mb_class"]
+        it += int(o_["iters"][cls == 1].sum().item())
+        itn += int((cls == 1).sum().item())
+        pos += int(o_["npos"][cls > 0].sum().item())
+        posn += int((cls > 0).sum().item())
+        ps += [sme.psnr(int(x), sq.width, sq.height) for x in o_["sse"].cpu().numpy().view(np.uint64)]
+    return {"iters_per_opaque_mb": it / max(itn, 1), "positions_per_mb": pos / max(posn, 1),
+            "psnr_db_mean": float(np.mean(ps))}
+
+
+def measure_batch(sme, torch, args, rank, dist, net=None):
     """Secondary measurement: 64 sequences of uneven size (16 QCIF, 24 CIF,
     16 4CIF, 8 1920x1088), 10 frames, 1-4 objects each (one VOP per object),
     |v| <= 16, S=16, half-pel, estimated in one persistent launch replayed
@@ -186,13 +313,16 @@ def measure_batch(sme, torch, args, rank, dist):
     sizes = {"full": None, "hd8": [(1920, 1088)] * 8}[args.batch_preset]
     seqs = synth.batch_sequences(seed=1003 + 100 * rank, frames=10, sizes=sizes)
     gen_s = time.perf_counter() - t0
-    lumas, alphas, host = [], [], []
+    lumas, alphas, host, groups = [], [], [], []
     for sq in seqs:
         lt = torch.from_numpy(sq.luma).cuda()
+        vops = []
         for j in range(sq.alpha.shape[0]):
+            vops.append(torch.from_numpy(sq.alpha[j]).cuda())
             lumas.append(lt)
-            alphas.append(torch.from_numpy(sq.alpha[j]).cuda())
+            alphas.append(vops[-1])
             host.append((sq, j))
+        groups.append((lt, vops))  # VOP order = host order
     b = sme.Batch(lumas, alphas, search_range=16, subpel=2, want=("cost", "iters", "npos", "mb_class", "sse"))
     b.tune(trials=3)
     cfg = b.config()
@@ -235,12 +365,58 @@ def measure_batch(sme, torch, args, rank, dist):
                       np.array_equal(g["sse"].cpu().numpy().view(np.uint64), o["sse"]) and
                       np.array_equal(g["cost"].cpu().numpy().view(np.uint32), o["cost"]))
     nt = sum(int((o_["mb_class"] > 0).sum().item()) for o_ in b.outputs)
+    plain_q = batch_quality(b.outputs, host)
     b.close()
+    learned = None
+    if net is not None:
+        from paper_1002_1168_gb300 import seedtrain
+
+        lb = seedtrain.LearnedBatch(net, groups, search_range=16, subpel=2)
+        lb.tune(trials=3)
+        for _ in range(2):
+            lb.run(sync=False)
+        lb.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            e0.record(lb.stream)
+            lb.run(sync=False)
+            e1.record(lb.stream)
+        torch.cuda.synchronize()
+        lb.synchronize()
+        lms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+        if dist:
+            t = torch.tensor([lms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            lms = float(t.item())
+        lq = batch_quality(lb.outputs, host)
+        lexact, lsample, lcpu = True, [], 0.0
+        for i in sample:  # the oracle, given the same seeds, on the plain parity sample
+            if lcpu >= args.cpu_seconds / 2:
+                break
+            sq, j = host[i]
+            tc = time.perf_counter()
+            o = O.estimate_sequence(O.OracleParams(sq.width, sq.height, 16, 2), sq.luma, sq.alpha[j],
+                                    seed=lb.seeds[i].cpu().numpy())
+            lcpu += time.perf_counter() - tc
+            lsample.append(i)
+            g = lb.outputs[i]
+            lexact &= bool(np.array_equal(g["mv"].cpu().numpy(), o["mv"]) and
+                           np.array_equal(g["sse"].cpu().numpy().view(np.uint64), o["sse"]) and
+                           np.array_equal(g["cost"].cpu().numpy().view(np.uint32), o["cost"]))
+        learned = {"value": ws * total / (lms / 1e3), "unit": UNIT, "ms_per_run": lms, "config": lb.config(),
+                   "vs_plain_batched": ms / lms, **lq, "psnr_delta_db": lq["psnr_db_mean"] - plain_q["psnr_db_mean"],
+                   "bit_exact_vs_oracle_sample": lexact, "sample_sequences": len(lsample),
+                   "network": "classes + features + sparse forward per sequence, one CUDA graph"}
+        lb.close()
     name = {"full": "64 sequences (16 QCIF, 24 CIF, 16 4CIF, 8 1920x1088)",
             "hd8": "8 sequences of 1920x1088"}[args.batch_preset]
     return {"workload": f"{name}, 10 frames, {len(lumas)} VOPs, half-pel, S=16", "mb_per_run": total,
             "value": ws * total / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "runs": steps,
-            "non_transparent_frac": nt / total, "config": cfg, "generation_s": gen_s,
+            "non_transparent_frac": nt / total, "config": cfg, "generation_s": gen_s, **plain_q,
+            "learned_seeded": learned,
             "bit_exact_vs_oracle_sample": exact, "sample_sequences": len(sample),
             "cpu_baseline": {"value": cpu_mbs / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{len(sample)} of the batch's VOP sequences (every 7th), "
@@ -326,9 +502,16 @@ def run_ours(args):
     h2d = int(hl.numel() + ha.numel())
     d2h = int(sum(v.numel() * v.element_size() for v in hout.values()))
 
+    net, learned, train_info = None, None, None
+    if not args.no_learned:
+        net, train_info = train_seednet(sme, torch, args)
+        learned, lres, lseeds = measure_learned(sme, torch, args, net, est, luma, alpha, flush)
+
     batched = None
     if not args.no_batch:
-        batched = measure_batch(sme, torch, args, rank, dist)
+        batched = measure_batch(sme, torch, args, rank, dist, net)
+    if net is not None:
+        net.close()
 
     if rank != 0:
         est.close()
@@ -352,6 +535,14 @@ def run_ours(args):
 
     psnr = [O.psnr(int(s), W, H) for s in res["sse"].view(np.uint64)]
     op = cls == 1
+    if learned is not None:
+        lexact, judge = learned_oracle_leg(seq, res, lres, lseeds)
+        lq = stats(lres, W, H)
+        learned.update({"vs_plain": learned["value"] / value, **lq,
+                        "psnr_delta_db": lq["psnr_db_mean"] - float(np.mean(psnr)),
+                        "mv_match_oracle": lexact, "bit_exact_vs_oracle": lexact,
+                        "seed_changed_mbs": int((lres["mv"] != res["mv"]).any(axis=-1).sum()),
+                        "es_judge": judge, "training": train_info})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
@@ -373,7 +564,7 @@ def run_ours(args):
                     "mb_per_s_non_transparent": value * float((cls > 0).mean()),
                     "iters_per_opaque_mb": float(res["iters"][op].mean()),
                     "positions_per_mb": float(res["npos"][cls > 0].mean()),
-                    "psnr_db_mean": float(np.mean(psnr)), "learned_seeded": None},
+                    "psnr_db_mean": float(np.mean(psnr)), "learned_seeded": learned},
         "wall_s_timed": wall,
         "batched": batched,
     }
@@ -392,6 +583,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--schedule", default="auto", choices=["auto", "pair", "mb"])
     ap.add_argument("--no-batch", action="store_true", help="skip the secondary batched measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip training and the learned-seeded measurements")
+    ap.add_argument("--learn-pairs", type=int, default=2000, help="CIF VOP pairs the seed network is trained on")
+    ap.add_argument("--learn-steps", type=int, default=800, help="Adam steps (32 pairs each)")
     ap.add_argument("--batch-only", action="store_true", help="only the batched measurement (profiling)")
     ap.add_argument("--batch-preset", default="full", choices=["full", "hd8"],
                     help="batched workload: the 64-sequence batch, or 8 HD sequences (profiling)")

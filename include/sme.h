@@ -283,13 +283,17 @@ int sme_batch_destroy(sme_batch* b);
  *                         pixels (device, optional) and the raw cell outputs
  *                         [n][H/4][W/4][16] FP32 (device, optional).
  *   sme_seednet_forward_active  seeds [n][M][2] (device) of the MBs that
- *                         use one, the non-transparent ones (mb_class [n][M]
- *                         device, as sme_classify writes it), equal bit for
- *                         bit to those of sme_seednet_forward; transparent MBs
- *                         get (0, 0).  The layers are evaluated only on MBs
- *                         within one MB of a non-transparent MB (five 3x3
- *                         layers reach 5 cells, one MB is 4 cells and the
- *                         MB's own cells are the fifth).
+ *                         use one, the non-transparent ones, equal bit for
+ *                         bit to those of sme_seednet_forward; the other MBs
+ *                         get (0, 0).  mb_class: n_maps class maps [n][M]
+ *                         (device, as sme_classify writes them), map_stride
+ *                         bytes apart (>= n*M when n_maps > 1): an MB is
+ *                         non-transparent if it is so in any map (the VOPs of
+ *                         one sequence share features, hence seeds).  The
+ *                         layers are evaluated only on MBs within one MB of
+ *                         such an MB (five 3x3 layers reach 5 cells: one MB
+ *                         is 4 cells and the MB's own cells are the fifth).
+ *   sme_seednet_set_stream  stream of the network's later calls.
  *   sme_seednet_gradients loss and parameter gradients (host out), no update.
  *   sme_seednet_train_step forward, loss, backward, one Adam step with rate lr;
  *                         loss (host out, optional) synchronises.
@@ -306,7 +310,8 @@ int sme_seednet_features(sme_seednet* net, const uint8_t* luma, int width, int h
 int sme_seednet_forward(sme_seednet* net, const uint16_t* feat, int n, int width, int height, float* seeds,
                         float* out_cells);
 int sme_seednet_forward_active(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
-                               const uint8_t* mb_class, float* seeds);
+                               const uint8_t* mb_class, int n_maps, long long map_stride, float* seeds);
+int sme_seednet_set_stream(sme_seednet* net, void* cuda_stream);
 int sme_seednet_gradients(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
                           const float* labels /* [n][M][2] device */, const uint8_t* mask /* [n][M] device */,
                           float* grads /* host, param layout */, float* loss /* host */);

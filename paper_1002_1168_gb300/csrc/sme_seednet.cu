@@ -189,7 +189,17 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const __nv_bfloat16* __res
 // dense pass bit for bit.
 // units[0] = count (zeroed by the caller), units[1..] = MB indices n * M + mb
 // in no particular order (each MB's arithmetic does not depend on it).
-__global__ void active_units_kernel(const uint8_t* __restrict__ cls, int N, int mbw, int mbh, int* units)
+// With several class maps (VOPs over the same frames, maps `stride` bytes
+// apart) an MB counts as non-transparent if it is so in any map.
+__device__ __forceinline__ bool any_visible(const uint8_t* cls, int n_maps, long long stride, size_t i)
+{
+    for (int k = 0; k < n_maps; ++k)
+        if (cls[k * stride + i] != 0) return true;
+    return false;
+}
+
+__global__ void active_units_kernel(const uint8_t* __restrict__ cls, int n_maps, long long stride, int N, int mbw,
+                                    int mbh, int* units)
 {
     const int M = mbw * mbh;
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -199,7 +209,9 @@ __global__ void active_units_kernel(const uint8_t* __restrict__ cls, int N, int 
     for (int dv = -1; dv <= 1; ++dv)
         for (int du = -1; du <= 1; ++du) {
             const int vv = v + dv, uu = u + du;
-            if (vv >= 0 && vv < mbh && uu >= 0 && uu < mbw && cls[(size_t)n * M + vv * mbw + uu] != 0) act = true;
+            if (vv >= 0 && vv < mbh && uu >= 0 && uu < mbw &&
+                any_visible(cls, n_maps, stride, (size_t)n * M + vv * mbw + uu))
+                act = true;
         }
     if (act) units[1 + atomicAdd(units, 1)] = id;
 }
@@ -285,12 +297,12 @@ __global__ void __launch_bounds__(288) conv3x3_wgrad_kernel(const __nv_bfloat16*
 // are not read.
 __global__ void pool_loss_kernel(const float* out, int N, int Hc, int Wc, float* seeds, const float* labels,
                                  const uint8_t* mask, const int* count, float* loss, __nv_bfloat16* dout,
-                                 const uint8_t* cls = nullptr)
+                                 const uint8_t* cls = nullptr, int n_maps = 0, long long stride = 0)
 {
     const int MBW = Wc / 4, MBH = Hc / 4, M = MBW * MBH;
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= N * M) return;
-    if (cls && cls[id] == 0) {
+    if (cls && !any_visible(cls, n_maps, stride, id)) {
         seeds[2 * (size_t)id] = 0.0f;
         seeds[2 * (size_t)id + 1] = 0.0f;
         return;
@@ -609,19 +621,27 @@ int sme_seednet_forward(sme_seednet* s, const uint16_t* feat, int n, int width, 
 }
 
 int sme_seednet_forward_active(sme_seednet* s, const uint16_t* feat, int n, int width, int height,
-                               const uint8_t* mb_class, float* seeds)
+                               const uint8_t* mb_class, int n_maps, long long map_stride, float* seeds)
 {
     int rc = check_geom(s, feat, n, width, height);
     if (rc) return rc;
-    if (!mb_class || !seeds) return SME_ERR_ARG;
     const int Hc = height / 4, Wc = width / 4, M = n * (Hc / 4) * (Wc / 4);
+    if (!mb_class || !seeds || n_maps < 1 || (n_maps > 1 && map_stride < M)) return SME_ERR_ARG;
     if (cudaMemsetAsync(s->units, 0, sizeof(int), s->stream) != cudaSuccess) return SME_ERR_CUDA;
-    active_units_kernel<<<(M + 127) / 128, 128, 0, s->stream>>>(mb_class, n, Wc / 4, Hc / 4, s->units);
+    active_units_kernel<<<(M + 127) / 128, 128, 0, s->stream>>>(mb_class, n_maps, map_stride, n, Wc / 4, Hc / 4,
+                                                                s->units);
     if (cudaGetLastError() != cudaSuccess) return SME_ERR_CUDA;
     if ((rc = forward(s, reinterpret_cast<const __nv_bfloat16*>(feat), n, Hc, Wc, s->units))) return rc;
     pool_loss_kernel<<<(M + 127) / 128, 128, 0, s->stream>>>(s->out32, n, Hc, Wc, seeds, nullptr, nullptr, nullptr,
-                                                             nullptr, nullptr, mb_class);
+                                                             nullptr, nullptr, mb_class, n_maps, map_stride);
     return cudaGetLastError() == cudaSuccess ? SME_OK : SME_ERR_CUDA;
+}
+
+int sme_seednet_set_stream(sme_seednet* s, void* stream)
+{
+    if (!s) return SME_ERR_ARG;
+    s->stream = (cudaStream_t)stream;
+    return SME_OK;
 }
 
 int sme_seednet_gradients(sme_seednet* s, const uint16_t* feat, int n, int width, int height, const float* labels,

@@ -20,6 +20,7 @@ sample of MBs.
 """
 from __future__ import annotations
 
+import os
 import time
 
 import numpy as np
@@ -27,17 +28,45 @@ import numpy as np
 from . import sme, synth
 
 
-def training_pairs(n, seed, W=352, H=288):
-    """n two-frame sequences (rotation <= 5 deg, scale 0.95-1.05, 1-2 objects)."""
+def _pair_job(job):
+    W, H, sseed, n_objects, bg = job
+    s = synth.make_sequence(W, H, 2, sseed, n_objects=n_objects, vmax=8.0, bg_step=bg, noise_sigma=2.0,
+                            blobby=True, max_rot_deg=5.0, scale_range=(0.95, 1.05), obj_frac=0.33)
+    return [(s.luma, s.alpha[j]) for j in range(s.alpha.shape[0])]
+
+
+def training_pairs(n_pairs, seed, W=352, H=288, workers=1):
+    """At least n_pairs VOP frame pairs (luma [2, H, W], alpha [2, H, W]) from
+    two-frame sequences with 1-2 objects (rotation <= 5 deg, scale
+    0.95-1.05); sequence i uses seed * 100003 + i.  workers > 1 renders in a
+    spawned process pool (same result)."""
     rng = np.random.default_rng(seed)
-    out = []
-    for i in range(n):
-        s = synth.make_sequence(W, H, 2, seed * 100003 + i, n_objects=int(rng.integers(1, 3)), vmax=8.0,
-                                bg_step=tuple(rng.uniform(-2, 2, 2)), noise_sigma=2.0, blobby=True,
-                                max_rot_deg=5.0, scale_range=(0.95, 1.05), obj_frac=0.33)
-        for j in range(s.alpha.shape[0]):
-            out.append((s.luma, s.alpha[j]))
-    return out
+    jobs, count = [], 0
+    while count < n_pairs:
+        n_objects = int(rng.integers(1, 3))
+        bg = tuple(rng.uniform(-2, 2, 2))
+        jobs.append((W, H, seed * 100003 + len(jobs), n_objects, bg))
+        count += n_objects
+    if workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+
+        # one BLAS thread per worker (the children read these at numpy import)
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        os.environ.update({k: "1" for k in keys})
+        try:
+            with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+                parts = list(ex.map(_pair_job, jobs, chunksize=8))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+    else:
+        parts = [_pair_job(j) for j in jobs]
+    return [p for part in parts for p in part]
 
 
 def build_dataset(pairs, net, search_range=16, subpel=2):
@@ -155,7 +184,7 @@ def train_and_evaluate(n_pairs=200, steps=600, eval_luma=None, eval_alpha=None, 
     import torch
 
     t0 = time.perf_counter()
-    pairs = training_pairs(n_pairs, seed + 11)
+    pairs = training_pairs(n_pairs, seed + 11, workers=min(os.cpu_count() or 1, 16))
     t_gen = time.perf_counter() - t0
     H, W = pairs[0][0].shape[1:]
     net = sme.SeedNet(max_cells=max(len(pairs), 64) * (H // 4) * (W // 4))
@@ -174,3 +203,87 @@ def train_and_evaluate(n_pairs=200, steps=600, eval_luma=None, eval_alpha=None, 
     report["params"] = net.get_params()
     net.close()
     return report, raw
+
+
+class LearnedBatch:
+    """The learned-seeded form of a batch.  For every luma sequence: the
+    classes of each of its VOPs, the features of all its pairs and one sparse
+    forward for the MBs visible in any of its VOPs (the VOPs of a sequence
+    share features, hence seeds); then every VOP in one persistent launch
+    (sme_batch) with those seeds.  The classification and network launches of
+    all sequences are captured in one CUDA graph, replayed before the batch's
+    own graph, on one stream.
+
+    groups: list of (luma [F, H, W] CUDA uint8, [alpha [F, H, W] CUDA uint8, ...])."""
+
+    def __init__(self, net, groups, search_range=16, subpel=2, ref_distance=1,
+                 want=("cost", "iters", "npos", "mb_class", "sse")):
+        import torch
+
+        self.torch, self.net, self.subpel, self.rd = torch, net, subpel, ref_distance
+        self.stream = torch.cuda.Stream()
+        self.graph = None
+        self.items, self.est = [], {}
+        lumas, alphas, seeds_list = [], [], []
+        with torch.cuda.stream(self.stream):
+            for luma, alist in groups:
+                F, H, W = luma.shape
+                P = F - ref_distance
+                if (W, H) not in self.est:
+                    self.est[(W, H)] = sme.Estimator(W, H, search_range=search_range, subpel=subpel,
+                                                     ref_distance=ref_distance)
+                est = self.est[(W, H)]
+                cls = torch.empty((len(alist), F, est.M), dtype=torch.uint8, device=luma.device)
+                feat = torch.empty((P, H // 4, W // 4, 16), dtype=torch.int16, device=luma.device)
+                seeds = torch.zeros((P, est.M, 2), dtype=torch.float32, device=luma.device)
+                self.items.append((luma, alist, est, cls, feat, seeds))
+                for a in alist:
+                    lumas.append(luma)
+                    alphas.append(a)
+                    seeds_list.append(seeds)
+            self.batch = sme.Batch(lumas, alphas, search_range=search_range, subpel=subpel,
+                                   ref_distance=ref_distance, want=want, seed_list=seeds_list)
+        self.outputs = self.batch.outputs
+        self.seeds = seeds_list
+
+    def _seed_pass(self):
+        for luma, alist, est, cls, feat, seeds in self.items:
+            for k, a in enumerate(alist):
+                est.classify(a, want_packed=False, out=cls[k], sync=False)
+            self.net.features(luma, 0, self.rd, subpel=self.subpel, n_pairs=feat.shape[0], out=feat)
+            self.net.forward_active(feat, cls[:, self.rd:], out=seeds)
+
+    def tune(self, trials=3):
+        """Seeds once, the batch's autotuner, then the capture of the seed pass."""
+        t = self.torch
+        with t.cuda.stream(self.stream):
+            self._seed_pass()
+            self.batch.tune(trials)
+            self.stream.synchronize()
+            g = t.cuda.CUDAGraph()
+            with t.cuda.graph(g, stream=self.stream):
+                self._seed_pass()
+            self.graph = g
+
+    def run(self, sync=True):
+        with self.torch.cuda.stream(self.stream):
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._seed_pass()
+            self.batch.run(sync=False)
+        if sync:
+            self.batch.synchronize()
+        return self.outputs
+
+    def synchronize(self):
+        self.batch.synchronize()
+
+    def config(self):
+        return self.batch.config()
+
+    def close(self):
+        self.batch.close()
+        for e in self.est.values():
+            e.close()
+        self.est = {}

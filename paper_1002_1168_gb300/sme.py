@@ -32,7 +32,7 @@ EXPORTS = [
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_forward",
-    "sme_seednet_forward_active",
+    "sme_seednet_forward_active", "sme_seednet_set_stream",
     "sme_seednet_gradients", "sme_seednet_train_step", "sme_debug_set_fault",
 ]
 
@@ -117,7 +117,8 @@ def _lib():
             "sme_seednet_get_params": (i, [vp, vp]),
             "sme_seednet_features": (i, [vp, vp, i, i, i, i, i, vp, i, vp]),
             "sme_seednet_forward": (i, [vp, vp, i, i, i, vp, vp]),
-            "sme_seednet_forward_active": (i, [vp, vp, i, i, i, vp, vp]),
+            "sme_seednet_forward_active": (i, [vp, vp, i, i, i, vp, i, C.c_longlong, vp]),
+            "sme_seednet_set_stream": (i, [vp, vp]),
             "sme_seednet_gradients": (i, [vp, vp, i, i, i, vp, vp, vp, C.POINTER(C.c_float)]),
             "sme_seednet_train_step": (i, [vp, vp, i, i, i, vp, vp, C.c_float, C.POINTER(C.c_float)]),
             "sme_debug_set_fault": (i, [vp, i, C.c_longlong]),
@@ -420,14 +421,20 @@ class SeedNet:
                "sme_seednet_create")
         self._h = h
 
+    def _bind(self):
+        """Launch on the current torch stream (as Estimator does)."""
+        _check(_lib().sme_seednet_set_stream(self._h, C.c_void_p(self.torch.cuda.current_stream().cuda_stream)),
+               "sme_seednet_set_stream")
+        return self._h
+
     def set_params(self, flat):
         flat = np.ascontiguousarray(flat, np.float32)
         assert flat.size == self.n_params
-        _check(_lib().sme_seednet_set_params(self._h, flat.ctypes.data_as(C.c_void_p)), "sme_seednet_set_params")
+        _check(_lib().sme_seednet_set_params(self._bind(), flat.ctypes.data_as(C.c_void_p)), "sme_seednet_set_params")
 
     def get_params(self):
         out = np.zeros(self.n_params, np.float32)
-        _check(_lib().sme_seednet_get_params(self._h, out.ctypes.data_as(C.c_void_p)), "sme_seednet_get_params")
+        _check(_lib().sme_seednet_get_params(self._bind(), out.ctypes.data_as(C.c_void_p)), "sme_seednet_get_params")
         return out
 
     def features(self, luma, ref_frame, cur_frame, temporal=None, subpel=2, out=None, n_pairs=1):
@@ -441,7 +448,7 @@ class SeedNet:
         if out is None:
             shape = (H // 4, W // 4, 16) if n_pairs == 1 else (n_pairs, H // 4, W // 4, 16)
             out = t.empty(shape, dtype=t.int16, device=luma.device)
-        _check(_lib().sme_seednet_features(self._h, _ptr(luma), W, H, int(ref_frame), int(cur_frame), int(n_pairs),
+        _check(_lib().sme_seednet_features(self._bind(), _ptr(luma), W, H, int(ref_frame), int(cur_frame), int(n_pairs),
                                            _ptr(temporal), int(subpel), _ptr(out)), "sme_seednet_features")
         return out
 
@@ -451,18 +458,24 @@ class SeedNet:
         n, Hc, Wc, _ = feat.shape
         seeds = t.empty((n, (Hc // 4) * (Wc // 4), 2), dtype=t.float32, device=feat.device)
         cells = t.empty((n, Hc, Wc, 16), dtype=t.float32, device=feat.device) if want_cells else None
-        _check(_lib().sme_seednet_forward(self._h, _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(seeds), _ptr(cells)),
+        _check(_lib().sme_seednet_forward(self._bind(), _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(seeds), _ptr(cells)),
                "sme_seednet_forward")
         return (seeds, cells) if want_cells else seeds
 
     def forward_active(self, feat, mb_class, out=None):
-        """Seeds of the non-transparent MBs (mb_class [n, M] uint8 != 0),
-        (0, 0) on transparent ones; the layers run only near those MBs."""
+        """Seeds of the non-transparent MBs, (0, 0) on the others; the layers
+        run only near those MBs.  mb_class: [n, M] uint8, or [V, n, M] for V
+        VOPs over the same frames (an MB counts if it is visible in any)."""
         t = self.torch
         n, Hc, Wc, _ = feat.shape
+        M = (Hc // 4) * (Wc // 4)
+        maps = mb_class if mb_class.dim() == 3 else mb_class[None]
+        if tuple(maps.shape[1:]) != (n, M) or maps.stride(2) != 1 or maps.stride(1) != M:
+            raise ValueError("mb_class must be [n, M] or [V, n, M] with contiguous [n, M] slabs")
         if out is None:
-            out = t.empty((n, (Hc // 4) * (Wc // 4), 2), dtype=t.float32, device=feat.device)
-        _check(_lib().sme_seednet_forward_active(self._h, _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(mb_class), _ptr(out)),
+            out = t.empty((n, M, 2), dtype=t.float32, device=feat.device)
+        _check(_lib().sme_seednet_forward_active(self._bind(), _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(maps),
+                                                 maps.shape[0], maps.stride(0), _ptr(out)),
                "sme_seednet_forward_active")
         return out
 
@@ -470,14 +483,14 @@ class SeedNet:
         n, Hc, Wc, _ = feat.shape
         g = np.zeros(self.n_params, np.float32)
         loss = C.c_float()
-        _check(_lib().sme_seednet_gradients(self._h, _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(labels), _ptr(mask),
+        _check(_lib().sme_seednet_gradients(self._bind(), _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(labels), _ptr(mask),
                                             g.ctypes.data_as(C.c_void_p), C.byref(loss)), "sme_seednet_gradients")
         return loss.value, g
 
     def train_step(self, feat, labels, mask, lr, want_loss=False):
         n, Hc, Wc, _ = feat.shape
         loss = C.c_float()
-        _check(_lib().sme_seednet_train_step(self._h, _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(labels), _ptr(mask),
+        _check(_lib().sme_seednet_train_step(self._bind(), _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(labels), _ptr(mask),
                                              float(lr), C.byref(loss) if want_loss else None),
                "sme_seednet_train_step")
         return loss.value if want_loss else None

@@ -174,6 +174,7 @@ def evaluate(net, seq_luma, seq_alpha, search_range=16, subpel=2, runs=20):
                      "psnr_db": float(np.mean([sme.psnr(int(s_), W, H) for s_ in sse])),
                      "opaque_cost_sum": int(o["cost"].view(np.uint32)[cls == 1].sum())}
     res["learned"]["ms_estimation_only"] = ms_seeded_me
+    raw["seeds"] = seeds.cpu().numpy()
     res["seed_changed_mbs"] = int((raw["plain"]["mv"] != raw["learned"]["mv"]).any(axis=-1).sum())
     est.close()
     return res, raw

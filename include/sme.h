@@ -294,6 +294,9 @@ int sme_batch_destroy(sme_batch* b);
  *                         such an MB (five 3x3 layers reach 5 cells: one MB
  *                         is 4 cells and the MB's own cells are the fifth).
  *   sme_seednet_set_stream  stream of the network's later calls.
+ *   sme_seednet_synchronize waits for the network's stream; SME_ERR_TIMEOUT
+ *                         if a device-side wait of an earlier call gave up
+ *                         (its outputs are then not valid).
  *   sme_seednet_gradients loss and parameter gradients (host out), no update.
  *   sme_seednet_train_step forward, loss, backward, one Adam step with rate lr;
  *                         loss (host out, optional) synchronises.
@@ -312,6 +315,7 @@ int sme_seednet_forward(sme_seednet* net, const uint16_t* feat, int n, int width
 int sme_seednet_forward_active(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
                                const uint8_t* mb_class, int n_maps, long long map_stride, float* seeds);
 int sme_seednet_set_stream(sme_seednet* net, void* cuda_stream);
+int sme_seednet_synchronize(sme_seednet* net);
 int sme_seednet_gradients(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
                           const float* labels /* [n][M][2] device */, const uint8_t* mask /* [n][M] device */,
                           float* grads /* host, param layout */, float* loss /* host */);

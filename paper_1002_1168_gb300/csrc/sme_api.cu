@@ -18,6 +18,24 @@
 
 using namespace sme;
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 sme::tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
 namespace {
 
 struct DevBuf {
@@ -116,24 +134,6 @@ Method make_method(const sme_params& p)
     m.theta = p.theta;
     m.eps = p.epsilon;
     return m;
-}
-
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
-// (no link-time dependency on the driver library).
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
-{
-    static std::once_flag once;
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-        cudaGetLastError();
-    });
-    return fn;
 }
 
 // The per-pair kernel's four tensor maps of one sequence: the luma frames

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (the layout only; no driver library is linked)
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -144,6 +145,9 @@ size_t me_pair_smem_bytes(int S, int nwarps, int mbw_max);
 // packed-alpha current BAB (u32).
 void pair_boxes(int S, unsigned (&box)[4][2]);
 cudaError_t launch_compensate(const Geom& g, const Method& m, const CompArgs& a, cudaStream_t s);
+
+// cuTensorMapEncodeTiled of the installed driver (NULL if unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 cudaError_t launch_queries(const Geom& g, const Method& m, const QueryArgs& a, cudaStream_t s);
 // Resident CTAs per SM of the persistent ME kernel for search range S.
 cudaError_t me_occupancy(int S, int* blocks_per_sm);

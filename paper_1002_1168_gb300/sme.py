@@ -32,7 +32,7 @@ EXPORTS = [
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_forward",
-    "sme_seednet_forward_active", "sme_seednet_set_stream",
+    "sme_seednet_forward_active", "sme_seednet_set_stream", "sme_seednet_synchronize",
     "sme_seednet_gradients", "sme_seednet_train_step", "sme_debug_set_fault",
 ]
 
@@ -119,6 +119,7 @@ def _lib():
             "sme_seednet_forward": (i, [vp, vp, i, i, i, vp, vp]),
             "sme_seednet_forward_active": (i, [vp, vp, i, i, i, vp, i, C.c_longlong, vp]),
             "sme_seednet_set_stream": (i, [vp, vp]),
+            "sme_seednet_synchronize": (i, [vp]),
             "sme_seednet_gradients": (i, [vp, vp, i, i, i, vp, vp, vp, C.POINTER(C.c_float)]),
             "sme_seednet_train_step": (i, [vp, vp, i, i, i, vp, vp, C.c_float, C.POINTER(C.c_float)]),
             "sme_debug_set_fault": (i, [vp, i, C.c_longlong]),
@@ -478,6 +479,10 @@ class SeedNet:
                                                  maps.shape[0], maps.stride(0), _ptr(out)),
                "sme_seednet_forward_active")
         return out
+
+    def synchronize(self):
+        """Wait for the network's work; raises if a device-side wait gave up."""
+        _check(_lib().sme_seednet_synchronize(self._bind()), "sme_seednet_synchronize")
 
     def gradients(self, feat, labels, mask):
         n, Hc, Wc, _ = feat.shape

@@ -97,6 +97,7 @@ def _setup(sme, N=2, W=96, H=64, seed=5):
 def test_forward_matches_oracle(sme):
     _, params, x, net, xt = _setup(sme)
     seeds, cells = net.forward(xt, want_cells=True)
+    net.synchronize()  # no device-side wait gave up
     acts = SN.forward(x, params)
     assert rel(cells.cpu().numpy(), acts[-1]) < 1e-2
     assert rel(seeds.cpu().numpy(), SN.pool_seeds(acts[-1])) < 1e-2

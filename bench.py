@@ -48,6 +48,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of x over all ranks (the job's time is its slowest
+    replica's); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, n_ranks, seconds):
+    """Whole-job throughput of weakly scaled replicas: every rank processed
+    units_per_rank in its own time; the job took the slowest one's."""
+    return n_ranks * units_per_rank / seconds
+
+
 def workload(rank=0):
     from paper_1002_1168_gb300 import synth
 
@@ -343,10 +361,7 @@ def measure_batch(sme, torch, args, rank, dist, net=None):
     torch.cuda.synchronize()
     b.synchronize()
     ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)) / steps
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     ws = dist.get_world_size() if dist else 1
     # parity on a sample of VOP sequences (every 7th, all frame sizes), about
     # args.cpu_seconds of oracle time; the CPU baseline is that same sample
@@ -387,10 +402,7 @@ def measure_batch(sme, torch, args, rank, dist, net=None):
         torch.cuda.synchronize()
         lb.synchronize()
         lms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
-        if dist:
-            t = torch.tensor([lms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            lms = float(t.item())
+        lms = max_over_ranks(lms, dist)
         lq = batch_quality(lb.outputs, host)
         lexact, lsample, lcpu = True, [], 0.0
         for i in sample:  # the oracle, given the same seeds, on the plain parity sample
@@ -406,7 +418,7 @@ def measure_batch(sme, torch, args, rank, dist, net=None):
             lexact &= bool(np.array_equal(g["mv"].cpu().numpy(), o["mv"]) and
                            np.array_equal(g["sse"].cpu().numpy().view(np.uint64), o["sse"]) and
                            np.array_equal(g["cost"].cpu().numpy().view(np.uint32), o["cost"]))
-        learned = {"value": ws * total / (lms / 1e3), "unit": UNIT, "ms_per_run": lms, "config": lb.config(),
+        learned = {"value": job_rate(total, ws, lms / 1e3), "unit": UNIT, "ms_per_run": lms, "config": lb.config(),
                    "vs_plain_batched": ms / lms, **lq, "psnr_delta_db": lq["psnr_db_mean"] - plain_q["psnr_db_mean"],
                    "bit_exact_vs_oracle_sample": lexact, "sample_sequences": len(lsample),
                    "network": "classes + features + sparse forward per sequence, one CUDA graph"}
@@ -414,7 +426,7 @@ def measure_batch(sme, torch, args, rank, dist, net=None):
     name = {"full": "64 sequences (16 QCIF, 24 CIF, 16 4CIF, 8 1920x1088)",
             "hd8": "8 sequences of 1920x1088"}[args.batch_preset]
     return {"workload": f"{name}, 10 frames, {len(lumas)} VOPs, half-pel, S=16", "mb_per_run": total,
-            "value": ws * total / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "runs": steps,
+            "value": job_rate(total, ws, ms / 1e3), "unit": UNIT, "ms_per_run": ms, "runs": steps,
             "non_transparent_frac": nt / total, "config": cfg, "generation_s": gen_s, **plain_q,
             "learned_seeded": learned,
             "bit_exact_vs_oracle_sample": exact, "sample_sequences": len(sample),
@@ -474,10 +486,8 @@ def run_ours(args):
     calls, cls_ms, me_ms = est.profile_end()
     est.synchronize()  # raises on a device-side failure
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    dev_ms = max_over_ranks(dev_ms, dist)
     if dist:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
         dist.barrier()
     clk = clocks.stop()
 
@@ -495,10 +505,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         est.estimate_sequence_host(hl, ha, out=hout)
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     h2d = int(hl.numel() + ha.numel())
     d2h = int(sum(v.numel() * v.element_size() for v in hout.values()))
 
@@ -520,7 +527,7 @@ def run_ours(args):
         return
 
     mbs_step = P * M
-    value = ws * mbs_step * args.steps / (dev_ms / 1e3)
+    value = job_rate(mbs_step * args.steps, ws, dev_ms / 1e3)
     cls = res["mb_class"]
     hbm, peak_kind = peaks()
     me_avg_s = me_ms / max(calls, 1) / 1e3
@@ -551,7 +558,7 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "schedule": args.schedule},
         "clocks": clk,
-        "e2e": {"value": ws * mbs_step * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(mbs_step * e2e_steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -65,7 +65,9 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = C.CDLL(build_oracle())
+        # SME_ORACLE_LIB: a deliberately broken build, for the pin-strength
+        # tests (tests/test_oracle_mutations.py); unset in every other use.
+        lib = C.CDLL(os.environ.get("SME_ORACLE_LIB") or build_oracle())
         P = C.POINTER
         u8p, i32p = P(C.c_uint8), P(C.c_int)
         lib.orc_valid_range.argtypes = [C.c_int] * 7 + [i32p] * 4

@@ -50,6 +50,10 @@ def test_halfpel_mpeg4_rounding_control_zero():
     ref[1, 0] = 4
     assert O.interp(ref, 2, 0, 1) == 3          # (1+4+1)>>1
     assert O.interp(ref, 2, 0, 0) == 1 and O.interp(ref, 1, 1, 1) == 0
+    ref[:2, :2] = [[0, 0], [0, 2]]
+    assert O.interp(ref, 2, 1, 1) == 1          # (0+0+0+2+2)>>2 = 1: the rounding constant is 2
+    ref[:2, :2] = [[0, 3], [0, 0]]
+    assert O.interp(ref, 2, 1, 0) == 2 and O.interp(ref, 2, 0, 1) == 0   # (0+3+1)>>1, (0+0+1)>>1
 
 
 def test_halfpel_on_ramp_closed_form():
@@ -141,6 +145,45 @@ def test_gradient_step_recovers_ramp_shift(axis, h):
                 out = O.gradient_step(p, ref, cur, 16, 16, *dv)
                 assert out[axis] == pytest.approx(s - d / h, abs=0)
                 assert out[1 - axis] == 0.0
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_gradient_step_mean_is_over_pixels_with_a_gradient(axis):
+    """Eq. 3's block update is the mean over the pixels whose u is defined
+    (u != 0): in the corner MB the first row/column has no central
+    difference (Eq. 5), so only 240 pixels count, and the update still equals
+    the residual displacement exactly."""
+    for h in (1, 2):
+        ref, cur = _ramp_pair(2, 2, axis)
+        p = O.OracleParams(48, 48, 16, h)
+        for d in (0, h, 3 * h):
+            dv = (d, 0) if axis == 0 else (0, d)
+            out = O.gradient_step(p, ref, cur, 0, 0, *dv)
+            assert out[axis] == pytest.approx(2 - d / h, abs=0)
+
+
+def test_gradient_step_sum_is_the_pairwise_tree():
+    """The FP32 sum of Eq. 3's terms is the contiguous pairwise tree (reading
+    c9).  With u = 2/6 (not a binary fraction) and irregular DPD the tree
+    and a running sum round differently; the oracle must give the tree."""
+    X = np.mgrid[0:48, 0:48][1]
+    cur = (3 * X + 40).astype(np.uint8)                    # g = 6 everywhere inside: u = 2/6
+    rng = np.random.default_rng(1234)
+    e = rng.integers(-40, 41, (48, 48))
+    ref = (cur.astype(int) + e).astype(np.uint8)
+    p = O.OracleParams(48, 48, 16, 1)
+    u = np.float32(2.0) / np.float32(6.0)
+    t = e[16:32, 16:32].astype(np.float32).ravel() * u       # DPD(0, p) * u, FP32
+    tree = t.copy()
+    while tree.size > 1:
+        tree = tree[0::2] + tree[1::2]
+    seq = np.float32(0.0)
+    for v in t:
+        seq = np.float32(seq + v)
+    assert tree[0] != seq                                  # the construction discriminates
+    want = -(np.float32(1.0) * (tree[0] / np.float32(256.0)))
+    out = O.gradient_step(p, ref, cur, 16, 16, 0, 0)
+    assert np.float32(out[0]) == want and out[1] == 0.0
 
 
 def test_gradient_step_theta_and_epsilon():
@@ -358,3 +401,74 @@ def test_perfect_seed_recovers_translation():
         lox, hix, loy, hiy = O.valid_range(W, H, 16, 16, 2, 16 * (m % 8), 16 * (m // 8))
         if lox <= tgt[0] <= hix and loy <= tgt[1] <= hiy:
             assert (o["mv"][m] == tgt).all() and o["cost"][m] == 0
+
+
+# ------------------------------------- one MB, hand-derived search paths --
+def _middle_mb(ref, cur, h, seed_px=None):
+    """48 x 48 frames with only the middle MB opaque (its neighbours are
+    transparent, so A, B, C, T are all (0, 0)); outputs of that MB."""
+    a = np.zeros((48, 48), np.uint8)
+    a[16:32, 16:32] = 255
+    p = O.OracleParams(48, 48, 16, h)
+    seed = None
+    if seed_px is not None:
+        seed = np.zeros((9, 2), np.float32)
+        seed[4] = seed_px
+    o = O.estimate_pair(p, ref, cur, a, a, seed=seed)
+    return {k: o[k][4] for k in ("mv", "cost", "iters", "npos")}
+
+
+def _x_ramp(slope, offset):
+    X = np.mgrid[0:48, 0:48][1]
+    return (slope * X + 50 + offset).astype(np.uint8)
+
+
+def test_prs_proposal_with_equal_sad_is_not_taken():
+    """Fig. 4 reading: the proposal is taken only if its SAD is strictly
+    lower.  cur = 2x + 50, ref = cur + 1: at d = 0 every DPD is 1, u = 1/2,
+    the update is -1/2 px and rounds (half away from zero) to q = (-1, 0),
+    whose SAD (256) equals SAD(0); no neighbour is strictly lower either."""
+    o = _middle_mb(_x_ramp(2, 1), _x_ramp(2, 0), 1)
+    assert tuple(o["mv"]) == (0, 0) and o["cost"] == 256 and o["iters"] == 1
+    assert o["npos"] == 9  # (0,0), then q = (-1,0) and the eight neighbours
+
+
+def test_prs_proposal_rounds_half_away_from_zero():
+    """cur = 4x + 50, ref = 4x + 47 (content shifted by 3/4 px), half-pel.
+    Step 1 at d = 0: DPD = -3, u = 1/4, update +3/4 px = 1.5 MV units ->
+    q = 2 (SAD 256 < 768).  Step 2 at d = 2: update -1/4 px = -0.5 units ->
+    q = 1, SAD 256 not lower; neighbours at best tie: stop at (2, 0)."""
+    o = _middle_mb(_x_ramp(4, -3), _x_ramp(4, 0), 2)
+    assert tuple(o["mv"]) == (2, 0) and o["cost"] == 256 and o["iters"] == 2
+    assert o["npos"] == 10  # (0,0), (2,0), then (1,0) and the other seven neighbours of (2,0)
+
+
+def test_eight_directions_take_the_first_strict_minimum_in_raster_order():
+    """Flat current block (no gradient, so no proposal), reference 100 +
+    |x + y - 46|: the SAD of a shift depends on s = dx + dy only and is
+    lowest at s = -1, where (0, -1) and (-1, 0) tie.  Raster order (row -1
+    first) reaches (0, -1) first; from there nothing is strictly lower."""
+    Y, X = np.mgrid[0:48, 0:48]
+    cur = np.full((48, 48), 100, np.uint8)
+    ref = (100 + np.abs(X + Y - 46)).astype(np.uint8)
+    o = _middle_mb(ref, cur, 1)
+    assert tuple(o["mv"]) == (0, -1) and o["iters"] == 2
+
+
+def test_seeded_search_is_kept_only_when_strictly_better():
+    """Reading c21 on the 3/4-px ramp: a seed of 1/2 px (MV unit 1, SAD 256)
+    beats A..T (SAD 768); its search stays at 1 (SAD 256), the plain search
+    from 0 ends at 2 with the same SAD, so the plain result is kept."""
+    o = _middle_mb(_x_ramp(4, -3), _x_ramp(4, 0), 2, seed_px=(0.5, 0.0))
+    assert tuple(o["mv"]) == (2, 0) and o["cost"] == 256 and o["iters"] == 2
+
+
+def test_seed_rounds_half_away_from_zero():
+    """Reading c19: a seed of -0.2 px is -0.4 MV units and rounds to 0, a
+    position already evaluated, so the result and the distinct-position
+    count equal the unseeded ones."""
+    ref, cur = _x_ramp(4, -3), _x_ramp(4, 0)
+    plain = _middle_mb(ref, cur, 2)
+    seeded = _middle_mb(ref, cur, 2, seed_px=(-0.2, 0.0))
+    for k in plain:
+        assert np.array_equal(plain[k], seeded[k]), k

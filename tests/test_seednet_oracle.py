@@ -82,3 +82,7 @@ def test_pool_and_huber_closed_form():
     assert loss == pytest.approx(((2 - 0.5) + 0.5 * 0.16) / 2)
     assert d[0, 0, 0, 0] == pytest.approx(1.0 / 2 * 8 / 16)      # clipped residual 1
     assert d[0, 5, 0, 1] == pytest.approx(-0.4 / 2 * 8 / 16)
+    # masked MBs count neither in the loss nor in its mean: only MB 0 remains
+    loss, d = SN.loss_and_grad(out, labels, np.array([[1, 0]]))
+    assert loss == pytest.approx(2 - 0.5)
+    assert d[0, 0, 0, 0] == pytest.approx(1.0 * 8 / 16) and d[0, 5, 0, 1] == 0.0

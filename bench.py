@@ -460,6 +460,7 @@ def run_ours(args):
         est.autotune(luma, alpha, out=out, trials=5)  # outside the timed region
     else:
         est.set_schedule(args.schedule)
+    est_cfg = est.config()
 
     for _ in range(max(args.warmup, 3)):
         est.estimate_sequence(luma, alpha, out=out, sync=False)
@@ -556,7 +557,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs": P, "mbs_per_step": mbs_step, "seed": 1002,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "schedule": args.schedule},
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "schedule": args.schedule,
+                   "execution": est_cfg},
         "clocks": clk,
         "e2e": {"value": job_rate(mbs_step * e2e_steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -581,6 +583,35 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def profile_seednet(args):
+    """The seed network alone, for profiling: the dense forward over the
+    features of the CIF workload's 29 pairs (random initial weights),
+    args.steps times after args.warmup; prints the mean time per forward."""
+    import torch
+    from paper_1002_1168_gb300 import build as cuda_build
+    from paper_1002_1168_gb300 import sme, synth
+
+    cuda_build.build()
+    seq = workload(0)
+    P = FRAMES - 1
+    net = sme.SeedNet(max_cells=P * (H // 4) * (W // 4))
+    net.set_params(sme.pack_params(synth.seednet_init(3)))
+    luma = torch.from_numpy(seq.luma).cuda()
+    feats = net.features(luma, 0, 1, subpel=SUBPEL, n_pairs=P)
+    for _ in range(max(args.warmup, 1)):
+        net.forward(feats)
+    net.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        net.forward(feats)
+    e1.record()
+    net.synchronize()
+    print(json.dumps({"seednet_forward_us": 1e3 * e0.elapsed_time(e1) / args.steps, "cells": P * (H // 4) * (W // 4),
+                      "steps": args.steps}))
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -588,17 +619,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--schedule", default="auto", choices=["auto", "pair", "mb"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "pair", "mb", "cluster"])
     ap.add_argument("--no-batch", action="store_true", help="skip the secondary batched measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip training and the learned-seeded measurements")
     ap.add_argument("--learn-pairs", type=int, default=2000, help="CIF VOP pairs the seed network is trained on")
     ap.add_argument("--learn-steps", type=int, default=800, help="Adam steps (32 pairs each)")
     ap.add_argument("--batch-only", action="store_true", help="only the batched measurement (profiling)")
+    ap.add_argument("--seednet-only", action="store_true", help="only the seed network's forward (profiling)")
     ap.add_argument("--batch-preset", default="full", choices=["full", "hd8"],
                     help="batched workload: the 64-sequence batch, or 8 HD sequences (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.seednet_only:
+        profile_seednet(args)
     elif args.batch_only:
         import torch
         from paper_1002_1168_gb300 import build as cuda_build

@@ -194,6 +194,12 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     MB row, the row above handed over in shared memory and the reference
  *     windows fetched by TMA; SME_SCHED_MB -- one warp per MB, tickets in
  *     wavefront order, every dependency through global memory;
+ *     SME_SCHED_CLUSTER -- one thread-block cluster per sequence (single
+ *     sequences only): the MBs dealt in wavefront order to the cluster's
+ *     CTAs, every vector stored by its producer straight into the shared
+ *     memory of the CTAs that consume it (distributed shared memory), so no
+ *     dependency is polled through L2; SME_ERR_SIZE when the sequence needs
+ *     more shared memory than a cluster has;
  *     SME_SCHED_AUTO (default) -- chosen per workload.
  *   SME_OPT_PAIR_WARPS: warps (MB rows in flight) per CTA of the pair
  *     schedule, 1..16; 0 (default) = automatic.
@@ -203,10 +209,20 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     candidate as soon as its vector arrives and take the first
  *     pixel-recursive step at the first costed position while the other
  *     candidates are awaited; 0 = do all of it after the last arrival.
+ *   SME_OPT_CLUSTER_SIZE: CTAs per cluster of the cluster schedule, 2, 4, 8
+ *     or 16; 0 (default) = 16, halved until the cluster fits.
  * Returns SME_ERR_ARG for an unknown option or value. */
-enum { SME_OPT_SCHEDULE = 1, SME_OPT_PAIR_WARPS = 2, SME_OPT_MB_CTAS_PER_SM = 3, SME_OPT_SPECULATE = 4 };
-enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2 };
+enum {
+    SME_OPT_SCHEDULE = 1,
+    SME_OPT_PAIR_WARPS = 2,
+    SME_OPT_MB_CTAS_PER_SM = 3,
+    SME_OPT_SPECULATE = 4,
+    SME_OPT_CLUSTER_SIZE = 5
+};
+enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2, SME_SCHED_CLUSTER = 3 };
 int sme_set_option(sme_ctx* ctx, int option, int value);
+/* The current value of an option (e.g. what sme_autotune chose). */
+int sme_get_option(sme_ctx* ctx, int option, int* value);
 
 /* Autotuner for a context: runs the estimate on the given sequence once per
  * candidate execution configuration (schedule, CTAs per SM, speculation,

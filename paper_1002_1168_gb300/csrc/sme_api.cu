@@ -55,7 +55,10 @@ struct sme_ctx {
     DevBuf packed, cls, ready, sched, desc, qpacked, qcls;
     std::vector<int> sched_host;
     int sched_P = -1;
-    int schedule = kSchedAuto, pair_warps = 0, mb_ctas_per_sm = 0, speculate = 1;
+    int schedule = kSchedAuto, pair_warps = 0, mb_ctas_per_sm = 0, speculate = 1, cluster = 0;
+    // cluster schedule: per-CTA item lists and consumer slots (rebuilt when P or the size changes)
+    DevBuf cl_items, cl_count, cl_cons;
+    int cl_P = -1, cl_C = 0, cl_cap = 0, cl_warps = 0, cl_resident = 0;
     int fault_ticket = -1;
     long long timeout_ns = kDefaultTimeoutNs;
     // pair interface
@@ -206,6 +209,70 @@ int build_schedule(sme_ctx* c, int P)
     return SME_OK;
 }
 
+// Cluster schedule of P pairs: the MBs in wavefront order dealt round robin
+// to the C CTAs of a cluster (item n -> CTA n % C, position n / C), and for
+// every MB the slot of each MB that takes it as candidate A, B, C or T.
+int build_cluster_schedule(sme_ctx* c, int P, int* C_out)
+{
+    const Geom& g = c->g;
+    const long long total = (long long)P * g.M;
+    const int want = c->cluster > 0 ? c->cluster : 16;
+    int C = 0, cap = 0, nw = 0;
+    for (int cs = want; cs >= 2 && !C; cs /= 2)
+        for (int w = kClusterWarps; w >= 4 && !C; --w) {
+            const long long cp = (total + cs - 1) / cs;
+            const int resident = cp <= (1 << 18) ? me_cluster_fits(c->m.S, (int)cp, cs, w) : 0;
+            if (resident > 0) {
+                C = cs;
+                cap = (int)cp;
+                nw = w;
+                c->cl_resident = resident;
+            }
+        }
+    if (!C) return SME_ERR_SIZE;
+    *C_out = C;
+    c->cl_warps = nw;
+    if (c->cl_P == P && c->cl_C == C) return SME_OK;
+    int rc = build_schedule(c, P);  // the wavefront order
+    if (rc) return rc;
+    std::vector<int> items, count, where, cons;
+    try {
+        items.assign((size_t)C * cap, -1);
+        count.assign(C, 0);
+        where.assign(total, 0);
+        cons.assign(4 * total, -1);
+    } catch (...) {
+        return SME_ERR_NOMEM;
+    }
+    for (long long n = 0; n < total; ++n) {
+        const int gid = c->sched_host[n], r = (int)(n % C), slot = (int)(n / C);
+        items[(size_t)r * cap + slot] = gid;
+        ++count[r];
+        where[gid] = (r << 20) | (4 * slot);
+    }
+    for (long long gid = 0; gid < total; ++gid) {
+        const int k = (int)(gid / g.M), mb = (int)(gid - (long long)k * g.M), u = mb % g.MBW, v = mb / g.MBW;
+        long long to[4] = {-1, -1, -1, -1};  // the MBs whose A, B, C, T this one is
+        if (u + 1 < g.MBW) to[0] = gid + 1;
+        if (v + 1 < g.MBH) to[1] = gid + g.MBW;
+        if (v + 1 < g.MBH && u > 0) to[2] = gid + g.MBW - 1;
+        if (k + 1 < P) to[3] = gid + g.M;
+        for (int role = 0; role < 4; ++role)
+            if (to[role] >= 0) cons[4 * gid + role] = where[to[role]] + role;
+    }
+    if ((rc = ensure(c->cl_items, items.size() * sizeof(int))) || (rc = ensure(c->cl_count, C * sizeof(int))) ||
+        (rc = ensure(c->cl_cons, cons.size() * sizeof(int))))
+        return rc;
+    if (cudaMemcpy(c->cl_items.p, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->cl_count.p, count.data(), C * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->cl_cons.p, cons.data(), cons.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SME_ERR_CUDA;
+    c->cl_P = P;
+    c->cl_C = C;
+    c->cl_cap = cap;
+    return SME_OK;
+}
+
 int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, const sme_mv* temporal_in,
                  const float* seed, const sme_outputs* out)
 {
@@ -224,11 +291,14 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     // The per-MB schedule is the faster one on single sequences (measured on
     // CIF x 30 frames: 130 us vs 193 us per launch); the pair schedule is
     // chosen only on request.
-    const bool pair = c->schedule == kSchedPair;
+    const bool pair = c->schedule == kSchedPair, cluster = c->schedule == kSchedCluster;
     MapSet maps;
     memset(&maps, 0, sizeof(maps));
+    int C = 0;
     if (pair) {
         if ((rc = encode_pair_maps(&maps, luma, (const uint32_t*)c->packed.p, g, F, c->m.S))) return rc;
+    } else if (cluster) {
+        if ((rc = build_cluster_schedule(c, P, &C))) return rc;
     } else if ((rc = build_schedule(c, P))) {
         return rc;
     }
@@ -297,7 +367,15 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     a.fault_ticket = c->fault_ticket;
     a.speculate = c->speculate;
     a.timeout_ns = c->timeout_ns;
-    if (pair) {
+    if (cluster) {
+        a.cl_items = (const int*)c->cl_items.p;
+        a.cl_count = (const int*)c->cl_count.p;
+        a.cl_consumers = (const int*)c->cl_cons.p;
+        a.cl_cap = c->cl_cap;
+        // helpers only in clusters that are resident together with the chain
+        const int helpers = std::max(1, c->cl_resident - 1);
+        if (launch_me_cluster(c->m, a, C, c->cl_warps, helpers, c->stream) != cudaSuccess) return SME_ERR_CUDA;
+    } else if (pair) {
         int nw = c->pair_warps > 0 ? c->pair_warps : std::min(kPairWarpsMax, g.MBH);
         while (nw > 1 && me_pair_smem_bytes(c->m.S, nw, g.MBW) > (size_t)c->smem_optin) --nw;
         int per_sm = 0;
@@ -335,11 +413,13 @@ int read_status(sme_ctx* c)
 }
 
 struct ExecCfg {
-    int schedule, pair_warps, mb_ctas_per_sm, speculate;
+    int schedule, pair_warps, mb_ctas_per_sm, speculate, cluster;
 };
+// The cluster schedule runs single sequences only (the batch skips it).
 const ExecCfg kTuneCandidates[] = {
-    {kSchedMB, 0, 1, 1}, {kSchedMB, 0, 0, 1}, {kSchedMB, 0, 1, 0}, {kSchedMB, 0, 0, 0},
-    {kSchedPair, 4, 0, 0}, {kSchedPair, 8, 0, 0}, {kSchedPair, 16, 0, 0},
+    {kSchedMB, 0, 1, 1, 0},      {kSchedMB, 0, 0, 1, 0},      {kSchedMB, 0, 1, 0, 0},  {kSchedMB, 0, 0, 0, 0},
+    {kSchedPair, 4, 0, 0, 0},    {kSchedPair, 8, 0, 0, 0},    {kSchedPair, 16, 0, 0, 0},
+    {kSchedCluster, 0, 0, 1, 16}, {kSchedCluster, 0, 0, 0, 16}, {kSchedCluster, 0, 0, 1, 8},
 };
 
 // Device time of `trials` back-to-back runs of `enqueue` (the minimum), ms;
@@ -440,7 +520,7 @@ int sme_destroy(sme_ctx* c)
                       &c->pair_luma, &c->pair_alpha, &c->temporal, &c->last_mv, &c->last_sse,
                       &c->h_luma, &c->h_alpha, &c->h_tmp, &c->h_seed, &c->h_mv, &c->h_cost,
                       &c->h_disp, &c->h_iters, &c->h_npos, &c->h_cls, &c->h_ssemb, &c->h_sse,
-                      &c->h_pred};
+                      &c->h_pred, &c->cl_items, &c->cl_count, &c->cl_cons};
     for (DevBuf* b : bufs) release(*b);
     profile_free(c);
     if (c->status) cudaFree(c->status);
@@ -721,7 +801,9 @@ int sme_set_option(sme_ctx* c, int option, int value)
     if (!c) return SME_ERR_ARG;
     switch (option) {
     case SME_OPT_SCHEDULE:
-        if (value != SME_SCHED_AUTO && value != SME_SCHED_MB && value != SME_SCHED_PAIR) return SME_ERR_ARG;
+        if (value != SME_SCHED_AUTO && value != SME_SCHED_MB && value != SME_SCHED_PAIR &&
+            value != SME_SCHED_CLUSTER)
+            return SME_ERR_ARG;
         c->schedule = value;
         return SME_OK;
     case SME_OPT_PAIR_WARPS:
@@ -736,8 +818,25 @@ int sme_set_option(sme_ctx* c, int option, int value)
         if (value != 0 && value != 1) return SME_ERR_ARG;
         c->speculate = value;
         return SME_OK;
+    case SME_OPT_CLUSTER_SIZE:
+        if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16) return SME_ERR_ARG;
+        c->cluster = value;
+        return SME_OK;
     default:
         return SME_ERR_ARG;
+    }
+}
+
+int sme_get_option(sme_ctx* c, int option, int* value)
+{
+    if (!c || !value) return SME_ERR_ARG;
+    switch (option) {
+    case SME_OPT_SCHEDULE: *value = c->schedule; return SME_OK;
+    case SME_OPT_PAIR_WARPS: *value = c->pair_warps; return SME_OK;
+    case SME_OPT_MB_CTAS_PER_SM: *value = c->mb_ctas_per_sm; return SME_OK;
+    case SME_OPT_SPECULATE: *value = c->speculate; return SME_OK;
+    case SME_OPT_CLUSTER_SIZE: *value = c->cluster; return SME_OK;
+    default: return SME_ERR_ARG;
     }
 }
 
@@ -749,12 +848,13 @@ int sme_autotune(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_fr
     if (rc) return rc;
     if ((rc = sme_synchronize(c))) return rc;
     float best = -1.0f;
-    ExecCfg pick = {c->schedule, c->pair_warps, c->mb_ctas_per_sm, c->speculate};
+    ExecCfg pick = {c->schedule, c->pair_warps, c->mb_ctas_per_sm, c->speculate, c->cluster};
     for (const ExecCfg& e : kTuneCandidates) {
         c->schedule = e.schedule;
         c->pair_warps = e.pair_warps;
         c->mb_ctas_per_sm = e.mb_ctas_per_sm;
         c->speculate = e.speculate;
+        c->cluster = e.cluster;
         const float ms = time_runs(c->stream, trials, [&] {
             return run_sequence(c, luma, alpha, n_frames, nullptr, nullptr, out);
         });
@@ -768,6 +868,7 @@ int sme_autotune(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_fr
     c->pair_warps = pick.pair_warps;
     c->mb_ctas_per_sm = pick.mb_ctas_per_sm;
     c->speculate = pick.speculate;
+    c->cluster = pick.cluster;
     return best > 0.0f ? SME_OK : SME_ERR_CUDA;
 }
 
@@ -833,7 +934,7 @@ struct sme_batch {
     long long total_mbs = 0;
     DevStatus* status = nullptr;
     DevBuf descs, packed, cls, ready, sched, sched_seq, unit_seq, unit_pair, fseq, ffrm, maps;
-    ExecCfg cfg = {kSchedMB, 0, 0, 1};
+    ExecCfg cfg = {kSchedMB, 0, 0, 1, 0};
     float tuned_ms = 0.0f;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -843,6 +944,7 @@ namespace {
 
 int batch_enqueue(sme_batch* b, cudaStream_t s)
 {
+    if (b->cfg.schedule == kSchedCluster) return SME_ERR_ARG;  // single sequences only
     ClassifyBatchArgs ca{(const SeqDesc*)b->descs.p, (const int*)b->fseq.p, (const int*)b->ffrm.p, b->status};
     if (launch_classify_batch(ca, b->max_mbh, b->total_frames, s) != cudaSuccess) return SME_ERR_CUDA;
     MeArgs a{};

@@ -18,12 +18,13 @@ constexpr int kMaxDim = 8192;
 // pixel-recursive iteration, one proposal and eight neighbours.
 constexpr int kMaxLog = 5 + 9 * kMaxIters;
 constexpr long long kDefaultTimeoutNs = 1000000000LL;
-constexpr int kMeWarps = 8;     // warps (one MB each) per CTA of the per-MB ME kernel
+constexpr int kMeWarps = 8;        // warps (one MB each) per CTA of the per-MB ME kernel
+constexpr int kClusterWarps = 12;  // warps (one MB each) per CTA of the cluster schedule
 constexpr int kPairWarpsMax = 16;  // warps (MB rows) per CTA of the per-pair ME kernel
 
 // ME schedules: one warp per MB with tickets in wavefront order, or one CTA
 // per frame pair with one warp per MB row.
-enum Schedule { kSchedAuto = 0, kSchedMB = 1, kSchedPair = 2 };
+enum Schedule { kSchedAuto = 0, kSchedMB = 1, kSchedPair = 2, kSchedCluster = 3 };
 
 // Device status words (scratch).  `err` is sticky until read by
 // sme_synchronize; `abort` and `ticket` are reset by the classify kernel at
@@ -107,6 +108,11 @@ struct MeArgs {
     int fault_ticket;
     int speculate;
     long long timeout_ns;
+    // cluster schedule (one sequence per cluster)
+    const int* cl_items;      // [cluster][cl_cap] global MB ids, each CTA's list in wavefront order
+    const int* cl_count;      // [cluster] items per CTA
+    const int* cl_consumers;  // [total][4] consumer slot of each MB in the roles A, B, C, T (or -1)
+    int cl_cap;
 };
 
 struct CompArgs {
@@ -144,6 +150,12 @@ size_t me_pair_smem_bytes(int S, int nwarps, int mbw_max);
 // kernel: luma window, current block, packed-alpha reference strip (u32),
 // packed-alpha current BAB (u32).
 void pair_boxes(int S, unsigned (&box)[4][2]);
+// Cluster schedule: dynamic shared memory of one CTA of `warps` warps for
+// `cap` items per CTA; how many clusters of `cluster` such CTAs can be
+// resident at once (0: none).
+size_t me_cluster_smem_bytes(int S, int cap, int warps);
+int me_cluster_fits(int S, int cap, int cluster, int warps);
+cudaError_t launch_me_cluster(const Method& m, const MeArgs& a, int cluster, int warps, int helpers, cudaStream_t s);
 cudaError_t launch_compensate(const Geom& g, const Method& m, const CompArgs& a, cudaStream_t s);
 
 // cuTensorMapEncodeTiled of the installed driver (NULL if unavailable).

@@ -1038,16 +1038,255 @@ __device__ __forceinline__ P8 load8(const uint8_t* p)
 }
 
 // ====================================================== ME, per-MB warps ==
+// Where the candidate vectors of an MB come from and where its own vector
+// goes.  GlobalLinks: a ready word per MB in global memory, (epoch << 32) |
+// vector, polled by whichever warp of the grid holds a consumer.
+struct GlobalLinks {
+    unsigned long long* ready;
+    unsigned epoch;
+    int fault;  // an MB whose vector is never published (failure-detection tests)
+    __device__ __forceinline__ unsigned long long poll(int dep, int) const { return ld_ready(ready + dep); }
+    __device__ __forceinline__ bool arrived(unsigned long long w) const { return (unsigned)(w >> 32) == epoch; }
+    __device__ __forceinline__ void publish(int gid, int key, int lane) const
+    {
+        if (lane == 0 && gid != fault) st_ready(ready + gid, ((unsigned long long)epoch << 32) | (unsigned)key);
+    }
+    // A poll through L2 already takes long enough to leave the SM's issue
+    // slots to the other warps.
+    __device__ __forceinline__ void idle() const {}
+};
+
+// ClusterLinks: the CTAs of one thread-block cluster share a sequence, and
+// every MB's consumers -- the MBs that take it as A, B, C or T -- are known
+// in advance.  The producer stores (1 << 32) | vector straight into each
+// consumer's slot in the consumer CTA's shared memory (distributed shared
+// memory); a consumer polls its own slots.  slots: this CTA's slots, four per
+// item (roles A, B, C, T), zeroed at launch.
+struct ClusterLinks {
+    unsigned long long* slots;
+    int slot;   // the item's position in this CTA's list
+    int cons;   // lanes 0..3: the consumer slot in role `lane` (rank << 20 | slot * 4 + role), or -1
+    int fault;
+    __device__ __forceinline__ unsigned long long poll(int, int role) const
+    {
+        return *reinterpret_cast<volatile unsigned long long*>(slots + 4 * slot + role);
+    }
+    __device__ __forceinline__ bool arrived(unsigned long long w) const { return (w >> 32) != 0; }
+    __device__ __forceinline__ void publish(int gid, int key, int lane) const
+    {
+        if (lane >= 4 || gid == fault) return;
+        const int c = cons;
+        if (c < 0) return;
+        const uint32_t local = (uint32_t)__cvta_generic_to_shared(slots + (c & 0xFFFFF));
+        uint32_t remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(c >> 20));
+        asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(remote),
+                     "l"((1ull << 32) | (unsigned)key)
+                     : "memory");
+    }
+    __device__ __forceinline__ void idle() const {}
+};
+
+// One MB (global id gid of sequence sd) by one warp: Fig. 1 from the class
+// on, with the candidates of Fig. 3 taken from `L`.  Returns false when a
+// bounded wait gave up (the launch's error status is raised).
+template <class Links>
+__device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int gid, const SeqDesc* sd, uint8_t* win,
+                                          int* slog, const float* s_rcp, const Links& L, int lane, int pitch)
+{
+    const int h = m.h;
+    const int W = sd->W, H = sd->H, M = sd->M, MBW = sd->MBW, rd = sd->rd;
+    const int idx = gid - sd->gid_base;
+    const int k = idx / M, mb = idx - k * M;
+    const int u = mb % MBW, v = mb / MBW;
+    const int X0 = 16 * u, Y0 = 16 * v;
+    const int x0 = X0 + 8 * (lane & 1), y = Y0 + (lane >> 1);
+    const size_t FS = (size_t)W * H;
+    const uint8_t* ref = sd->luma + (size_t)k * FS;
+    const uint8_t* cur = sd->luma + (size_t)(k + rd) * FS;
+    const int cls = __ldg(sd->cls + (size_t)(k + rd) * M + mb);
+    const P8 c8 = load8(cur + (size_t)y * W + x0);
+
+    if (cls == SME_TRANSPARENT) {
+        L.publish(gid, 0, lane);
+        transparent_mb(sd, idx, k, ref, c8, lane, FS, W, y, x0);
+        return true;
+    }
+
+    // ---- work that does not depend on the neighbours: prefetch ----
+    int wx0, wy0;
+    stage_window(win, ref, W, H, m.S, X0, Y0, lane, wx0, wy0);
+    float ux[8], uy[8];
+    int nx = 0, ny = 0;
+    if (cls == SME_OPAQUE) mb_factors(cur, W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny);
+    const VRange V = valid_range(W, H, m, X0, Y0);
+
+    // ---- candidates A, B, C, T (Fig. 1, Fig. 3) + optional seed ----
+    // Lanes 0..3 poll the ready words of A, B, C, T.  While the warp
+    // waits, every candidate whose vector has arrived is costed at once,
+    // and the first pixel-recursive step is taken speculatively at the
+    // first costed position; the results are exactly those the search
+    // computes after the wait, so nothing changes but the latency.
+    int dep = -1;
+    if (lane == 0 && u > 0) dep = gid - 1;                       // A
+    if (lane == 1 && v > 0) dep = gid - MBW;                     // B
+    if (lane == 2 && v > 0 && u < MBW - 1) dep = gid - MBW + 1;  // C
+    if (lane == 3 && k > 0) dep = gid - M;                       // T
+    int key = 0;
+    if (lane == 3 && k == 0 && sd->temporal_in)
+        key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
+    if (lane == 4 && sd->seed) key = seed_key(sd, idx, h, V);
+    if (lane < 4) key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
+    const int nc = sd->seed ? 5 : 4;
+    bool res_l = dep < 0;
+    unsigned have = __ballot_sync(kFull, lane < nc && res_l) & ((1u << nc) - 1u);
+    const unsigned all = (1u << nc) - 1u;
+    unsigned costed = 0;
+    unsigned ccost[5] = {0u, 0u, 0u, 0u, 0u};
+    int ckey[5] = {0, 0, 0, 0, 0};
+    P8 cs8[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) cs8[c] = c8;
+    bool spec = false;
+    int spec_key = 0;
+    PrsStep sp;
+    const uint32_t* pcur = sd->packed + (size_t)(k + rd) * H * sd->Wp;
+    const uint32_t* pref = sd->packed + (size_t)k * H * sd->Wp;
+    const int lx = x0 - wx0, ly = y - wy0;
+    bool failed = false;
+    unsigned long long t_start = 0;
+    for (unsigned it = 0;; ++it) {
+        // The next poll is issued first, so its latency overlaps the
+        // costing below; its result is consumed at the end of the pass.
+        unsigned long long w = 0;
+        if (lane < 4 && !res_l) w = L.poll(dep, lane);
+        const unsigned fresh = (a.speculate || have == all) ? (have & ~costed) : 0u;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            if (fresh & (1u << c)) {
+                const int kc = __shfl_sync(kFull, key, c);
+                ckey[c] = kc;
+                // A position already costed is not evaluated again.
+                bool dup = false;
+#pragma unroll
+                for (int e = 0; e < 5; ++e)
+                    if (e != c && !dup && (costed & (1u << e)) && ckey[e] == kc) {
+                        ccost[c] = ccost[e];
+                        cs8[c] = cs8[e];
+                        dup = true;
+                    }
+                if (!dup) {
+                    if (cls == SME_BOUNDARY) {
+                        ccost[c] = shape_cost1(pcur, pref, sd->Wp, X0, Y0, kc, h, lane);
+                    } else {
+                        cs8[c] = ref8(win, pitch, lx, ly, mv_x(kc), mv_y(kc), h);
+                        ccost[c] = __reduce_add_sync(kFull, sad8(cs8[c], c8));
+                    }
+                }
+                costed |= 1u << c;
+            }
+        if (costed == all) break;
+        if (a.speculate && cls == SME_OPAQUE && costed && m.K > 0) {
+            // The first pixel-recursive step at the provisional winner
+            // (first strict minimum among the candidates costed so far).
+            int pb = -1;
+            unsigned pc = 0;
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                if ((costed & (1u << c)) && (pb < 0 || ccost[c] < pc)) {
+                    pb = c;
+                    pc = ccost[c];
+                }
+            int pk = ckey[0];
+            P8 r0 = cs8[0];
+#pragma unroll
+            for (int c = 1; c < 5; ++c)
+                if (c == pb) {
+                    pk = ckey[c];
+                    r0 = cs8[c];
+                }
+            if (!spec || pk != spec_key) {
+                sp = prs_eval(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, mv_x(pk), mv_y(pk), r0, pc);
+                spec_key = pk;
+                spec = true;
+            }
+        }
+        if (lane < 4 && !res_l && L.arrived(w)) {
+            const int kk = (int)(unsigned)w;
+            key = pack_mv(clampi(mv_x(kk), V.lox, V.hix), clampi(mv_y(kk), V.loy, V.hiy));
+            res_l = true;
+        }
+        const unsigned before = have;
+        have = __ballot_sync(kFull, lane < nc && res_l) & all;
+        if (have == before && !fresh) L.idle();  // nothing arrived, nothing to cost
+        if ((it & 15u) == 15u) {
+            // Bounded wait: the launch's abort word, a time limit, an iteration cap.
+            int give_up = 0;
+            if (lane == 0) {
+                const unsigned long long now = globaltimer();
+                if (t_start == 0) t_start = now;
+                give_up = ld_relaxed(&a.status->abort) || (long long)(now - t_start) > a.timeout_ns ||
+                          it > (1u << 24);
+            }
+            if (__shfl_sync(kFull, give_up, 0)) {
+                if (lane == 0 && !ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
+                failed = true;
+                break;
+            }
+        }
+    }
+    if (failed) return false;
+    int cand[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) cand[c] = __shfl_sync(kFull, key, c);
+    if (lane < nc) slog[lane] = key;
+
+    // First strict minimum in the order A, B, C, T (+ seed).
+    MbResult r;
+    int bi = 0;
+    unsigned bcost = ccost[0];
+#pragma unroll
+    for (int c = 1; c < 5; ++c)
+        if (c < nc && ccost[c] < bcost) {
+            bcost = ccost[c];
+            bi = c;
+        }
+    int nlog = nc;
+    if (cls == SME_OPAQUE) {
+        // Sec. 3.2 (the first step may be the speculative one, taken at
+        // the same position).
+        opaque_search(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, ccost, cs8, nc, bi, slog, nlog, lane,
+                      spec, spec_key, sp, r);
+    } else {
+        int bk = cand[0];
+#pragma unroll
+        for (int c = 1; c < 5; ++c)
+            if (c == bi) bk = cand[c];
+        r.dx = mv_x(bk);
+        r.dy = mv_y(bk);
+        r.cost = bcost;
+        r.iters = 0;
+        r.lastx = r.lasty = 0.0f;
+        r.r8 = ref8(win, pitch, lx, ly, r.dx, r.dy, h);  // prediction at the shape winner
+    }
+    r.nlog = nlog;
+
+    // ---- publish the vector first: it is on the dependency chain ----
+    L.publish(gid, pack_mv(r.dx, r.dy), lane);
+    if (lane == 0) sd->mv[idx] = sme_mv{(int16_t)r.dx, (int16_t)r.dy};
+    finish_mb(sd, idx, k, cls, r, c8, slog, lane, FS, W, y, x0);
+    return true;
+}
+
 __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const Method m = a.m;
-    const int h = m.h, pitch = win_pitch(m.S);
+    const int pitch = win_pitch(m.S);
     uint8_t* win = smem + (size_t)wid * warp_smem(m.S);
     int* slog = reinterpret_cast<int*>(win + win_bytes(m.S));
-    const unsigned epoch = ld_relaxed(&a.status->epoch);
-    const unsigned long long tag = (unsigned long long)epoch << 32;
+    const GlobalLinks L{a.ready, ld_relaxed(&a.status->epoch), a.fault_ticket};
     __shared__ float s_rcp[512];
     fill_rcp(s_rcp);
     __syncthreads();
@@ -1062,188 +1301,129 @@ __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
         if (t >= a.total) break;
         const int gid = __ldg(a.sched + t);
         const SeqDesc* sd = a.seqs + (a.sched_seq ? __ldg(a.sched_seq + t) : 0);
-        const int W = sd->W, H = sd->H, M = sd->M, MBW = sd->MBW, rd = sd->rd;
-        const int idx = gid - sd->gid_base;
-        const int k = idx / M, mb = idx - k * M;
-        const int u = mb % MBW, v = mb / MBW;
-        const int X0 = 16 * u, Y0 = 16 * v;
-        const int x0 = X0 + 8 * (lane & 1), y = Y0 + (lane >> 1);
-        const size_t FS = (size_t)W * H;
-        const uint8_t* ref = sd->luma + (size_t)k * FS;
-        const uint8_t* cur = sd->luma + (size_t)(k + rd) * FS;
-        const int cls = __ldg(sd->cls + (size_t)(k + rd) * M + mb);
-        const P8 c8 = load8(cur + (size_t)y * W + x0);
-
-        if (cls == SME_TRANSPARENT) {
-            if (lane == 0 && gid != a.fault_ticket) st_ready(a.ready + gid, tag);
-            transparent_mb(sd, idx, k, ref, c8, lane, FS, W, y, x0);
-            continue;
-        }
-
-        // ---- work that does not depend on the neighbours: prefetch ----
-        int wx0, wy0;
-        stage_window(win, ref, W, H, m.S, X0, Y0, lane, wx0, wy0);
-        float ux[8], uy[8];
-        int nx = 0, ny = 0;
-        if (cls == SME_OPAQUE) mb_factors(cur, W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny);
-        const VRange V = valid_range(W, H, m, X0, Y0);
-
-        // ---- candidates A, B, C, T (Fig. 1, Fig. 3) + optional seed ----
-        // Lanes 0..3 poll the ready words of A, B, C, T.  While the warp
-        // waits, every candidate whose vector has arrived is costed at once,
-        // and the first pixel-recursive step is taken speculatively at the
-        // first costed position; the results are exactly those the search
-        // computes after the wait, so nothing changes but the latency.
-        int dep = -1;
-        if (lane == 0 && u > 0) dep = gid - 1;                       // A
-        if (lane == 1 && v > 0) dep = gid - MBW;                     // B
-        if (lane == 2 && v > 0 && u < MBW - 1) dep = gid - MBW + 1;  // C
-        if (lane == 3 && k > 0) dep = gid - M;                       // T
-        int key = 0;
-        if (lane == 3 && k == 0 && sd->temporal_in)
-            key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
-        if (lane == 4 && sd->seed) key = seed_key(sd, idx, h, V);
-        if (lane < 4) key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
-        const int nc = sd->seed ? 5 : 4;
-        bool res_l = dep < 0;
-        unsigned have = __ballot_sync(kFull, lane < nc && res_l) & ((1u << nc) - 1u);
-        const unsigned all = (1u << nc) - 1u;
-        unsigned costed = 0;
-        unsigned ccost[5] = {0u, 0u, 0u, 0u, 0u};
-        int ckey[5] = {0, 0, 0, 0, 0};
-        P8 cs8[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) cs8[c] = c8;
-        bool spec = false;
-        int spec_key = 0;
-        PrsStep sp;
-        const uint32_t* pcur = sd->packed + (size_t)(k + rd) * H * sd->Wp;
-        const uint32_t* pref = sd->packed + (size_t)k * H * sd->Wp;
-        const int lx = x0 - wx0, ly = y - wy0;
-        bool failed = false;
-        unsigned long long t_start = 0;
-        for (unsigned it = 0;; ++it) {
-            // The next poll is issued first, so its latency overlaps the
-            // costing below; its result is consumed at the end of the pass.
-            unsigned long long w = 0;
-            if (lane < 4 && !res_l) w = ld_ready(a.ready + dep);
-            const unsigned fresh = (a.speculate || have == all) ? (have & ~costed) : 0u;
-#pragma unroll
-            for (int c = 0; c < 5; ++c)
-                if (fresh & (1u << c)) {
-                    const int kc = __shfl_sync(kFull, key, c);
-                    ckey[c] = kc;
-                    // A position already costed is not evaluated again.
-                    bool dup = false;
-#pragma unroll
-                    for (int e = 0; e < 5; ++e)
-                        if (e != c && !dup && (costed & (1u << e)) && ckey[e] == kc) {
-                            ccost[c] = ccost[e];
-                            cs8[c] = cs8[e];
-                            dup = true;
-                        }
-                    if (!dup) {
-                        if (cls == SME_BOUNDARY) {
-                            ccost[c] = shape_cost1(pcur, pref, sd->Wp, X0, Y0, kc, h, lane);
-                        } else {
-                            cs8[c] = ref8(win, pitch, lx, ly, mv_x(kc), mv_y(kc), h);
-                            ccost[c] = __reduce_add_sync(kFull, sad8(cs8[c], c8));
-                        }
-                    }
-                    costed |= 1u << c;
-                }
-            if (costed == all) break;
-            if (a.speculate && cls == SME_OPAQUE && costed && m.K > 0) {
-                // The first pixel-recursive step at the provisional winner
-                // (first strict minimum among the candidates costed so far).
-                int pb = -1;
-                unsigned pc = 0;
-#pragma unroll
-                for (int c = 0; c < 5; ++c)
-                    if ((costed & (1u << c)) && (pb < 0 || ccost[c] < pc)) {
-                        pb = c;
-                        pc = ccost[c];
-                    }
-                int pk = ckey[0];
-                P8 r0 = cs8[0];
-#pragma unroll
-                for (int c = 1; c < 5; ++c)
-                    if (c == pb) {
-                        pk = ckey[c];
-                        r0 = cs8[c];
-                    }
-                if (!spec || pk != spec_key) {
-                    sp = prs_eval(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, mv_x(pk), mv_y(pk), r0, pc);
-                    spec_key = pk;
-                    spec = true;
-                }
-            }
-            if (lane < 4 && !res_l && (unsigned)(w >> 32) == epoch) {
-                const int kk = (int)(unsigned)w;
-                key = pack_mv(clampi(mv_x(kk), V.lox, V.hix), clampi(mv_y(kk), V.loy, V.hiy));
-                res_l = true;
-            }
-            have = __ballot_sync(kFull, lane < nc && res_l) & all;
-            if ((it & 15u) == 15u) {
-                // Bounded wait: the launch's abort word, a time limit, an iteration cap.
-                int give_up = 0;
-                if (lane == 0) {
-                    const unsigned long long now = globaltimer();
-                    if (t_start == 0) t_start = now;
-                    give_up = ld_relaxed(&a.status->abort) || (long long)(now - t_start) > a.timeout_ns ||
-                              it > (1u << 24);
-                }
-                if (__shfl_sync(kFull, give_up, 0)) {
-                    if (lane == 0 && !ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
-                    failed = true;
-                    break;
-                }
-            }
-        }
-        if (failed) break;
-        int cand[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) cand[c] = __shfl_sync(kFull, key, c);
-        if (lane < nc) slog[lane] = key;
-
-        // First strict minimum in the order A, B, C, T (+ seed).
-        MbResult r;
-        int bi = 0;
-        unsigned bcost = ccost[0];
-#pragma unroll
-        for (int c = 1; c < 5; ++c)
-            if (c < nc && ccost[c] < bcost) {
-                bcost = ccost[c];
-                bi = c;
-            }
-        int nlog = nc;
-        if (cls == SME_OPAQUE) {
-            // Sec. 3.2 (the first step may be the speculative one, taken at
-            // the same position).
-            opaque_search(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, ccost, cs8, nc, bi, slog, nlog, lane,
-                          spec, spec_key, sp, r);
-        } else {
-            int bk = cand[0];
-#pragma unroll
-            for (int c = 1; c < 5; ++c)
-                if (c == bi) bk = cand[c];
-            r.dx = mv_x(bk);
-            r.dy = mv_y(bk);
-            r.cost = bcost;
-            r.iters = 0;
-            r.lastx = r.lasty = 0.0f;
-            r.r8 = ref8(win, pitch, lx, ly, r.dx, r.dy, h);  // prediction at the shape winner
-        }
-        r.nlog = nlog;
-
-        // ---- publish the vector first: it is on the dependency chain ----
-        if (lane == 0) {
-            const int key_out = pack_mv(r.dx, r.dy);
-            if (gid != a.fault_ticket) st_ready(a.ready + gid, tag | (unsigned)key_out);
-            sd->mv[idx] = sme_mv{(int16_t)r.dx, (int16_t)r.dy};
-        }
-        finish_mb(sd, idx, k, cls, r, c8, slog, lane, FS, W, y, x0);
+        if (!me_one_mb(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) break;
     }
+}
+
+// ============================================ ME, one cluster per sequence ==
+// The first cluster of the launch (the chain cluster) estimates every
+// non-transparent MB of one sequence; the other clusters (helpers) finish the
+// transparent MBs, whose vector (0,0) is known from the classes alone.  The
+// host deals all MBs, in wavefront order, round robin to the chain cluster's
+// CTAs (a.cl_items: CTA r's list, a.cl_cap entries apart; a.cl_count[r]
+// items).  Each CTA keeps the non-transparent items of its list (order kept),
+// fills the slots whose producer is transparent with (0,0) itself, and its
+// warps take the kept items in order; every other dependency travels through
+// ClusterLinks, so no link is polled through L2.  Deadlock-free for the same
+// reason as the per-MB schedule: an item waits only on items of smaller
+// wavefront step, which every CTA takes first.  Dynamic shared memory: the
+// warps' windows, the item slots, the kept-item list.
+__device__ __forceinline__ int item_class(const SeqDesc* sd, int gid)
+{
+    const int k = gid / sd->M, mb = gid - k * sd->M;
+    return __ldg(sd->cls + (size_t)(k + sd->rd) * sd->M + mb);
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(32 * kClusterWarps, 1) me_cluster_kernel(const MeArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, tid = threadIdx.x, nw = blockDim.x >> 5;
+    const Method m = a.m;
+    const SeqDesc* sd = a.seqs;
+    unsigned rank, cid, csize;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
+
+    if (cid > 0) {
+        // ---- helpers: outputs and prediction error of every transparent MB
+        const int nhw = ((int)gridDim.x - (int)csize) * nw;
+        const int W = sd->W, M = sd->M, MBW = sd->MBW, rd = sd->rd;
+        const size_t FS = (size_t)W * sd->H;
+        for (int gid = ((int)blockIdx.x - (int)csize) * nw + wid; gid < a.total; gid += nhw) {
+            if (item_class(sd, gid) != SME_TRANSPARENT) continue;
+            const int k = gid / M, mb = gid - k * M, u = mb % MBW, v = mb / MBW;
+            const int x0 = 16 * u + 8 * (lane & 1), y = 16 * v + (lane >> 1);
+            const uint8_t* ref = sd->luma + (size_t)k * FS;
+            const P8 c8 = load8(sd->luma + (size_t)(k + rd) * FS + (size_t)y * W + x0);
+            transparent_mb(sd, gid, k, ref, c8, lane, FS, W, y, x0);
+        }
+        return;
+    }
+
+    // ---- the chain cluster
+    const int pitch = win_pitch(m.S);
+    uint8_t* win = smem + (size_t)wid * warp_smem(m.S);
+    int* slog = reinterpret_cast<int*>(win + win_bytes(m.S));
+    unsigned long long* slots =
+        reinterpret_cast<unsigned long long*>(smem + (size_t)nw * warp_smem(m.S));
+    int* work = reinterpret_cast<int*>(slots + 4 * (size_t)a.cl_cap);  // kept positions, then their MB ids
+    __shared__ float s_rcp[512];
+    __shared__ int s_ticket, s_nwork, s_warp[kClusterWarps];
+    const int n_items = __ldg(a.cl_count + rank);
+    const int* items = a.cl_items + (size_t)rank * a.cl_cap;
+    for (int i = tid; i < 4 * n_items; i += blockDim.x) slots[i] = 0ull;
+    if (tid == 0) s_ticket = 0;
+    fill_rcp(s_rcp);
+    // Keep the non-transparent items, in order: each thread counts a
+    // contiguous chunk, a block scan gives its offset, then it writes them.
+    const int per = (n_items + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int i0 = min(n_items, tid * per), i1 = min(n_items, i0 + per);
+    int cnt = 0;
+    for (int i = i0; i < i1; ++i) cnt += item_class(sd, __ldg(items + i)) != SME_TRANSPARENT;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < wid; ++w) base += s_warp[w];
+    if (tid == blockDim.x - 1) s_nwork = base + incl;
+    int o = base + incl - cnt;
+    for (int i = i0; i < i1; ++i)
+        if (item_class(sd, __ldg(items + i)) != SME_TRANSPARENT) work[o++] = i;
+    __syncthreads();
+    int* work_gid = work + s_nwork;
+    for (int j = tid; j < s_nwork; j += blockDim.x) work_gid[j] = __ldg(items + work[j]);
+    // A transparent producer's vector is (0,0): its consumers' slots here are
+    // filled now rather than by the producer.
+    const int n_work = s_nwork, M = sd->M, MBW = sd->MBW;
+    for (int j = tid; j < n_work; j += blockDim.x) {
+        const int i = work[j], gid = work_gid[j];
+        const int k = gid / M, mb = gid - k * M, u = mb % MBW, v = mb / MBW;
+        const int prod[4] = {u > 0 ? gid - 1 : -1, v > 0 ? gid - MBW : -1,
+                             (v > 0 && u < MBW - 1) ? gid - MBW + 1 : -1, k > 0 ? gid - M : -1};
+#pragma unroll
+        for (int role = 0; role < 4; ++role)
+            if (prod[role] >= 0 && item_class(sd, prod[role]) == SME_TRANSPARENT) slots[4 * i + role] = 1ull << 32;
+    }
+    // every slot of the cluster is settled before any producer stores into it
+    cluster_sync_all();
+
+    for (;;) {
+        int t = 0;
+        if (lane == 0) {
+            t = atomicAdd(&s_ticket, 1);
+            if (ld_relaxed(&a.status->abort)) t = n_work;
+        }
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= n_work) break;
+        const int i = work[t], gid = work_gid[t];
+        // the consumer slots are fetched now; they are needed only at the end
+        const int cons = lane < 4 ? __ldg(a.cl_consumers + 4 * (size_t)gid + lane) : -1;
+        const ClusterLinks L{slots, i, cons, a.fault_ticket};
+        if (!me_one_mb(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) break;
+    }
+    // no CTA leaves while a peer may still store into its slots
+    cluster_sync_all();
 }
 
 // ================================================ ME, per-pair CTAs ==
@@ -1810,6 +1990,58 @@ cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, me_kernel, a);
+}
+
+size_t me_cluster_smem_bytes(int S, int cap, int warps)
+{
+    return (size_t)warps * warp_smem(S) + (size_t)cap * (4 * sizeof(unsigned long long) + 2 * sizeof(int));
+}
+
+int me_cluster_fits(int S, int cap, int cluster, int warps)
+{
+    const size_t smem = me_cluster_smem_bytes(S, cap, warps);
+    if (smem > 227 * 1024 ||
+        cudaFuncSetAttribute(me_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(me_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster);
+    cfg.blockDim = dim3(32 * warps);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, me_cluster_kernel, &cfg) == cudaSuccess && n >= 1) return n;
+    cudaGetLastError();
+    return 0;
+}
+
+cudaError_t launch_me_cluster(const Method& m, const MeArgs& a, int cluster, int warps, int helpers, cudaStream_t s)
+{
+    // The chain cluster's CTAs wait on one another only through distributed
+    // shared memory, and a cluster is always resident as a whole; the helper
+    // clusters wait on nothing.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster * (1 + helpers));
+    cfg.blockDim = dim3(32 * warps);
+    cfg.dynamicSmemBytes = me_cluster_smem_bytes(m.S, a.cl_cap, warps);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, me_cluster_kernel, a);
 }
 
 void pair_boxes(int S, unsigned (&box)[4][2])

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsme.so")
 
 SME_TRANSPARENT, SME_OPAQUE, SME_BOUNDARY = 0, 1, 2
 SME_OPT_SCHEDULE, SME_OPT_PAIR_WARPS, SME_OPT_MB_CTAS_PER_SM, SME_OPT_SPECULATE = 1, 2, 3, 4
-SCHEDULES = {"auto": 0, "mb": 1, "pair": 2}
+SME_OPT_CLUSTER_SIZE = 5
+SCHEDULES = {"auto": 0, "mb": 1, "pair": 2, "cluster": 3}
 STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4: "SME_ERR_TIMEOUT",
           5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE", 8: "SME_ERR_SCRATCH"}
 
@@ -28,7 +29,7 @@ EXPORTS = [
     "sme_estimate_sequence_host", "sme_set_reference", "sme_set_current", "sme_estimate",
     "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field",
     "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
-    "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_autotune",
+    "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_get_option", "sme_autotune",
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_forward",
@@ -102,6 +103,7 @@ def _lib():
             "sme_profile_end": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "sme_estimate_sequence_noalloc": (i, [C.POINTER(Params), vp, vp, i, vp, vp, C.POINTER(Outputs), vp]),
             "sme_set_option": (i, [vp, i, i]),
+            "sme_get_option": (i, [vp, i, C.POINTER(C.c_int)]),
             "sme_autotune": (i, [vp, vp, vp, i, C.POINTER(Outputs), i]),
             "sme_batch_create": (i, [ip, C.POINTER(Params), C.POINTER(Sequence), i, vp]),
             "sme_batch_tune": (i, [vp, i]),
@@ -314,10 +316,24 @@ class Estimator:
     def set_option(self, option, value):
         _check(_lib().sme_set_option(self._h, int(option), int(value)), "sme_set_option")
 
-    def set_schedule(self, name, pair_warps=0):
-        """'auto', 'mb' (one warp per MB) or 'pair' (one CTA per frame pair)."""
+    def set_schedule(self, name, pair_warps=0, cluster=0):
+        """'auto', 'mb' (one warp per MB), 'pair' (one CTA per frame pair) or
+        'cluster' (one thread-block cluster per sequence)."""
         self.set_option(SME_OPT_SCHEDULE, SCHEDULES[name])
         self.set_option(SME_OPT_PAIR_WARPS, pair_warps)
+        self.set_option(SME_OPT_CLUSTER_SIZE, cluster)
+
+    def get_option(self, option):
+        v = C.c_int()
+        _check(_lib().sme_get_option(self._h, int(option), C.byref(v)), "sme_get_option")
+        return v.value
+
+    def config(self):
+        """The execution configuration in use (after autotune: the chosen one)."""
+        names = {v: k for k, v in SCHEDULES.items()}
+        return {"schedule": names[self.get_option(SME_OPT_SCHEDULE)], "pair_warps": self.get_option(SME_OPT_PAIR_WARPS),
+                "mb_ctas_per_sm": self.get_option(SME_OPT_MB_CTAS_PER_SM),
+                "speculate": self.get_option(SME_OPT_SPECULATE), "cluster": self.get_option(SME_OPT_CLUSTER_SIZE)}
 
     def autotune(self, luma, alpha, out=None, trials=3, want=("cost", "disp", "iters", "npos", "mb_class", "sse")):
         """Pick the fastest execution configuration for this sequence shape."""

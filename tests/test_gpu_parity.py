@@ -30,7 +30,7 @@ def cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-SCHEDULES = ["pair", "mb"]
+SCHEDULES = ["pair", "mb", "cluster"]
 
 
 def run_both(sme, luma, alpha, S=16, h=1, K=8, theta=2.0, eps=1.0, rd=1, temporal=None, seed=None,

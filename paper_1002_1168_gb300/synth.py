@@ -166,10 +166,10 @@ def _bounce_path(rng, start, F, vmax, half_extent, W, H, change_every, integer=F
     return path
 
 
-def make_sequence(W, H, F, seed, n_objects=1, vmax=8.0, bg_step=(1.0, 0.5), noise_sigma=3.0,
-                  blobby=True, change_every=10, max_rot_deg=0.0, scale_range=(1.0, 1.0),
-                  obj_frac=0.30, integer_motion=False):
-    """Generic sequence: n_objects moving objects over a translating background."""
+def draw_scene(W, H, F, seed, n_objects=1, vmax=8.0, bg_step=(1.0, 0.5), blobby=True, change_every=10,
+               max_rot_deg=0.0, scale_range=(1.0, 1.0), obj_frac=0.30, integer_motion=False):
+    """Scene parameters of make_sequence (background texture and offsets, the
+    objects with their paths) and the generator, positioned for the noise."""
     rng = np.random.default_rng(seed)
     background = Texture.random(rng)
     bstep = np.array(bg_step, np.float64)
@@ -191,6 +191,16 @@ def make_sequence(W, H, F, seed, n_objects=1, vmax=8.0, bg_step=(1.0, 0.5), nois
         else:
             hc, hp = np.zeros(0), np.zeros(0)
         objects.append(MovingObject(a, b, Texture.random(rng), centers, angles, scales, hc, hp))
+    return background, bg_offsets, objects, rng
+
+
+def make_sequence(W, H, F, seed, n_objects=1, vmax=8.0, bg_step=(1.0, 0.5), noise_sigma=3.0,
+                  blobby=True, change_every=10, max_rot_deg=0.0, scale_range=(1.0, 1.0),
+                  obj_frac=0.30, integer_motion=False):
+    """Generic sequence: n_objects moving objects over a translating background."""
+    background, bg_offsets, objects, rng = draw_scene(W, H, F, seed, n_objects, vmax, bg_step, blobby, change_every,
+                                                      max_rot_deg, scale_range, obj_frac, integer_motion)
+    bstep = np.array(bg_step, np.float64)
     luma, alpha = render(W, H, F, background, bg_offsets, objects, noise_sigma, rng)
     meta = dict(width=W, height=H, frames=F, n_objects=n_objects, vmax=vmax, noise_sigma=noise_sigma,
                 bg_step=list(bstep), seed=seed, generator="numpy PCG64")

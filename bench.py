@@ -435,6 +435,108 @@ def measure_batch(sme, torch, args, rank, dist, net=None):
                                        f"{cpu_mbs} MBs, {cpu_s:.1f} s, single-threaded C"}}
 
 
+def _device_quality(outputs, W, H):
+    """iters/opaque MB, positions/non-transparent MB, mean PSNR over every pair
+    of every VOP, reduced on the device (the fields are too large to copy)."""
+    import torch
+
+    from paper_1002_1168_gb300 import sme
+
+    it = itn = pos = posn = 0
+    ps = []
+    for o in outputs:
+        op, nt = o["mb_class"] == 1, o["mb_class"] > 0
+        it += int(o["iters"][op].sum(dtype=torch.int64))
+        itn += int(op.sum())
+        pos += int(o["npos"][nt].sum(dtype=torch.int64))
+        posn += int(nt.sum())
+        ps += [sme.psnr(int(x), W, H) for x in o["sse"].cpu().numpy().view(np.uint64)]
+    return {"iters_per_opaque_mb": it / max(itn, 1), "positions_per_mb": pos / max(posn, 1),
+            "psnr_db_mean": float(np.mean(ps)), "non_transparent_frac": posn / sum(o["mb_class"].numel() for o in outputs)}
+
+
+def measure_at_scale(sme, torch, args, params, dist):
+    """Learned proposal + batching at scale: 16 sequences of 3840x2160, 60
+    frames, 8 objects (8 VOPs) each, |v| <= 32, rotation <= 3 deg, S = 32,
+    half-pel, rendered on the device; the plain batch and the learned batch
+    (seed network with the trained weights), both autotuned and replayed
+    from CUDA graphs; the oracle on one sampled pair of each (given the GPU's
+    previous field and the seeds)."""
+    import gc
+
+    import oracle as O
+    from paper_1002_1168_gb300 import seedtrain, synth_gpu
+
+    W4, H4, S4 = 3840, 2160, 32
+    t0 = time.perf_counter()
+    seqs = synth_gpu.uhd_batch(seed=1005)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    F = seqs[0][0].shape[0]
+    groups = [(l, [a[j] for j in range(a.shape[0])]) for l, a, _ in seqs]
+    lumas = [l for l, vops in groups for _ in vops]
+    alphas = [a for _, vops in groups for a in vops]
+    total = len(alphas) * (F - 1) * (W4 // 16) * (H4 // 16)
+    want = ("cost", "disp", "iters", "npos", "mb_class", "sse")
+    steps = max(3, args.steps // 10)
+
+    def timed(run, stream=None):
+        for _ in range(2):
+            run()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            run()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps, dist)
+
+    def oracle_sample(out, s, j, k, seeds=None):
+        luma, alpha, _ = seqs[s]
+        tmp = None if k == 0 else out["mv"][k - 1].cpu().numpy()
+        sd = None if seeds is None else seeds[k:k + 1].cpu().numpy()
+        o = O.estimate_sequence(O.OracleParams(W4, H4, S4, 2), luma[k:k + 2].cpu().numpy(),
+                                alpha[j, k:k + 2].cpu().numpy(), temporal_in=tmp, seed=sd)
+        return bool(np.array_equal(out["mv"][k].cpu().numpy(), o["mv"][0]) and
+                    np.array_equal(out["cost"][k].cpu().numpy().view(np.uint32), o["cost"][0]) and
+                    int(out["sse"][k].item()) == int(o["sse"][0]))
+
+    b = sme.Batch(lumas, alphas, search_range=S4, subpel=2, want=want)
+    b.tune(trials=2)
+    ms = timed(lambda: b.run(sync=False))
+    b.synchronize()
+    plain = {"value": job_rate(total, dist.get_world_size() if dist else 1, ms / 1e3), "unit": UNIT, "ms_per_run": ms,
+             "config": b.config(), **_device_quality(b.outputs, W4, H4),
+             "bit_exact_vs_oracle_sample": oracle_sample(b.outputs[8 * 7 + 3], 7, 3, 30)}
+    b.close()
+    del b
+    gc.collect()
+    learned = None
+    if params is not None:
+        net = sme.SeedNet(max_cells=(F - 1) * (H4 // 4) * (W4 // 4))
+        net.set_params(params)
+        lb = seedtrain.LearnedBatch(net, groups, search_range=S4, subpel=2, want=want)
+        lb.tune(trials=2)
+        lms = timed(lambda: lb.run(sync=False), lb.stream)
+        lb.synchronize()
+        lq = _device_quality(lb.outputs, W4, H4)
+        learned = {"value": job_rate(total, dist.get_world_size() if dist else 1, lms / 1e3), "unit": UNIT,
+                   "ms_per_run": lms, "config": lb.config(), **lq, "vs_plain_at_scale": ms / lms,
+                   "psnr_delta_db": lq["psnr_db_mean"] - plain["psnr_db_mean"],
+                   "bit_exact_vs_oracle_sample": oracle_sample(lb.outputs[8 * 7 + 3], 7, 3, 30,
+                                                               lb.seeds[8 * 7 + 3])}
+        lb.close()
+        net.close()
+        del lb
+    del seqs, groups, lumas, alphas
+    gc.collect()
+    torch.cuda.empty_cache()
+    return {"workload": "16 sequences of 3840x2160, 60 frames, 8 VOPs each (128 VOPs), |v| <= 32, rotation <= 3 deg, "
+                        "S=32, half-pel, rendered on the device",
+            "mb_per_run": total, "generation_s": gen_s, "runs": steps, "plain": plain, "learned_seeded": learned}
+
+
 def run_ours(args):
     import torch
 
@@ -518,6 +620,9 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = measure_batch(sme, torch, args, rank, dist, net)
+    at_scale = None
+    if not args.no_scale:
+        at_scale = measure_at_scale(sme, torch, args, net.get_params() if net is not None else None, dist)
     if net is not None:
         net.close()
 
@@ -576,6 +681,7 @@ def run_ours(args):
                     "psnr_db_mean": float(np.mean(psnr)), "learned_seeded": learned},
         "wall_s_timed": wall,
         "batched": batched,
+        "at_scale": at_scale,
     }
     print(json.dumps(line))
     est.close()
@@ -622,6 +728,7 @@ def main():
     ap.add_argument("--schedule", default="auto", choices=["auto", "pair", "mb", "cluster"])
     ap.add_argument("--no-batch", action="store_true", help="skip the secondary batched measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip training and the learned-seeded measurements")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 16 x 3840x2160 measurement")
     ap.add_argument("--learn-pairs", type=int, default=2000, help="CIF VOP pairs the seed network is trained on")
     ap.add_argument("--learn-steps", type=int, default=800, help="Adam steps (32 pairs each)")
     ap.add_argument("--batch-only", action="store_true", help="only the batched measurement (profiling)")

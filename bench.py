@@ -140,7 +140,7 @@ def peaks():
 # DRAM bytes (read + write) of one me_kernel launch on this workload, from the
 # ncu capture summarised in profiles/me_kernel_cif30_halfpel.md (set to None
 # whenever the kernel changes until it is captured again).
-ME_KERNEL_TRAFFIC_BYTES = 3502592 + 15872
+ME_KERNEL_TRAFFIC_BYTES = 3510784 + 11776
 
 
 def algorithmic_bytes(P, M, F):
@@ -151,6 +151,23 @@ def algorithmic_bytes(P, M, F):
     bytes) and 8 bytes of SSE per pair."""
     wp = (W + 31) // 32 + 1
     return F * W * H + F * H * wp * 4 + P * M + P * M * 19 + P * 8
+
+
+# Integer pipe of a GB300: 152 SMs x 128 32-bit integer lanes x 2.07 GHz
+# (maximum SM clock), counting a packed 4-byte SIMD operation as one op.
+ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+
+
+def algorithmic_int_ops(res):
+    """Integer (and gradient FP32) operations the method needs for one pass,
+    from its own counters: per evaluated texture position 64 packed words x 3
+    ops (interpolate, absolute difference, accumulate); per pixel-recursive
+    iteration 256 pixels x 5 ops (Eqs. 3-5); per evaluated shape position 16
+    rows x 4 ops (XOR, popcount, shift, add); per MB the compensation and SSE,
+    64 words x 3 ops."""
+    cls, npos, iters = res["mb_class"], res["npos"].astype(np.int64), res["iters"].astype(np.int64)
+    op, bd = cls == 1, cls == 2
+    return int(192 * npos[op].sum() + 1280 * iters[op].sum() + 64 * npos[bd].sum() + 192 * cls.size)
 
 
 def run_reference(args):
@@ -455,6 +472,104 @@ def _device_quality(outputs, W, H):
             "psnr_db_mean": float(np.mean(ps)), "non_transparent_frac": posn / sum(o["mb_class"].numel() for o in outputs)}
 
 
+def es_psnr_like_method(sme, est, luma, mv_es, cls, rd, W_, H_):
+    """Mean PSNR of the exhaustive-search field with the transparent MBs at
+    (0,0), as Fig. 1 leaves them: the comparison with the method on the same
+    MBs (the method does not estimate the background outside its VOP)."""
+    import torch
+
+    mv = mv_es.clone()
+    mv[torch.from_numpy(cls == 0).to(mv.device)] = 0
+    return float(np.mean([sme.psnr(est.compensate(luma[k], luma[k + rd], mv[k].contiguous(), want_pred=False)[0],
+                                   W_, H_) for k in range(mv.shape[0])]))
+
+
+def measure_es(sme, torch, est, luma, flush, steps):
+    """The exhaustive search on the headline workload (the ES of Table 1,
+    the comparison method of Table 2): its time, positions per MB, the PSNR
+    of its field and the integer-pipe roofline of its kernel.  Returns the
+    record and the fields (for the oracle leg)."""
+    P = FRAMES - 1
+    for _ in range(3):
+        est.full_search(luma, sync=False)
+    est.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i, (e0, e1) in enumerate(ev):
+        flush.fill_(i & 0xff)
+        e0.record()
+        est.full_search(luma, sync=False)
+        e1.record()
+    torch.cuda.synchronize()
+    est.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+    mv, sad = est.full_search(luma)
+    psnr = []
+    for k in range(P):
+        sse, _ = est.compensate(luma[k], luma[k + 1], mv[k].contiguous(), want_pred=False)
+        psnr.append(sme.psnr(sse, W, H))
+    # |V| per MB (Table 1's ES count at 16 x 16, half-pel)
+    npos = 0
+    for v in range(H // 16):
+        for u in range(W // 16):
+            lox, hix = max(-S * SUBPEL, -16 * u * SUBPEL), min(S * SUBPEL, (W - 16 - 16 * u) * SUBPEL)
+            loy, hiy = max(-S * SUBPEL, -16 * v * SUBPEL), min(S * SUBPEL, (H - 16 - 16 * v) * SUBPEL)
+            npos += (hix - lox + 1) * (hiy - loy + 1)
+    M = (W // 16) * (H // 16)
+    ops = P * npos * 16 * 4 * 3  # per position and row: 4 words x (align, absolute difference, add)
+    rec = {"mb_per_s": P * M / (ms / 1e3), "ms_per_step": ms, "positions_per_mb": npos / M,
+           "psnr_db_mean": float(np.mean(psnr)),
+           "roofline": {"bound": "alu", "kernel": "es_kernel", "achieved_tops": ops / (ms / 1e3) / 1e12,
+                        "peak_tops": ALU_PEAK_TOPS, "frac": ops / (ms / 1e3) / 1e12 / ALU_PEAK_TOPS,
+                        "ops_per_launch": ops}}
+    return rec, mv, sad.cpu().numpy().view(np.uint32)
+
+
+def measure_paper_setup(sme, torch):
+    """The paper's own experimental setting, on a synthetic stand-in (the
+    QCIF test sequences of Sec. 4 are not available): QCIF 176x144, 30
+    frames, reference two frames back (ref_distance 2), 16x16 MBs, half-pel,
+    search range 7 (the window of Table 1's exhaustive-search count).  Reports
+    the method's distinct search points per block against the exhaustive
+    search's (Table 1) and both PSNRs (Table 2), with the whole field checked
+    against the oracle and the ES field against the oracle's ES."""
+    import oracle as O
+    from paper_1002_1168_gb300 import synth
+
+    Wq, Hq, Sq, rd, Fq = 176, 144, 7, 2, 30
+    seq = synth.make_sequence(Wq, Hq, Fq, seed=1006, n_objects=1, vmax=3.0, bg_step=(0.75, -0.25), noise_sigma=2.0,
+                              obj_frac=0.45)
+    est = sme.Estimator(Wq, Hq, search_range=Sq, subpel=2, ref_distance=rd)
+    luma = torch.from_numpy(seq.luma).cuda()
+    g = est.estimate_sequence(luma, torch.from_numpy(seq.alpha[0]).cuda())
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    mv_es, sad_es = est.full_search(luma)
+    P = Fq - rd
+    psnr_es = [sme.psnr(est.compensate(luma[k], luma[k + rd], mv_es[k].contiguous(), want_pred=False)[0], Wq, Hq)
+               for k in range(P)]
+    o = O.estimate_sequence(O.OracleParams(Wq, Hq, Sq, 2), seq.luma, seq.alpha[0], ref_distance=rd)
+    exact = all(np.array_equal(g[a_].view(np.uint8), o[b_].view(np.uint8)) for a_, b_ in
+                [("mv", "mv"), ("cost", "cost"), ("iters", "iters"), ("npos", "npos"), ("mb_class", "mbclass"),
+                 ("sse", "sse")])
+    es_ok = True
+    for k in (0, P - 1):
+        bm, bs, _ = O.full_search(seq.luma[k], seq.luma[k + rd], Wq, Hq, 2, Sq)
+        es_ok &= bool(np.array_equal(mv_es[k].cpu().numpy(), bm) and
+                      np.array_equal(sad_es[k].cpu().numpy().view(np.uint32), bs))
+    _, _, es_total = O.full_search(None, None, Wq, Hq, 2, Sq)
+    cls = g["mb_class"]
+    psnr_es_vop = es_psnr_like_method(sme, est, luma, mv_es, cls, rd, Wq, Hq)
+    est.close()
+    psnr_pa = [sme.psnr(int(x), Wq, Hq) for x in g["sse"].view(np.uint64)]
+    return {"workload": "QCIF 176x144, 30 frames, ref_distance 2, 16x16, half-pel, S=7, 1 VOP",
+            "search_points_per_mb": {"method": float(g["npos"][cls > 0].mean()), "es": es_total / 99,
+                                     "paper_table1_pa_qcif_8x8": "6.43-6.51", "paper_table1_es_8x8_fullpel": 204.2828},
+            "psnr_db": {"method": float(np.mean(psnr_pa)), "es": float(np.mean(psnr_es)),
+                        "es_transparent_at_zero": psnr_es_vop,
+                        "paper_table2_pa_minus_es": "-0.03 to -0.88 (real QCIF sequences, 8x8)"},
+            "iters_per_opaque_mb": float(g["iters"][cls == 1].mean()),
+            "bit_exact_vs_oracle": bool(exact), "es_bit_exact_vs_oracle_sample": es_ok}
+
+
 def measure_at_scale(sme, torch, args, params, dist):
     """Learned proposal + batching at scale: 16 sequences of 3840x2160, 60
     frames, 8 objects (8 VOPs) each, |v| <= 32, rotation <= 3 deg, S = 32,
@@ -612,6 +727,7 @@ def run_ours(args):
     h2d = int(hl.numel() + ha.numel())
     d2h = int(sum(v.numel() * v.element_size() for v in hout.values()))
 
+    es_rec, es_mv, es_sad = measure_es(sme, torch, est, luma, flush, max(args.steps // 4, 3))
     net, learned, train_info = None, None, None
     if not args.no_learned:
         net, train_info = train_seednet(sme, torch, args)
@@ -620,6 +736,7 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = measure_batch(sme, torch, args, rank, dist, net)
+    paper_setup = measure_paper_setup(sme, torch) if rank == 0 else None
     at_scale = None
     if not args.no_scale:
         at_scale = measure_at_scale(sme, torch, args, net.get_params() if net is not None else None, dist)
@@ -648,6 +765,17 @@ def run_ours(args):
 
     psnr = [O.psnr(int(s), W, H) for s in res["sse"].view(np.uint64)]
     op = cls == 1
+    # exhaustive search: the oracle's on two pairs, and the Table 1 / Table 2 comparison
+    es_exact = True
+    es_mv_np = es_mv.cpu().numpy()
+    for k in (0, P // 2):
+        bm, bs, _ = O.full_search(seq.luma[k], seq.luma[k + 1], W, H, SUBPEL, S)
+        es_exact &= bool(np.array_equal(es_mv_np[k], bm) and np.array_equal(es_sad[k], bs))
+    es_vop = es_psnr_like_method(sme, est, luma, es_mv, cls, 1, W, H)
+    es_rec.update({"bit_exact_vs_oracle_sample": es_exact, "pairs_checked": [0, P // 2],
+                   "search_points_ratio_method_vs_es": float(res["npos"][cls > 0].mean()) / es_rec["positions_per_mb"],
+                   "psnr_db_mean_transparent_at_zero": es_vop,
+                   "psnr_method_minus_es_db": float(np.mean(psnr)) - es_vop})
     if learned is not None:
         lexact, judge = learned_oracle_leg(seq, res, lres, lseeds)
         lq = stats(lres, W, H)
@@ -672,16 +800,22 @@ def run_ours(args):
                      "frac": achieved / hbm, "traffic": ME_KERNEL_TRAFFIC_BYTES, "kernel": "me_kernel",
                      "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg,
                      "avg_launch_ms": me_avg_s * 1e3, "classify_avg_ms": cls_ms / max(calls, 1),
-                     "critical_path_steps": (W // 16 - 1) + 2 * (H // 16 - 1) + P},
+                     "critical_path_steps": (W // 16 - 1) + 2 * (H // 16 - 1) + P,
+                     "alu": {"achieved_tops": algorithmic_int_ops(res) / me_avg_s / 1e12, "peak_tops": ALU_PEAK_TOPS,
+                             "frac": algorithmic_int_ops(res) / me_avg_s / 1e12 / ALU_PEAK_TOPS,
+                             "ops_per_launch": algorithmic_int_ops(res),
+                             "peak_kind": "derived: 152 SMs x 128 int32 lanes x 2.07 GHz"}},
         "cpu_baseline": cb,
         "quality": {"mv_match_oracle": match, "bit_exact_vs_oracle": exact,
                     "mb_per_s_non_transparent": value * float((cls > 0).mean()),
                     "iters_per_opaque_mb": float(res["iters"][op].mean()),
                     "positions_per_mb": float(res["npos"][cls > 0].mean()),
-                    "psnr_db_mean": float(np.mean(psnr)), "learned_seeded": learned},
+                    "psnr_db_mean": float(np.mean(psnr)), "learned_seeded": learned,
+                    "exhaustive_search": es_rec},
         "wall_s_timed": wall,
         "batched": batched,
         "at_scale": at_scale,
+        "paper_setup": paper_setup,
     }
     print(json.dumps(line))
     est.close()

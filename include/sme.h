@@ -221,6 +221,17 @@ enum {
 };
 enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2, SME_SCHED_CLUSTER = 3 };
 int sme_set_option(sme_ctx* ctx, int option, int value);
+/* Exhaustive search (the ES of Sec. 1 / Table 1 / Table 2, the comparison
+ * method of the paper's experiments; not part of the method): for every MB
+ * of every pair (frame k, frame k + ref_distance) of a [n_frames][H][W] luma
+ * sequence (device, 16-byte aligned), the texture SAD at every vector of the
+ * valid set V of the context's parameters (search range, subpel) and the
+ * first minimum in raster order (dy outer, dx inner).  Every MB of the frame
+ * grid, whatever its class.  mv [P][M] (device out), sad [P][M] (device out,
+ * optional).  Asynchronous on the context's stream; SME_ERR_SIZE if the
+ * search window does not fit in shared memory. */
+int sme_full_search(sme_ctx* ctx, const uint8_t* luma, int n_frames, sme_mv* mv, uint32_t* sad);
+
 /* The current value of an option (e.g. what sme_autotune chose). */
 int sme_get_option(sme_ctx* ctx, int option, int* value);
 

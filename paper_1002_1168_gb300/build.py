@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libsme.so")
-SOURCES = ["sme_api.cu", "sme_kernels.cu", "sme_noalloc.cu", "sme_seednet.cu"]
+SOURCES = ["sme_api.cu", "sme_kernels.cu", "sme_noalloc.cu", "sme_seednet.cu", "sme_es.cu"]
 HEADERS = ["sme_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

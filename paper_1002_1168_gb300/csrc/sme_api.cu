@@ -827,6 +827,15 @@ int sme_set_option(sme_ctx* c, int option, int value)
     }
 }
 
+int sme_full_search(sme_ctx* c, const uint8_t* luma, int n_frames, sme_mv* mv, uint32_t* sad)
+{
+    if (!c || !luma || !mv || !aligned16(luma)) return SME_ERR_ARG;
+    const int rd = c->prm.ref_distance;
+    if (n_frames <= rd || n_frames - rd > 65535) return SME_ERR_ARG;
+    if (es_smem_bytes(c->m.S, c->m.h) > (size_t)c->smem_optin) return SME_ERR_SIZE;
+    return cuda_status(launch_es(luma, c->g.W, c->g.H, c->m.S, c->m.h, rd, n_frames - rd, mv, sad, c->stream));
+}
+
 int sme_get_option(sme_ctx* c, int option, int* value)
 {
     if (!c || !value) return SME_ERR_ARG;

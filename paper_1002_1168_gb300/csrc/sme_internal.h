@@ -158,6 +158,11 @@ int me_cluster_fits(int S, int cap, int cluster, int warps);
 cudaError_t launch_me_cluster(const Method& m, const MeArgs& a, int cluster, int warps, int helpers, cudaStream_t s);
 cudaError_t launch_compensate(const Geom& g, const Method& m, const CompArgs& a, cudaStream_t s);
 
+// Exhaustive search over V for every MB of `pairs` frame pairs (sme_es.cu).
+size_t es_smem_bytes(int S, int h);
+cudaError_t launch_es(const uint8_t* luma, int W, int H, int S, int h, int rd, int pairs, sme_mv* mv, uint32_t* sad,
+                      cudaStream_t s);
+
 // cuTensorMapEncodeTiled of the installed driver (NULL if unavailable).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 cudaError_t launch_queries(const Geom& g, const Method& m, const QueryArgs& a, cudaStream_t s);

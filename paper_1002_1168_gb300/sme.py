@@ -30,6 +30,7 @@ EXPORTS = [
     "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field",
     "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
     "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_get_option", "sme_autotune",
+    "sme_full_search",
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_forward",
@@ -104,6 +105,7 @@ def _lib():
             "sme_estimate_sequence_noalloc": (i, [C.POINTER(Params), vp, vp, i, vp, vp, C.POINTER(Outputs), vp]),
             "sme_set_option": (i, [vp, i, i]),
             "sme_get_option": (i, [vp, i, C.POINTER(C.c_int)]),
+            "sme_full_search": (i, [vp, vp, i, vp, vp]),
             "sme_autotune": (i, [vp, vp, vp, i, C.POINTER(Outputs), i]),
             "sme_batch_create": (i, [ip, C.POINTER(Params), C.POINTER(Sequence), i, vp]),
             "sme_batch_tune": (i, [vp, i]),
@@ -322,6 +324,18 @@ class Estimator:
         self.set_option(SME_OPT_SCHEDULE, SCHEDULES[name])
         self.set_option(SME_OPT_PAIR_WARPS, pair_warps)
         self.set_option(SME_OPT_CLUSTER_SIZE, cluster)
+
+    def full_search(self, luma, want_sad=True, sync=True):
+        """Exhaustive search over V for every MB of every pair (the ES of
+        Table 1); returns mv [P, M, 2] int16 and sad [P, M] int32 (device)."""
+        t = self.torch
+        P = luma.shape[0] - self.ref_distance
+        mv = t.empty((P, self.M, 2), dtype=t.int16, device=luma.device)
+        sad = t.empty((P, self.M), dtype=t.int32, device=luma.device) if want_sad else None
+        _check(_lib().sme_full_search(self._bind(), _ptr(luma), luma.shape[0], _ptr(mv), _ptr(sad)), "sme_full_search")
+        if sync:
+            self.synchronize()
+        return mv, sad
 
     def get_option(self, option):
         v = C.c_int()

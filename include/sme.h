@@ -211,13 +211,18 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     candidates are awaited; 0 = do all of it after the last arrival.
  *   SME_OPT_CLUSTER_SIZE: CTAs per cluster of the cluster schedule, 2, 4, 8
  *     or 16; 0 (default) = 16, halved until the cluster fits.
+ *   SME_OPT_PAIR_DIRECT: 1 (default) = in the pair schedule, runs of
+ *     transparent MBs (known from the classification launch) are finished
+ *     straight from global memory, four at a time, and only the other MBs
+ *     are staged by TMA; 0 = every MB is staged.
  * Returns SME_ERR_ARG for an unknown option or value. */
 enum {
     SME_OPT_SCHEDULE = 1,
     SME_OPT_PAIR_WARPS = 2,
     SME_OPT_MB_CTAS_PER_SM = 3,
     SME_OPT_SPECULATE = 4,
-    SME_OPT_CLUSTER_SIZE = 5
+    SME_OPT_CLUSTER_SIZE = 5,
+    SME_OPT_PAIR_DIRECT = 6
 };
 enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2, SME_SCHED_CLUSTER = 3 };
 int sme_set_option(sme_ctx* ctx, int option, int value);
@@ -280,7 +285,12 @@ int sme_batch_create(sme_batch** out, const sme_params* p, const sme_sequence* s
 int sme_batch_tune(sme_batch* b, int trials);
 int sme_batch_run(sme_batch* b);
 int sme_batch_synchronize(sme_batch* b);
-int sme_batch_config(sme_batch* b, int* schedule, int* param, int* speculate, float* best_ms);
+/* The batch's execution configuration (after sme_batch_tune: the chosen
+ * one): schedule (SME_SCHED_*), param (pair schedule: warps per CTA; per-MB
+ * schedule: CTAs per SM, 0 = as many as fit), flag (pair schedule:
+ * SME_OPT_PAIR_DIRECT; per-MB schedule: SME_OPT_SPECULATE) and the tuned time
+ * of one run in ms (0 before tuning).  Any output pointer may be NULL. */
+int sme_batch_config(sme_batch* b, int* schedule, int* param, int* flag, float* best_ms);
 int sme_batch_destroy(sme_batch* b);
 
 /* Learned seed proposal (no counterpart in the paper, whose seeds are the

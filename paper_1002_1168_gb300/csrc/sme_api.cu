@@ -55,7 +55,7 @@ struct sme_ctx {
     DevBuf packed, cls, ready, sched, desc, qpacked, qcls;
     std::vector<int> sched_host;
     int sched_P = -1;
-    int schedule = kSchedAuto, pair_warps = 0, mb_ctas_per_sm = 0, speculate = 1, cluster = 0;
+    int schedule = kSchedAuto, pair_warps = 0, mb_ctas_per_sm = 0, speculate = 1, cluster = 0, pair_direct = 1;
     // cluster schedule: per-CTA item lists and consumer slots (rebuilt when P or the size changes)
     DevBuf cl_items, cl_count, cl_cons;
     int cl_P = -1, cl_C = 0, cl_cap = 0, cl_warps = 0, cl_resident = 0;
@@ -366,6 +366,7 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     a.total = (int)total;
     a.fault_ticket = c->fault_ticket;
     a.speculate = c->speculate;
+    a.pair_direct = c->pair_direct;
     a.timeout_ns = c->timeout_ns;
     if (cluster) {
         a.cl_items = (const int*)c->cl_items.p;
@@ -379,7 +380,8 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
         int nw = c->pair_warps > 0 ? c->pair_warps : std::min(kPairWarpsMax, g.MBH);
         while (nw > 1 && me_pair_smem_bytes(c->m.S, nw, g.MBW) > (size_t)c->smem_optin) --nw;
         int per_sm = 0;
-        if (me_pair_occupancy(c->m.S, nw, g.MBW, &per_sm) != cudaSuccess || per_sm < 1) return SME_ERR_CUDA;
+        if (me_pair_occupancy(c->m.S, nw, g.MBW, a.pair_direct != 0, &per_sm) != cudaSuccess || per_sm < 1)
+            return SME_ERR_CUDA;
         const int grid = std::max(1, std::min(c->num_sms * per_sm, P));
         if (launch_me_pair(c->m, a, &maps, nw, grid, c->stream) != cudaSuccess) return SME_ERR_CUDA;
     } else {
@@ -413,13 +415,15 @@ int read_status(sme_ctx* c)
 }
 
 struct ExecCfg {
-    int schedule, pair_warps, mb_ctas_per_sm, speculate, cluster;
+    int schedule, pair_warps, mb_ctas_per_sm, speculate, cluster, pair_direct;
 };
 // The cluster schedule runs single sequences only (the batch skips it).
 const ExecCfg kTuneCandidates[] = {
-    {kSchedMB, 0, 1, 1, 0},      {kSchedMB, 0, 0, 1, 0},      {kSchedMB, 0, 1, 0, 0},  {kSchedMB, 0, 0, 0, 0},
-    {kSchedPair, 4, 0, 0, 0},    {kSchedPair, 8, 0, 0, 0},    {kSchedPair, 16, 0, 0, 0},
-    {kSchedCluster, 0, 0, 1, 16}, {kSchedCluster, 0, 0, 0, 16}, {kSchedCluster, 0, 0, 1, 8},
+    {kSchedMB, 0, 1, 1, 0, 1},       {kSchedMB, 0, 0, 1, 0, 1},       {kSchedMB, 0, 1, 0, 0, 1},
+    {kSchedMB, 0, 0, 0, 0, 1},       {kSchedPair, 4, 0, 0, 0, 1},     {kSchedPair, 8, 0, 0, 0, 1},
+    {kSchedPair, 16, 0, 0, 0, 1},    {kSchedPair, 4, 0, 0, 0, 0},     {kSchedPair, 8, 0, 0, 0, 0},
+    {kSchedPair, 16, 0, 0, 0, 0},    {kSchedCluster, 0, 0, 1, 16, 1}, {kSchedCluster, 0, 0, 0, 16, 1},
+    {kSchedCluster, 0, 0, 1, 8, 1},
 };
 
 // Device time of `trials` back-to-back runs of `enqueue` (the minimum), ms;
@@ -822,6 +826,10 @@ int sme_set_option(sme_ctx* c, int option, int value)
         if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16) return SME_ERR_ARG;
         c->cluster = value;
         return SME_OK;
+    case SME_OPT_PAIR_DIRECT:
+        if (value != 0 && value != 1) return SME_ERR_ARG;
+        c->pair_direct = value;
+        return SME_OK;
     default:
         return SME_ERR_ARG;
     }
@@ -845,6 +853,7 @@ int sme_get_option(sme_ctx* c, int option, int* value)
     case SME_OPT_MB_CTAS_PER_SM: *value = c->mb_ctas_per_sm; return SME_OK;
     case SME_OPT_SPECULATE: *value = c->speculate; return SME_OK;
     case SME_OPT_CLUSTER_SIZE: *value = c->cluster; return SME_OK;
+    case SME_OPT_PAIR_DIRECT: *value = c->pair_direct; return SME_OK;
     default: return SME_ERR_ARG;
     }
 }
@@ -857,13 +866,14 @@ int sme_autotune(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_fr
     if (rc) return rc;
     if ((rc = sme_synchronize(c))) return rc;
     float best = -1.0f;
-    ExecCfg pick = {c->schedule, c->pair_warps, c->mb_ctas_per_sm, c->speculate, c->cluster};
+    ExecCfg pick = {c->schedule, c->pair_warps, c->mb_ctas_per_sm, c->speculate, c->cluster, c->pair_direct};
     for (const ExecCfg& e : kTuneCandidates) {
         c->schedule = e.schedule;
         c->pair_warps = e.pair_warps;
         c->mb_ctas_per_sm = e.mb_ctas_per_sm;
         c->speculate = e.speculate;
         c->cluster = e.cluster;
+        c->pair_direct = e.pair_direct;
         const float ms = time_runs(c->stream, trials, [&] {
             return run_sequence(c, luma, alpha, n_frames, nullptr, nullptr, out);
         });
@@ -878,6 +888,7 @@ int sme_autotune(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_fr
     c->mb_ctas_per_sm = pick.mb_ctas_per_sm;
     c->speculate = pick.speculate;
     c->cluster = pick.cluster;
+    c->pair_direct = pick.pair_direct;
     return best > 0.0f ? SME_OK : SME_ERR_CUDA;
 }
 
@@ -943,7 +954,7 @@ struct sme_batch {
     long long total_mbs = 0;
     DevStatus* status = nullptr;
     DevBuf descs, packed, cls, ready, sched, sched_seq, unit_seq, unit_pair, fseq, ffrm, maps;
-    ExecCfg cfg = {kSchedMB, 0, 0, 1, 0};
+    ExecCfg cfg = {kSchedMB, 0, 0, 1, 0, 1};
     float tuned_ms = 0.0f;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -971,12 +982,14 @@ int batch_enqueue(sme_batch* b, cudaStream_t s)
     a.total = (int)b->total_mbs;
     a.fault_ticket = -1;
     a.speculate = b->cfg.speculate;
+    a.pair_direct = b->cfg.pair_direct;
     a.timeout_ns = kDefaultTimeoutNs;
     if (b->cfg.schedule == kSchedPair) {
         int nw = b->cfg.pair_warps > 0 ? b->cfg.pair_warps : kPairWarpsMax;
         while (nw > 1 && me_pair_smem_bytes(b->m.S, nw, b->mbw_max) > (size_t)b->smem_optin) --nw;
         int per_sm = 0;
-        if (me_pair_occupancy(b->m.S, nw, b->mbw_max, &per_sm) != cudaSuccess || per_sm < 1) return SME_ERR_CUDA;
+        if (me_pair_occupancy(b->m.S, nw, b->mbw_max, a.pair_direct != 0, &per_sm) != cudaSuccess || per_sm < 1)
+            return SME_ERR_CUDA;
         const int grid = std::max(1, std::min(b->num_sms * per_sm, b->total_units));
         MapSet unused;
         memset(&unused, 0, sizeof(unused));
@@ -1230,12 +1243,12 @@ int sme_batch_synchronize(sme_batch* b)
     return batch_read_status(b);
 }
 
-int sme_batch_config(sme_batch* b, int* schedule, int* param, int* speculate, float* best_ms)
+int sme_batch_config(sme_batch* b, int* schedule, int* param, int* flag, float* best_ms)
 {
     if (!b) return SME_ERR_ARG;
     if (schedule) *schedule = b->cfg.schedule;
     if (param) *param = b->cfg.schedule == kSchedPair ? b->cfg.pair_warps : b->cfg.mb_ctas_per_sm;
-    if (speculate) *speculate = b->cfg.speculate;
+    if (flag) *flag = b->cfg.schedule == kSchedPair ? b->cfg.pair_direct : b->cfg.speculate;
     if (best_ms) *best_ms = b->tuned_ms;
     return SME_OK;
 }

@@ -1449,6 +1449,7 @@ constexpr int kAcurWords = 4;                // current BAB: 16 rows x 4 words f
 
 struct PairLayout {
     int o_ref, o_cur, o_aref, o_acur, buf_bytes;  // one buffer (all sections 128-byte aligned)
+    int cls_off;                                  // the warp's copy of its row's MB classes
     int log_off, bar_off, warp_bytes;
     int R;                                        // row slots
     int rows_off, prog_off, unit_off, total;
@@ -1464,7 +1465,8 @@ __host__ __device__ __forceinline__ PairLayout pair_layout(int S, int nw, int mb
     L.buf_bytes = L.o_acur + ceil128(kAcurWords * 4 * 16);
     L.log_off = 2 * L.buf_bytes;
     L.bar_off = L.log_off + ceil16(kMaxLog * 4);
-    L.warp_bytes = ceil128(L.bar_off + 16);
+    L.cls_off = L.bar_off + 16;
+    L.warp_bytes = ceil128(L.cls_off + ceil16(mbw_max));
     L.R = nw + 1;
     L.rows_off = nw * L.warp_bytes;
     L.prog_off = L.rows_off + ceil16(L.R * mbw_max * 4);
@@ -1642,6 +1644,79 @@ __device__ __forceinline__ void factors_smem(const uint8_t* cb, int W, int H, in
     ny = (int)__reduce_add_sync(kFull, (unsigned)cy);
 }
 
+// First MB at or after `from` in the row whose class is not transparent (n if none).
+__device__ __forceinline__ int next_visible(const uint8_t* rowcls, int from, int n, int lane)
+{
+    for (int b = from; b < n; b += 32) {
+        const unsigned bal = __ballot_sync(kFull, b + lane < n && rowcls[b + lane] != SME_TRANSPARENT);
+        if (bal) return b + __ffs(bal) - 1;
+    }
+    return n;
+}
+
+// Transparent MBs u0..u1-1 of row v of pair k (Fig. 1: no vector, (0,0) is
+// final at once): published to the row below and the next pair, and their
+// outputs and co-located prediction error computed from global memory, four
+// MBs per pass so that their loads are in flight together.
+__device__ __forceinline__ void transparent_run(const SeqDesc* sd, const MeArgs& a, int k, int v, int u0, int u1,
+                                                int base, int slot, int* rowmv, int* prog, unsigned long long tag,
+                                                int lane)
+{
+    const int W = sd->W, MBW = sd->MBW, M = sd->M, y = 16 * v + (lane >> 1);
+    const size_t FS = (size_t)W * sd->H;
+    const uint8_t* ref = sd->luma + (size_t)k * FS + (size_t)y * W;
+    const uint8_t* cur = sd->luma + (size_t)(k + sd->rd) * FS + (size_t)y * W;
+    for (int u = u0; u < u1; u += 4) {
+        const int n = min(4, u1 - u);
+        P8 c8[4], r8[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < n) {
+                const int x0 = 16 * (u + j) + 8 * (lane & 1);
+                c8[j] = load8(cur + x0);
+                const uint2 t2 = __ldg(reinterpret_cast<const uint2*>(ref + x0));
+                r8[j].lo = t2.x;
+                r8[j].hi = t2.y;
+            }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < n) {
+                const int mb = v * MBW + u + j, idx = k * M + mb, gid = base + mb;
+                if (lane == 0) {
+                    rowmv[slot * a.mbw_max + u + j] = 0;
+                    st_release_cta(&prog[slot], v * 1024 + u + j + 1);
+                    if (gid != a.fault_ticket) st_ready(a.ready + gid, tag);
+                    sd->mv[idx] = sme_mv{0, 0};
+                    if (sd->cost) sd->cost[idx] = 0;
+                    if (sd->disp) {
+                        sd->disp[2 * idx] = 0.0f;
+                        sd->disp[2 * idx + 1] = 0.0f;
+                    }
+                    if (sd->iters) sd->iters[idx] = 0;
+                    if (sd->npos) sd->npos[idx] = 0;
+                    if (sd->out_cls) sd->out_cls[idx] = (uint8_t)SME_TRANSPARENT;
+                }
+                if (sd->pred)
+                    *reinterpret_cast<uint2*>(sd->pred + (size_t)k * FS + (size_t)y * W + 16 * (u + j) + 8 * (lane & 1)) =
+                        make_uint2(r8[j].lo, r8[j].hi);
+                if (sd->sse || sd->sse_mb) {
+                    const unsigned e = __reduce_add_sync(kFull, sq8(r8[j], c8[j]));
+                    if (lane == 0) {
+                        if (sd->sse) atomicAdd(sd->sse + k, (unsigned long long)e);
+                        if (sd->sse_mb) sd->sse_mb[idx] = e;
+                    }
+                }
+            }
+    }
+    __syncwarp();
+}
+
+// kDirect: runs of transparent MBs (known from the classification launch)
+// are finished by transparent_run and only the other MBs are staged by TMA;
+// otherwise every MB is staged and classified from its staged BAB.  Two
+// instantiations rather than a runtime switch, so that each keeps only its
+// own code (the kernel is at its register limit).
+template <bool kDirect>
 __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArgs a, const __grid_constant__ PairMaps maps0)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -1654,6 +1729,7 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
     uint8_t* wbase = smem + (size_t)wid * L.warp_bytes;
     int* slog = reinterpret_cast<int*>(wbase + L.log_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + L.bar_off);
+    uint8_t* s_rowcls = wbase + L.cls_off;
     int* rowmv = reinterpret_cast<int*>(smem + L.rows_off);
     int* prog = reinterpret_cast<int*>(smem + L.prog_off);
     int* s_unit = reinterpret_cast<int*>(smem + L.unit_off);
@@ -1695,22 +1771,59 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
         for (int v = wid; v < MBH && !failed; v += nw) {
             const int slot = v % L.R, pslot = (v + L.R - 1) % L.R;
             const int Y0 = 16 * v, y = Y0 + (lane >> 1);
+            if constexpr (kDirect) {
+                // the row's MB classes (Fig. 1 Block_Type, from the classification launch)
+                const uint8_t* rowcls = sd->cls + (size_t)(k + rd) * M + (size_t)v * MBW;
+                for (int i = lane; i < MBW; i += 32) s_rowcls[i] = __ldg(rowcls + i);
+            }
+            // Row slots are reused every R = nw + 1 rows.  Row v - R + 1, the one
+            // that reads slot v % R last, is this warp's previous row; waiting
+            // here until row v - R has filled the slot makes sure that the slot
+            // holds no older row, whose reader could still be running: a warp
+            // with transparent rows publishes without waiting for the row above
+            // and could otherwise run more than R rows ahead.
+            if (v >= L.R) {
+                bool ok = true;
+                if (lane == 0) ok = wait_progress(&prog[slot], (v - L.R) * 1024 + MBW, a.status, a.timeout_ns);
+                if (!__shfl_sync(kFull, ok, 0)) {
+                    if (lane == 0 && !ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
+                    failed = true;
+                    break;
+                }
+            }
+            __syncwarp();
             int akey = 0;  // A: this row's previous vector
-            if (lane == 0) issue_mb_boxes(wbase + cur * L.buf_bytes, L, mp, S, 0, Y0, k, k + rd, &bars[cur], tx);
-            pending |= 1u << cur;
+            // The boxes of the next staged MB are always in flight while the
+            // current one (or a transparent run before it) is processed.
+            int nt = 0;
+            if constexpr (kDirect) nt = next_visible(s_rowcls, 0, MBW, lane);
             unsigned long long tnext = 0;
-            if (lane == 3 && k > 0) tnext = ld_ready(a.ready + base + v * MBW - M);
-            for (int u = 0; u < MBW; ++u) {
+            if (nt < MBW) {
+                if (lane == 0) issue_mb_boxes(wbase + cur * L.buf_bytes, L, mp, S, 16 * nt, Y0, k, k + rd, &bars[cur], tx);
+                pending |= 1u << cur;
+                if (lane == 3 && k > 0) tnext = ld_ready(a.ready + base + v * MBW + nt - M);
+            }
+            for (int u = 0; u < MBW && !failed;) {
+                if constexpr (kDirect) {
+                    if (u < nt) {
+                        transparent_run(sd, a, k, v, u, nt, base, slot, rowmv, prog, tag, lane);
+                        akey = 0;
+                        u = nt;
+                        continue;
+                    }
+                }
                 const int mb = v * MBW + u, idx = k * M + mb, gid = base + mb;
                 const int X0 = 16 * u, x0 = X0 + 8 * (lane & 1);
+                int nn = u + 1;
+                if constexpr (kDirect) nn = next_visible(s_rowcls, u + 1, MBW, lane);
                 const int nb = cur ^ 1;
-                if (u + 1 < MBW) {
+                if (nn < MBW) {
                     if (lane == 0)
-                        issue_mb_boxes(wbase + nb * L.buf_bytes, L, mp, S, X0 + 16, Y0, k, k + rd, &bars[nb], tx);
+                        issue_mb_boxes(wbase + nb * L.buf_bytes, L, mp, S, 16 * nn, Y0, k, k + rd, &bars[nb], tx);
                     pending |= 1u << nb;
                 }
                 const unsigned long long tcur = tnext;
-                if (lane == 3 && k > 0 && u + 1 < MBW) tnext = ld_ready(a.ready + gid + 1 - M);
+                if (lane == 3 && k > 0 && nn < MBW) tnext = ld_ready(a.ready + base + v * MBW + nn - M);
 
                 bool ok = true;
                 if (lane == 0) ok = mbar_wait(&bars[cur], (parity >> cur) & 1u, a.timeout_ns);
@@ -1725,11 +1838,17 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
                 const uint8_t* buf = wbase + cur * L.buf_bytes;
                 const uint8_t* win = buf + L.o_ref;
                 const uint32_t* acur = reinterpret_cast<const uint32_t*>(buf + L.o_acur);
-                // Fig. 1 Block_Type from the current BAB (16 rows of 16 bits).
-                unsigned ones = 0;
-                if (lane < 16) ones = __popc((acur[lane * kAcurWords + (X0 >> 5) - ((X0 >> 5) & ~3)] >> (X0 & 31)) & 0xffffu);
-                ones = __reduce_add_sync(kFull, ones);
-                const int cls = ones == 0 ? SME_TRANSPARENT : (ones == 256 ? SME_OPAQUE : SME_BOUNDARY);
+                int cls;
+                if constexpr (kDirect) {
+                    cls = s_rowcls[u];  // boundary or opaque
+                } else {
+                    // Fig. 1 Block_Type from the staged current BAB (16 rows of 16 bits).
+                    unsigned ones = 0;
+                    if (lane < 16)
+                        ones = __popc((acur[lane * kAcurWords + (X0 >> 5) - ((X0 >> 5) & ~3)] >> (X0 & 31)) & 0xffffu);
+                    ones = __reduce_add_sync(kFull, ones);
+                    cls = ones == 0 ? SME_TRANSPARENT : (ones == 256 ? SME_OPAQUE : SME_BOUNDARY);
+                }
                 P8 c8;
                 {
                     const uint2 t2 = *reinterpret_cast<const uint2*>(buf + L.o_cur + (1 + (lane >> 1)) * kCurBoxW + 16 +
@@ -1738,7 +1857,7 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
                     c8.hi = t2.y;
                 }
 
-                if (cls == SME_TRANSPARENT) {
+                if (!kDirect && cls == SME_TRANSPARENT) {
                     // Fig. 1: (0,0) is final at once.
                     if (lane == 0) {
                         rowmv[slot * a.mbw_max + u] = 0;
@@ -1825,6 +1944,8 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
                     finish_mb(sd, idx, k, cls, r, c8, slog, lane, FS, W, y, x0);
                 }
                 cur = nb;
+                nt = nn;
+                ++u;
             }
             // A failing warp drains its own copies in flight before the CTA moves on.
             if (failed) {
@@ -2061,18 +2182,20 @@ size_t me_pair_smem_bytes(int S, int nwarps, int mbw_max)
     return (size_t)pair_layout(S, nwarps, mbw_max).total + 128;  // + alignment slack
 }
 
-cudaError_t me_pair_occupancy(int S, int nwarps, int mbw_max, int* blocks_per_sm)
+cudaError_t me_pair_occupancy(int S, int nwarps, int mbw_max, bool direct, int* blocks_per_sm)
 {
     const size_t smem = me_pair_smem_bytes(S, nwarps, mbw_max);
-    cudaError_t e = cudaFuncSetAttribute(me_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void* fn = direct ? (const void*)me_pair_kernel<true> : (const void*)me_pair_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, me_pair_kernel, 32 * nwarps, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 32 * nwarps, smem);
 }
 
 cudaError_t launch_me_pair(const Method& m, const MeArgs& a, const void* maps, int nwarps, int grid, cudaStream_t s)
 {
     const size_t smem = me_pair_smem_bytes(m.S, nwarps, a.mbw_max);
-    cudaError_t e = cudaFuncSetAttribute(me_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto* fn = a.pair_direct ? me_pair_kernel<true> : me_pair_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -2084,7 +2207,7 @@ cudaError_t launch_me_pair(const Method& m, const MeArgs& a, const void* maps, i
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, me_pair_kernel, a, *reinterpret_cast<const PairMaps*>(maps));
+    return cudaLaunchKernelEx(&cfg, fn, a, *reinterpret_cast<const PairMaps*>(maps));
 }
 
 cudaError_t launch_compensate(const Geom& g, const Method& m, const CompArgs& a, cudaStream_t s)

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsme.so")
 SME_TRANSPARENT, SME_OPAQUE, SME_BOUNDARY = 0, 1, 2
 SME_OPT_SCHEDULE, SME_OPT_PAIR_WARPS, SME_OPT_MB_CTAS_PER_SM, SME_OPT_SPECULATE = 1, 2, 3, 4
 SME_OPT_CLUSTER_SIZE = 5
+SME_OPT_PAIR_DIRECT = 6
 SCHEDULES = {"auto": 0, "mb": 1, "pair": 2, "cluster": 3}
 STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4: "SME_ERR_TIMEOUT",
           5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE", 8: "SME_ERR_SCRATCH"}
@@ -347,7 +348,8 @@ class Estimator:
         names = {v: k for k, v in SCHEDULES.items()}
         return {"schedule": names[self.get_option(SME_OPT_SCHEDULE)], "pair_warps": self.get_option(SME_OPT_PAIR_WARPS),
                 "mb_ctas_per_sm": self.get_option(SME_OPT_MB_CTAS_PER_SM),
-                "speculate": self.get_option(SME_OPT_SPECULATE), "cluster": self.get_option(SME_OPT_CLUSTER_SIZE)}
+                "speculate": self.get_option(SME_OPT_SPECULATE), "cluster": self.get_option(SME_OPT_CLUSTER_SIZE),
+                "pair_direct": self.get_option(SME_OPT_PAIR_DIRECT)}
 
     def autotune(self, luma, alpha, out=None, trials=3, want=("cost", "disp", "iters", "npos", "mb_class", "sse")):
         """Pick the fastest execution configuration for this sequence shape."""
@@ -424,7 +426,7 @@ class Batch:
         _check(_lib().sme_batch_config(self._h, C.byref(s_), C.byref(p_), C.byref(sp_), C.byref(ms)),
                "sme_batch_config")
         name = {v: k for k, v in SCHEDULES.items()}[s_.value]
-        return {"schedule": name, "param": p_.value, "speculate": sp_.value, "tuned_ms": ms.value}
+        return {"schedule": name, "param": p_.value, "flag": sp_.value, "tuned_ms": ms.value}
 
     def close(self):
         if getattr(self, "_h", None):

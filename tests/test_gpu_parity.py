@@ -30,15 +30,25 @@ def cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-SCHEDULES = ["pair", "mb", "cluster"]
+# "pair_staged": the pair schedule with every MB staged by TMA (transparent
+# MBs included) instead of finishing transparent runs from global memory.
+SCHEDULES = ["pair", "pair_staged", "mb", "cluster"]
+
+
+def set_schedule(sme, est, schedule, pair_warps=0):
+    if schedule == "pair_staged":
+        est.set_schedule("pair", pair_warps=pair_warps)
+        est.set_option(sme.SME_OPT_PAIR_DIRECT, 0)
+    else:
+        est.set_schedule(schedule, pair_warps=pair_warps if schedule == "pair" else 0)
 
 
 def run_both(sme, luma, alpha, S=16, h=1, K=8, theta=2.0, eps=1.0, rd=1, temporal=None, seed=None,
-             want_pred=True, schedule="pair"):
+             want_pred=True, schedule="pair", pair_warps=0):
     F, H, W = luma.shape
     est = sme.Estimator(W, H, search_range=S, subpel=h, theta=theta, epsilon=eps, max_iters=K,
                         ref_distance=rd)
-    est.set_schedule(schedule)
+    set_schedule(sme, est, schedule, pair_warps)
     want = ("cost", "disp", "iters", "npos", "mb_class", "sse_mb", "sse") + (("pred",) if want_pred else ())
     g = est.estimate_sequence(cuda(luma), cuda(alpha),
                               temporal_in=None if temporal is None else cuda(temporal.astype(np.int16)),
@@ -209,6 +219,21 @@ def test_all_transparent_or_all_opaque(sme, fill, schedule):
         assert (g["mv"] == 0).all() and (g["npos"] == 0).all()
 
 
+@pytest.mark.parametrize("schedule", ["pair", "pair_staged"])
+@pytest.mark.parametrize("warps", [2, 3])
+def test_pair_row_slots_with_transparent_rows_below(sme, schedule, warps):
+    """Opaque MB rows over transparent ones, few warps per pair: a warp whose
+    rows are transparent finishes them quickly and must not reuse a row slot
+    (one per warp + 1) while a slower warp still reads the row it holds."""
+    luma, _ = synth.translated_pair(256, 256, (3, 1), seed=11, noise_sigma=1.0)
+    luma = np.concatenate([luma, np.roll(luma[1:], (1, 3), axis=(0, 1))])
+    alpha = np.zeros_like(luma)
+    alpha[:, :128] = 255
+    g, o, p = run_both(sme, luma, alpha, S=8, h=2, schedule=schedule, pair_warps=warps)
+    assert_parity(g, o, p, luma)
+    assert (g["mv"][:, :64] != 0).any(axis=-1).mean() > 0.5  # the rows read below carry vectors
+
+
 @pytest.mark.parametrize("schedule", SCHEDULES)
 def test_batch_shapes_each_sequence(sme, schedule):
     """Sequences of the uneven-size batch (one of each frame size, 4 frames)."""
@@ -316,7 +341,7 @@ def test_bounded_wait_reports_timeout_and_context_recovers(sme, schedule):
     luma = np.concatenate([luma, luma[:1]])
     alpha = np.concatenate([alpha, alpha[:1]])
     est = sme.Estimator(W, H, search_range=8, subpel=1)
-    est.set_schedule(schedule)
+    set_schedule(sme, est, schedule)
     # MB 0 of pair 0 is A of MB 1 and B of MB 4 (per-MB schedule) and T of
     # MB 0 of pair 1 (both schedules)
     est.debug_set_fault(skip_ticket=0, timeout_ns=20_000_000)

@@ -11,10 +11,14 @@ from .oracle import (  # noqa: F401
     build_oracle,
     classify_frame,
     compensate,
+    compensate4,
     estimate_pair,
+    estimate_pair4,
     estimate_sequence,
+    estimate_sequence4,
     full_search,
     gradient_step,
+    gradient_step_block,
     interp,
     psnr,
     shape_sad,

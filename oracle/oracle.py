@@ -92,6 +92,13 @@ def _load():
         lib.orc_estimate_sequence.restype = C.c_int
         lib.orc_full_search.argtypes = [C.c_void_p, C.c_void_p] + [C.c_int] * 5 + [C.c_void_p] * 2
         lib.orc_full_search.restype = C.c_uint64
+        lib.orc_gradient_step_block.argtypes = [P(_Params), u8p, u8p] + [C.c_int] * 5 + [P(C.c_float)]
+        lib.orc_estimate_pair4.argtypes = [P(_Params), u8p, u8p, u8p, u8p] + [C.c_void_p] * 7
+        lib.orc_estimate_pair4.restype = C.c_int
+        lib.orc_compensate4.argtypes = [P(_Params), u8p, u8p, C.c_void_p, C.c_void_p]
+        lib.orc_compensate4.restype = C.c_uint64
+        lib.orc_estimate_sequence4.argtypes = [P(_Params), u8p, u8p, C.c_int, C.c_int] + [C.c_void_p] * 9
+        lib.orc_estimate_sequence4.restype = C.c_int
         _lib = lib
         return lib
 
@@ -233,3 +240,73 @@ def full_search(ref, cur, W, H, h, S, block=16):
     cur = np.ascontiguousarray(cur, np.uint8)
     total = _load().orc_full_search(_ptr(ref), _ptr(cur), W, H, h, S, block, _ptr(bm), _ptr(bs))
     return bm, bs, total
+
+
+# ---- four motion vectors per MB (Sec. 3.2: the recursive search on 8x8 blocks) ----
+
+def gradient_step_block(params: OracleParams, ref, cur, X0, Y0, n, dx, dy):
+    """Eqs. 3-5 over the n x n block at (X0, Y0): one FP32 update (pixels)."""
+    ref, pr = _u8(ref)
+    cur, pc = _u8(cur)
+    out = (C.c_float * 2)()
+    cp = params.c()
+    _load().orc_gradient_step_block(C.byref(cp), pr, pc, X0, Y0, n, dx, dy, out)
+    return np.array([out[0], out[1]], np.float32)
+
+
+def _outputs4(n):
+    return dict(mv=np.zeros((n, 4, 2), np.int16), cost=np.zeros((n, 4), np.uint32),
+                disp=np.zeros((n, 4, 2), np.float32), iters=np.zeros((n, 4), np.uint8),
+                npos=np.zeros((n, 4), np.uint8), mbclass=np.zeros(n, np.uint8))
+
+
+def estimate_pair4(params: OracleParams, ref, cur, aref, acur, temporal4=None):
+    """Fig. 1 at MB level, then the pixel recursive search of each 8x8 block
+    (four vectors per MB); temporal4 [M, 4, 2] or None."""
+    M = params.mbs
+    ref, pr = _u8(ref)
+    cur, pc = _u8(cur)
+    aref, par = _u8(aref)
+    acur, pac = _u8(acur)
+    tmp = None if temporal4 is None else np.ascontiguousarray(temporal4, np.int16).reshape(M, 4, 2)
+    o = _outputs4(M)
+    cp = params.c()
+    rc = _load().orc_estimate_pair4(C.byref(cp), pr, pc, par, pac, _ptr(tmp), _ptr(o["mv"]), _ptr(o["cost"]),
+                                    _ptr(o["disp"]), _ptr(o["iters"]), _ptr(o["npos"]), _ptr(o["mbclass"]))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return o
+
+
+def compensate4(params: OracleParams, ref, cur, mv4, want_pred=False):
+    """Motion compensation with one vector per 8x8 block; (sse, pred or None)."""
+    ref, pr = _u8(ref)
+    cur, pc = _u8(cur)
+    mv4 = np.ascontiguousarray(mv4, np.int16).reshape(params.mbs, 4, 2)
+    pred = np.zeros_like(ref) if want_pred else None
+    cp = params.c()
+    sse = _load().orc_compensate4(C.byref(cp), pr, pc, _ptr(mv4), _ptr(pred))
+    if sse == 2 ** 64 - 1:
+        raise ValueError("a motion vector lies outside the valid set")
+    return sse, pred
+
+
+def estimate_sequence4(params: OracleParams, luma, alpha, ref_distance=1, temporal_in4=None, want_pred=False):
+    """Four vectors per MB over a sequence; outputs [P, M, 4, ...] (mbclass [P, M])."""
+    luma, pl = _u8(luma)
+    alpha, pa = _u8(alpha)
+    F = luma.shape[0]
+    P, M = F - ref_distance, params.mbs
+    tmp = None if temporal_in4 is None else np.ascontiguousarray(temporal_in4, np.int16).reshape(M, 4, 2)
+    o = {k: v.reshape((P, M) + v.shape[1:]) for k, v in _outputs4(P * M).items()}
+    o["sse"] = np.zeros(P, np.uint64)
+    pred = np.zeros((P,) + luma.shape[1:], np.uint8) if want_pred else None
+    cp = params.c()
+    rc = _load().orc_estimate_sequence4(C.byref(cp), pl, pa, F, ref_distance, _ptr(tmp), _ptr(o["mv"]),
+                                        _ptr(o["cost"]), _ptr(o["disp"]), _ptr(o["iters"]), _ptr(o["npos"]),
+                                        _ptr(o["mbclass"]), _ptr(o["sse"]), _ptr(pred))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    o["pred"] = pred
+    o["psnr"] = np.array([psnr(s, params.width, params.height) for s in o["sse"]])
+    return o

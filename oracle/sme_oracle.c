@@ -457,3 +457,239 @@ uint64_t orc_full_search(const uint8_t* ref, const uint8_t* cur, int W, int H, i
         }
     return total;
 }
+
+/* ================================================================== */
+/* Four motion vectors per macroblock (Sec. 3.2: MPEG-4 allows four    */
+/* vectors per MB, so the recursive search works on 8x8 blocks).        */
+/* Readings taken here:                                                 */
+/*  - The block recursive search stays at MB level exactly as in Fig. 1 */
+/*    (classes, 16x16 costs, first strict minimum of A, B, C, T); its   */
+/*    winner starts the pixel recursive search of each 8x8 block        */
+/*    b = 2*by + bx (raster order inside the MB), and every block keeps */
+/*    its own vector.                                                   */
+/*  - A neighbouring MB contributes the vector of its block nearest to  */
+/*    the first block of the current MB (the MPEG-4 predictor layout):  */
+/*    A = block 1 of the left MB, B = block 2 of the MB above, C = block */
+/*    2 of the MB above-right, T = block 0 of the same MB in the        */
+/*    previous field.                                                   */
+/*  - Block searches use the MB's valid set V; the gradient step of     */
+/*    Eqs. 3-5 runs over the block's 64 pixels, summed by the contiguous */
+/*    pairwise tree in block raster order.                              */
+/*  - Boundary MBs: the winner for all four blocks, each block costed by */
+/*    the alpha mismatches of its own quadrant; transparent MBs: zero.  */
+/*  - Positions of a block (Table 1 counts per 8x8 block): the distinct */
+/*    MB candidates plus the block's own PRS positions.                 */
+/* Arrays are [M][4] (block-major inside each MB).                      */
+/* ================================================================== */
+
+/* Eqs. 3-5 over the n x n block at (X0, Y0): as orc_gradient_step, for a
+ * block of any size n (n*n a power of two, at most 256). */
+void orc_gradient_step_block(const orc_params* P, const uint8_t* ref, const uint8_t* cur,
+                             int X0, int Y0, int n, int dx, int dy, float out[2])
+{
+    const int W = P->width, H = P->height, h = P->subpel;
+    float tx[256], ty[256];
+    int nx = 0, ny = 0;
+    const float lim = 2.0f * P->theta;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            int x = X0 + i, y = Y0 + j;
+            int dpd = ref_sample(ref, W, h, x * h + dx, y * h + dy) - (int)cur[(size_t)y * W + x];
+            float ux = 0.0f, uy = 0.0f;
+            if (x > 0 && x < W - 1) {
+                int g = (int)cur[(size_t)y * W + x + 1] - (int)cur[(size_t)y * W + x - 1];
+                if ((float)abs(g) >= lim) ux = 2.0f / (float)g;
+            }
+            if (y > 0 && y < H - 1) {
+                int g = (int)cur[(size_t)(y + 1) * W + x] - (int)cur[(size_t)(y - 1) * W + x];
+                if ((float)abs(g) >= lim) uy = 2.0f / (float)g;
+            }
+            nx += ux != 0.0f;
+            ny += uy != 0.0f;
+            tx[j * n + i] = (float)dpd * ux;
+            ty[j * n + i] = (float)dpd * uy;
+        }
+    float sx = pairwise_sum(tx, n * n), sy = pairwise_sum(ty, n * n);
+    out[0] = (nx > 0) ? -(P->epsilon * (sx / (float)nx)) : 0.0f;
+    out[1] = (ny > 0) ? -(P->epsilon * (sy / (float)ny)) : 0.0f;
+}
+
+/* Alpha mismatches over the n x n block at (X0, Y0), reference displaced by
+ * the full-pel part of d (trunc toward zero), as orc_shape_sad. */
+static uint32_t shape_block(const uint8_t* aref, const uint8_t* acur, int W, int h, int n,
+                            int X0, int Y0, int dx, int dy)
+{
+    int fx = dx / h, fy = dy / h;
+    uint32_t s = 0;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            int x = X0 + i, y = Y0 + j;
+            s += (uint32_t)((acur[(size_t)y * W + x] != 0) != (aref[(size_t)(y + fy) * W + (x + fx)] != 0));
+        }
+    return s;
+}
+
+/* Sec. 3.2 pixel recursive search of the n x n block at (X0, Y0), the same
+ * loop as prs_search with the block's SAD and gradient step. */
+static int prs_block(const orc_params* P, const uint8_t* ref, const uint8_t* cur, int X0, int Y0, int n,
+                     int lox, int hix, int loy, int hiy, int* pdx, int* pdy, uint32_t* pc,
+                     float last[2], pos_set* ps)
+{
+    const int W = P->width, h = P->subpel;
+    int dx = *pdx, dy = *pdy, k = 0;
+    uint32_t c = *pc;
+    last[0] = last[1] = 0.0f;
+    while (k < P->max_iters) {
+        ++k;
+        orc_gradient_step_block(P, ref, cur, X0, Y0, n, dx, dy, last);
+        int qx = iclamp(dx + (int)roundf((float)h * last[0]), lox, hix);
+        int qy = iclamp(dy + (int)roundf((float)h * last[1]), loy, hiy);
+        if (qx != dx || qy != dy) {
+            uint32_t cq = block_sad(ref, cur, W, h, n, X0, Y0, qx, qy);
+            pos_note(ps, qx, qy);
+            if (cq < c) { dx = qx; dy = qy; c = cq; continue; }
+        }
+        int bx = dx, by = dy;
+        uint32_t bcost = c;
+        for (int jj = -1; jj <= 1; ++jj)
+            for (int ii = -1; ii <= 1; ++ii) {
+                if (!ii && !jj) continue;
+                int nx = iclamp(dx + ii, lox, hix), ny = iclamp(dy + jj, loy, hiy);
+                if (nx == dx && ny == dy) continue;
+                uint32_t cn = block_sad(ref, cur, W, h, n, X0, Y0, nx, ny);
+                pos_note(ps, nx, ny);
+                if (cn < bcost) { bcost = cn; bx = nx; by = ny; }
+            }
+        if (bcost < c) { dx = bx; dy = by; c = bcost; continue; }
+        break;
+    }
+    *pdx = dx;
+    *pdy = dy;
+    *pc = c;
+    return k;
+}
+
+/* One frame pair with four vectors per MB; temporal4 is the previous
+ * field [M][4] (NULL: zero vectors).  Outputs [M][4] except mbclass [M]. */
+int orc_estimate_pair4(const orc_params* P, const uint8_t* ref, const uint8_t* cur,
+                       const uint8_t* aref, const uint8_t* acur, const orc_mv* temporal4,
+                       orc_mv* mv4, uint32_t* cost4, float* disp4, uint8_t* iters4,
+                       uint8_t* npos4, uint8_t* mbclass)
+{
+    const int W = P->width, H = P->height, h = P->subpel, S = P->search_range;
+    if (W <= 0 || H <= 0 || W % 16 || H % 16) return 1;
+    if (h != 1 && h != 2) return 1;
+    const int mbw = W / 16, mbh = H / 16;
+    for (int v = 0; v < mbh; ++v)
+        for (int u = 0; u < mbw; ++u) {
+            const int m = v * mbw + u, X0 = 16 * u, Y0 = 16 * v;
+            const int cls = orc_classify_mb(acur, W, X0, Y0);
+            mbclass[m] = (uint8_t)cls;
+            if (cls == ORC_TRANSPARENT) {
+                for (int b = 0; b < 4; ++b) {
+                    mv4[4 * m + b].dx = mv4[4 * m + b].dy = 0;
+                    cost4[4 * m + b] = 0;
+                    disp4[8 * m + 2 * b] = disp4[8 * m + 2 * b + 1] = 0.0f;
+                    iters4[4 * m + b] = 0;
+                    npos4[4 * m + b] = 0;
+                }
+                continue;
+            }
+            int lox, hix, loy, hiy;
+            orc_valid_range(W, H, 16, S, h, X0, Y0, &lox, &hix, &loy, &hiy);
+            int cx[4] = {0, 0, 0, 0}, cy[4] = {0, 0, 0, 0};
+            if (u > 0) { cx[0] = mv4[4 * (m - 1) + 1].dx; cy[0] = mv4[4 * (m - 1) + 1].dy; }   /* A */
+            if (v > 0) { cx[1] = mv4[4 * (m - mbw) + 2].dx; cy[1] = mv4[4 * (m - mbw) + 2].dy; } /* B */
+            if (v > 0 && u < mbw - 1) {                                                       /* C */
+                cx[2] = mv4[4 * (m - mbw + 1) + 2].dx;
+                cy[2] = mv4[4 * (m - mbw + 1) + 2].dy;
+            }
+            if (temporal4) { cx[3] = temporal4[4 * m].dx; cy[3] = temporal4[4 * m].dy; }      /* T */
+            pos_set brs;
+            brs.n = 0;
+            int best = -1;
+            uint32_t bc = 0;
+            for (int k = 0; k < 4; ++k) {
+                cx[k] = iclamp(cx[k], lox, hix);
+                cy[k] = iclamp(cy[k], loy, hiy);
+                uint32_t c = mb_cost(P, cls, ref, cur, aref, acur, X0, Y0, cx[k], cy[k]);
+                pos_note(&brs, cx[k], cy[k]);
+                if (best < 0 || c < bc) { best = k; bc = c; }
+            }
+            for (int b = 0; b < 4; ++b) {
+                const int BX = X0 + 8 * (b & 1), BY = Y0 + 8 * (b >> 1);
+                int dx = cx[best], dy = cy[best], k = 0;
+                float last[2] = {0.0f, 0.0f};
+                uint32_t c;
+                pos_set ps = brs;
+                if (cls == ORC_BOUNDARY) {
+                    c = shape_block(aref, acur, W, h, 8, BX, BY, dx, dy);
+                } else {
+                    c = block_sad(ref, cur, W, h, 8, BX, BY, dx, dy);
+                    k = prs_block(P, ref, cur, BX, BY, 8, lox, hix, loy, hiy, &dx, &dy, &c, last, &ps);
+                }
+                mv4[4 * m + b].dx = (int16_t)dx;
+                mv4[4 * m + b].dy = (int16_t)dy;
+                cost4[4 * m + b] = c;
+                disp4[8 * m + 2 * b] = last[0];
+                disp4[8 * m + 2 * b + 1] = last[1];
+                iters4[4 * m + b] = (uint8_t)k;
+                npos4[4 * m + b] = (uint8_t)ps.n;
+            }
+        }
+    return 0;
+}
+
+/* Motion compensation with four vectors per MB: pred(p) = ref(p + MV of the
+ * 8x8 block holding p); the SSE against cur.  Every vector must lie in its
+ * MB's V; returns UINT64_MAX otherwise. */
+uint64_t orc_compensate4(const orc_params* P, const uint8_t* ref, const uint8_t* cur,
+                         const orc_mv* mv4, uint8_t* pred)
+{
+    const int W = P->width, H = P->height, h = P->subpel, mbw = W / 16;
+    uint64_t sse = 0;
+    for (int v = 0; v < H / 16; ++v)
+        for (int u = 0; u < mbw; ++u) {
+            int lox, hix, loy, hiy;
+            orc_valid_range(W, H, 16, P->search_range, h, 16 * u, 16 * v, &lox, &hix, &loy, &hiy);
+            for (int b = 0; b < 4; ++b) {
+                const orc_mv d = mv4[4 * (v * mbw + u) + b];
+                if (d.dx < lox || d.dx > hix || d.dy < loy || d.dy > hiy) return UINT64_MAX;
+            }
+        }
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int b = 2 * ((y % 16) / 8) + (x % 16) / 8;
+            const orc_mv d = mv4[4 * ((y / 16) * mbw + x / 16) + b];
+            int p = ref_sample(ref, W, h, x * h + d.dx, y * h + d.dy);
+            int e = (int)cur[(size_t)y * W + x] - p;
+            sse += (uint64_t)(e * e);
+            if (pred) pred[(size_t)y * W + x] = (uint8_t)p;
+        }
+    return sse;
+}
+
+/* A whole sequence with four vectors per MB (as orc_estimate_sequence; the
+ * temporal candidate of pair k is block 0 of the field of pair k-1). */
+int orc_estimate_sequence4(const orc_params* P, const uint8_t* luma, const uint8_t* alpha,
+                           int n_frames, int ref_distance, const orc_mv* temporal_in4,
+                           orc_mv* mv4, uint32_t* cost4, float* disp4, uint8_t* iters4,
+                           uint8_t* npos4, uint8_t* mbclass, uint64_t* sse, uint8_t* pred)
+{
+    const size_t fs = (size_t)P->width * P->height;
+    const int M = (P->width / 16) * (P->height / 16);
+    const int np = n_frames - ref_distance;
+    if (ref_distance < 1 || np < 1) return 1;
+    for (int k = 0; k < np; ++k) {
+        const uint8_t* ref = luma + fs * k;
+        const uint8_t* cur = luma + fs * (k + ref_distance);
+        const orc_mv* tmp = k == 0 ? temporal_in4 : mv4 + (size_t)4 * (k - 1) * M;
+        int rc = orc_estimate_pair4(P, ref, cur, alpha + fs * k, alpha + fs * (k + ref_distance), tmp,
+                                    mv4 + (size_t)4 * k * M, cost4 + (size_t)4 * k * M,
+                                    disp4 + (size_t)8 * k * M, iters4 + (size_t)4 * k * M,
+                                    npos4 + (size_t)4 * k * M, mbclass + (size_t)k * M);
+        if (rc) return rc;
+        sse[k] = orc_compensate4(P, ref, cur, mv4 + (size_t)4 * k * M, pred ? pred + fs * k : NULL);
+    }
+    return 0;
+}

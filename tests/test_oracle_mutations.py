@@ -96,7 +96,53 @@ MUTANTS = [
 ]
 
 
-def _run_mutant(tmpdir, i, name, old, new):
+# Mistakes in the four-vector mode (Sec. 3.2, 8x8 blocks), caught by the pins
+# of tests/test_oracle_four_mv.py.
+MUTANTS4 = [
+    ("A from block 0 of the left MB",
+     "if (u > 0) { cx[0] = mv4[4 * (m - 1) + 1].dx; cy[0] = mv4[4 * (m - 1) + 1].dy; }",
+     "if (u > 0) { cx[0] = mv4[4 * (m - 1) + 0].dx; cy[0] = mv4[4 * (m - 1) + 0].dy; }"),
+    ("B from block 3 of the MB above",
+     "if (v > 0) { cx[1] = mv4[4 * (m - mbw) + 2].dx; cy[1] = mv4[4 * (m - mbw) + 2].dy; }",
+     "if (v > 0) { cx[1] = mv4[4 * (m - mbw) + 3].dx; cy[1] = mv4[4 * (m - mbw) + 3].dy; }"),
+    ("C from block 3 of the MB above-right",
+     "cx[2] = mv4[4 * (m - mbw + 1) + 2].dx;\n                cy[2] = mv4[4 * (m - mbw + 1) + 2].dy;",
+     "cx[2] = mv4[4 * (m - mbw + 1) + 3].dx;\n                cy[2] = mv4[4 * (m - mbw + 1) + 3].dy;"),
+    ("T from block 1 of the previous field",
+     "if (temporal4) { cx[3] = temporal4[4 * m].dx; cy[3] = temporal4[4 * m].dy; }",
+     "if (temporal4) { cx[3] = temporal4[4 * m + 1].dx; cy[3] = temporal4[4 * m + 1].dy; }"),
+    ("temporal field of four vectors not chained",
+     "const orc_mv* tmp = k == 0 ? temporal_in4 : mv4 + (size_t)4 * (k - 1) * M;",
+     "const orc_mv* tmp = temporal_in4;"),
+    ("blocks in column order",
+     "const int BX = X0 + 8 * (b & 1), BY = Y0 + 8 * (b >> 1);",
+     "const int BX = X0 + 8 * (b >> 1), BY = Y0 + 8 * (b & 1);"),
+    ("block search starts from the 16x16 cost",
+     "c = block_sad(ref, cur, W, h, 8, BX, BY, dx, dy);", "c = bc;"),
+    ("boundary quadrant costed at the MB origin",
+     "c = shape_block(aref, acur, W, h, 8, BX, BY, dx, dy);", "c = shape_block(aref, acur, W, h, 8, X0, Y0, dx, dy);"),
+    ("block positions without the MB candidates",
+     "pos_set ps = brs;", "pos_set ps;\n                ps.n = 0;"),
+    ("block gradient mean over all 64 pixels",
+     "out[0] = (nx > 0) ? -(P->epsilon * (sx / (float)nx)) : 0.0f;",
+     "out[0] = (nx > 0) ? -(P->epsilon * (sx / (float)(n * n))) : 0.0f;"),
+    ("block gradient terms laid out 16 wide",
+     "tx[j * n + i] = (float)dpd * ux;", "tx[j * 16 + i] = (float)dpd * ux;"),
+    ("block gradient summed sequentially",
+     "float sx = pairwise_sum(tx, n * n), sy = pairwise_sum(ty, n * n);",
+     "float sx = 0.0f, sy = pairwise_sum(ty, n * n);\n    for (int q = 0; q < n * n; ++q) sx = sx + tx[q];"),
+    ("compensation block index transposed",
+     "const int b = 2 * ((y % 16) / 8) + (x % 16) / 8;", "const int b = 2 * ((x % 16) / 8) + (y % 16) / 8;"),
+    ("block proposal taken on equal SAD",
+     "uint32_t cq = block_sad(ref, cur, W, h, n, X0, Y0, qx, qy);\n            pos_note(ps, qx, qy);\n            if (cq < c)",
+     "uint32_t cq = block_sad(ref, cur, W, h, n, X0, Y0, qx, qy);\n            pos_note(ps, qx, qy);\n            if (cq <= c)"),
+    ("block neighbours use the 16x16 SAD",
+     "uint32_t cn = block_sad(ref, cur, W, h, n, X0, Y0, nx, ny);",
+     "uint32_t cn = block_sad(ref, cur, W, h, 16, X0 - 8 * ((X0 / 8) & 1), Y0 - 8 * ((Y0 / 8) & 1), nx, ny);"),
+]
+
+
+def _run_mutant(tmpdir, i, name, old, new, pins="test_oracle_pins.py"):
     src = open(SRC).read()
     if src.count(old) < 1:
         return name, "anchor not found"
@@ -109,7 +155,7 @@ def _run_mutant(tmpdir, i, name, old, new):
     subprocess.run(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
                     "-o", so_path, c_path, "-lm"], check=True, capture_output=True)
     env = dict(os.environ, SME_ORACLE_LIB=so_path, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x",
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins), "-x",
                         "-q", "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True,
                        text=True, timeout=600)
     return name, ("killed" if r.returncode not in (0, 5) else "survived")
@@ -122,3 +168,12 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
                               [(i, *m) for i, m in enumerate(MUTANTS)]))
     bad = [(n, s) for n, s in results if s != "killed"]
     assert not bad, f"mutants not caught by the pins: {bad}"
+
+
+def test_every_planted_four_vector_mistake_fails_a_pin(tmp_path):
+    workers = min(8, os.cpu_count() or 1)
+    with ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(lambda a: _run_mutant(str(tmp_path), *a, pins="test_oracle_four_mv.py"),
+                              [(100 + i, *m) for i, m in enumerate(MUTANTS4)]))
+    bad = [(n, s) for n, s in results if s != "killed"]
+    assert not bad, f"mutants not caught by the four-vector pins: {bad}"

@@ -215,6 +215,21 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     transparent MBs (known from the classification launch) are finished
  *     straight from global memory, four at a time, and only the other MBs
  *     are staged by TMA; 0 = every MB is staged.
+ *   SME_OPT_FOUR_MV: 1 = four vectors per MB (Sec. 3.2: MPEG-4's four
+ *     vectors per macroblock, the recursive search on 8x8 blocks).  The
+ *     block recursive search stays at MB level (Fig. 1, 16x16 costs) and its
+ *     winner starts the pixel recursive search of each 8x8 block
+ *     b = 2*by + bx; the candidates of an MB are block 1 of the left MB (A),
+ *     block 2 of the MBs above and above-right (B, C) and block 0 of the same
+ *     MB in the previous field (T); boundary MBs give the winner to all four
+ *     blocks, each costed by the alpha mismatches of its quadrant.  Changes
+ *     the layout of the estimate outputs: mv, cost, iters, npos become
+ *     [P][M][4] and disp [P][M][4][2] (block-major inside each MB);
+ *     temporal_in becomes [M][4]; mb_class, sse_mb, sse, pred keep theirs.
+ *     Runs on the pair schedule with every MB staged (whatever
+ *     SME_OPT_SCHEDULE / SME_OPT_PAIR_DIRECT say); seeds are rejected
+ *     (SME_ERR_ARG); sme_estimate_sequence* only.  0 (default) = one vector
+ *     per MB.
  * Returns SME_ERR_ARG for an unknown option or value. */
 enum {
     SME_OPT_SCHEDULE = 1,
@@ -222,7 +237,8 @@ enum {
     SME_OPT_MB_CTAS_PER_SM = 3,
     SME_OPT_SPECULATE = 4,
     SME_OPT_CLUSTER_SIZE = 5,
-    SME_OPT_PAIR_DIRECT = 6
+    SME_OPT_PAIR_DIRECT = 6,
+    SME_OPT_FOUR_MV = 7
 };
 enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2, SME_SCHED_CLUSTER = 3 };
 int sme_set_option(sme_ctx* ctx, int option, int value);

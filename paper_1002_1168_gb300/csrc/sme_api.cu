@@ -56,6 +56,7 @@ struct sme_ctx {
     std::vector<int> sched_host;
     int sched_P = -1;
     int schedule = kSchedAuto, pair_warps = 0, mb_ctas_per_sm = 0, speculate = 1, cluster = 0, pair_direct = 1;
+    int four_mv = 0;
     // cluster schedule: per-CTA item lists and consumer slots (rebuilt when P or the size changes)
     DevBuf cl_items, cl_count, cl_cons;
     int cl_P = -1, cl_C = 0, cl_cap = 0, cl_warps = 0, cl_resident = 0;
@@ -290,8 +291,9 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     if ((rc = ensure(c->desc, sizeof(SeqDesc)))) return rc;
     // The per-MB schedule is the faster one on single sequences (measured on
     // CIF x 30 frames: 130 us vs 193 us per launch); the pair schedule is
-    // chosen only on request.
-    const bool pair = c->schedule == kSchedPair, cluster = c->schedule == kSchedCluster;
+    // chosen only on request, and always in the four-vector mode.
+    if (c->four_mv && seed) return SME_ERR_ARG;
+    const bool pair = c->schedule == kSchedPair || c->four_mv, cluster = !pair && c->schedule == kSchedCluster;
     MapSet maps;
     memset(&maps, 0, sizeof(maps));
     int C = 0;
@@ -366,7 +368,8 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     a.total = (int)total;
     a.fault_ticket = c->fault_ticket;
     a.speculate = c->speculate;
-    a.pair_direct = c->pair_direct;
+    a.pair_direct = c->four_mv ? 0 : c->pair_direct;
+    a.four_mv = c->four_mv;
     a.timeout_ns = c->timeout_ns;
     if (cluster) {
         a.cl_items = (const int*)c->cl_items.p;
@@ -378,9 +381,10 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
         if (launch_me_cluster(c->m, a, C, c->cl_warps, helpers, c->stream) != cudaSuccess) return SME_ERR_CUDA;
     } else if (pair) {
         int nw = c->pair_warps > 0 ? c->pair_warps : std::min(kPairWarpsMax, g.MBH);
-        while (nw > 1 && me_pair_smem_bytes(c->m.S, nw, g.MBW) > (size_t)c->smem_optin) --nw;
+        while (nw > 1 && me_pair_smem_bytes(c->m.S, nw, g.MBW, c->four_mv != 0) > (size_t)c->smem_optin) --nw;
         int per_sm = 0;
-        if (me_pair_occupancy(c->m.S, nw, g.MBW, a.pair_direct != 0, &per_sm) != cudaSuccess || per_sm < 1)
+        if (me_pair_occupancy(c->m.S, nw, g.MBW, a.pair_direct != 0, a.four_mv != 0, &per_sm) != cudaSuccess ||
+            per_sm < 1)
             return SME_ERR_CUDA;
         const int grid = std::max(1, std::min(c->num_sms * per_sm, P));
         if (launch_me_pair(c->m, a, &maps, nw, grid, c->stream) != cudaSuccess) return SME_ERR_CUDA;
@@ -572,10 +576,11 @@ int sme_estimate_sequence_host(sme_ctx* c, const uint8_t* luma, const uint8_t* a
     const int rd = c->prm.ref_distance;
     if (n_frames <= rd) return SME_ERR_ARG;
     const size_t FS = (size_t)g.W * g.H, P = (size_t)(n_frames - rd), PM = P * g.M;
+    const size_t NB = c->four_mv ? 4 : 1;  // vectors per MB
     const cudaStream_t s = c->stream;
     int rc;
     if ((rc = ensure(c->h_luma, FS * n_frames)) || (rc = ensure(c->h_alpha, FS * n_frames)) ||
-        (rc = ensure(c->h_mv, PM * sizeof(sme_mv))))
+        (rc = ensure(c->h_mv, NB * PM * sizeof(sme_mv))))
         return rc;
     if (cudaMemcpyAsync(c->h_luma.p, luma, FS * n_frames, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(c->h_alpha.p, alpha, FS * n_frames, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -583,8 +588,8 @@ int sme_estimate_sequence_host(sme_ctx* c, const uint8_t* luma, const uint8_t* a
     const sme_mv* dtmp = nullptr;
     const float* dseed = nullptr;
     if (temporal_in) {
-        if ((rc = ensure(c->h_tmp, g.M * sizeof(sme_mv)))) return rc;
-        if (cudaMemcpyAsync(c->h_tmp.p, temporal_in, g.M * sizeof(sme_mv), cudaMemcpyHostToDevice, s))
+        if ((rc = ensure(c->h_tmp, NB * g.M * sizeof(sme_mv)))) return rc;
+        if (cudaMemcpyAsync(c->h_tmp.p, temporal_in, NB * g.M * sizeof(sme_mv), cudaMemcpyHostToDevice, s))
             return SME_ERR_CUDA;
         dtmp = (const sme_mv*)c->h_tmp.p;
     }
@@ -602,10 +607,10 @@ int sme_estimate_sequence_host(sme_ctx* c, const uint8_t* luma, const uint8_t* a
         size_t bytes;
         void** dev;
     } opts[] = {
-        {out->cost, &c->h_cost, PM * 4, (void**)&d.cost},
-        {out->disp, &c->h_disp, PM * 8, (void**)&d.disp},
-        {out->iters, &c->h_iters, PM, (void**)&d.iters},
-        {out->npos, &c->h_npos, PM, (void**)&d.npos},
+        {out->cost, &c->h_cost, NB * PM * 4, (void**)&d.cost},
+        {out->disp, &c->h_disp, NB * PM * 8, (void**)&d.disp},
+        {out->iters, &c->h_iters, NB * PM, (void**)&d.iters},
+        {out->npos, &c->h_npos, NB * PM, (void**)&d.npos},
         {out->mb_class, &c->h_cls, PM, (void**)&d.mb_class},
         {out->sse_mb, &c->h_ssemb, PM * 4, (void**)&d.sse_mb},
         {out->sse, &c->h_sse, P * 8, (void**)&d.sse},
@@ -618,7 +623,7 @@ int sme_estimate_sequence_host(sme_ctx* c, const uint8_t* luma, const uint8_t* a
     }
     rc = run_sequence(c, (const uint8_t*)c->h_luma.p, (const uint8_t*)c->h_alpha.p, n_frames, dtmp, dseed, &d);
     if (rc) return rc;
-    if (cudaMemcpyAsync(out->mv, d.mv, PM * sizeof(sme_mv), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (cudaMemcpyAsync(out->mv, d.mv, NB * PM * sizeof(sme_mv), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SME_ERR_CUDA;
     for (Opt& o : opts)
         if (o.host && cudaMemcpyAsync(o.host, *o.dev, o.bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -654,7 +659,7 @@ int sme_set_current(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha)
 
 int sme_estimate(sme_ctx* c, const sme_outputs* out)
 {
-    if (!c) return SME_ERR_ARG;
+    if (!c || c->four_mv) return SME_ERR_ARG;
     if (!c->have_ref || !c->have_cur) return SME_ERR_STATE;
     const Geom& g = c->g;
     int rc;
@@ -830,6 +835,10 @@ int sme_set_option(sme_ctx* c, int option, int value)
         if (value != 0 && value != 1) return SME_ERR_ARG;
         c->pair_direct = value;
         return SME_OK;
+    case SME_OPT_FOUR_MV:
+        if (value != 0 && value != 1) return SME_ERR_ARG;
+        c->four_mv = value;
+        return SME_OK;
     default:
         return SME_ERR_ARG;
     }
@@ -854,6 +863,7 @@ int sme_get_option(sme_ctx* c, int option, int* value)
     case SME_OPT_SPECULATE: *value = c->speculate; return SME_OK;
     case SME_OPT_CLUSTER_SIZE: *value = c->cluster; return SME_OK;
     case SME_OPT_PAIR_DIRECT: *value = c->pair_direct; return SME_OK;
+    case SME_OPT_FOUR_MV: *value = c->four_mv; return SME_OK;
     default: return SME_ERR_ARG;
     }
 }
@@ -988,7 +998,7 @@ int batch_enqueue(sme_batch* b, cudaStream_t s)
         int nw = b->cfg.pair_warps > 0 ? b->cfg.pair_warps : kPairWarpsMax;
         while (nw > 1 && me_pair_smem_bytes(b->m.S, nw, b->mbw_max) > (size_t)b->smem_optin) --nw;
         int per_sm = 0;
-        if (me_pair_occupancy(b->m.S, nw, b->mbw_max, a.pair_direct != 0, &per_sm) != cudaSuccess || per_sm < 1)
+        if (me_pair_occupancy(b->m.S, nw, b->mbw_max, a.pair_direct != 0, false, &per_sm) != cudaSuccess || per_sm < 1)
             return SME_ERR_CUDA;
         const int grid = std::max(1, std::min(b->num_sms * per_sm, b->total_units));
         MapSet unused;

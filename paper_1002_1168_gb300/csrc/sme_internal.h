@@ -108,6 +108,7 @@ struct MeArgs {
     int fault_ticket;
     int speculate;
     int pair_direct;          // per-pair schedule: transparent MBs skip the TMA staging
+    int four_mv;              // per-pair schedule: four vectors per MB (8x8 blocks), outputs [P][M][4]
     long long timeout_ns;
     // cluster schedule (one sequence per cluster)
     const int* cl_items;      // [cluster][cl_cap] global MB ids, each CTA's list in wavefront order
@@ -145,8 +146,8 @@ cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s
 // `maps` points to 4 CUtensorMaps (128-byte aligned): luma window box, current
 // block box, packed-alpha reference strip, packed-alpha current BAB.
 cudaError_t launch_me_pair(const Method& m, const MeArgs& a, const void* maps, int nwarps, int grid, cudaStream_t s);
-cudaError_t me_pair_occupancy(int S, int nwarps, int mbw_max, bool direct, int* blocks_per_sm);
-size_t me_pair_smem_bytes(int S, int nwarps, int mbw_max);
+cudaError_t me_pair_occupancy(int S, int nwarps, int mbw_max, bool direct, bool four_mv, int* blocks_per_sm);
+size_t me_pair_smem_bytes(int S, int nwarps, int mbw_max, bool four_mv = false);
 // Boxes (elements wide, rows high) of the four TMA copies of the per-pair
 // kernel: luma window, current block, packed-alpha reference strip (u32),
 // packed-alpha current BAB (u32).

@@ -1455,7 +1455,7 @@ struct PairLayout {
     int rows_off, prog_off, unit_off, total;
 };
 
-__host__ __device__ __forceinline__ PairLayout pair_layout(int S, int nw, int mbw_max)
+__host__ __device__ __forceinline__ PairLayout pair_layout(int S, int nw, int mbw_max, bool four_mv = false)
 {
     PairLayout L;
     L.o_ref = 0;
@@ -1464,7 +1464,7 @@ __host__ __device__ __forceinline__ PairLayout pair_layout(int S, int nw, int mb
     L.o_acur = L.o_aref + ceil128(aref_words(S) * 4 * win_rows(S));
     L.buf_bytes = L.o_acur + ceil128(kAcurWords * 4 * 16);
     L.log_off = 2 * L.buf_bytes;
-    L.bar_off = L.log_off + ceil16(kMaxLog * 4);
+    L.bar_off = L.log_off + ceil16(kMaxLog * 4 * (four_mv ? 4 : 1));  // one log per 8x8 block in that mode
     L.cls_off = L.bar_off + 16;
     L.warp_bytes = ceil128(L.cls_off + ceil16(mbw_max));
     L.R = nw + 1;
@@ -1711,12 +1711,283 @@ __device__ __forceinline__ void transparent_run(const SeqDesc* sd, const MeArgs&
     __syncwarp();
 }
 
+
+// ===================================================== four vectors per MB ==
+// Sec. 3.2 with 8x8 blocks (MPEG-4's four vectors per MB).  Lane l holds the
+// 8 pixels of MB row l>>1, columns 8*(l&1)..+7, which lie in block
+// b = 2*((l>>1) >= 8) + (l&1); the 8 lanes of a block differ in bits 1-3 of l
+// (bit 1-3 = the row inside the block), so block sums are xor shuffles over
+// bits 1, 2, 3 and every lane of the block holds the same block state.
+__device__ __forceinline__ int blk_of(int lane) { return ((lane >> 4) << 1) | (lane & 1); }
+
+__device__ __forceinline__ unsigned blk_sum(unsigned v)
+{
+    v += __shfl_xor_sync(kFull, v, 2);
+    v += __shfl_xor_sync(kFull, v, 4);
+    v += __shfl_xor_sync(kFull, v, 8);
+    return v;
+}
+
+// Eq. 3 sums over the block's 64 pixels: the lane's 8 terms pairwise, then
+// rows pairwise (xor 2, 4, 8): the contiguous pairwise tree in block raster
+// order (FP32 addition is commutative, so both lanes of a pair agree).
+__device__ __forceinline__ void blk_grad_sums(const P8& r, const P8& c, const float (&ux)[8], const float (&uy)[8],
+                                              float& sx, float& sy)
+{
+    float tx[8], ty[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float dpd = (float)(byte_of(r, k) - byte_of(c, k));
+        tx[k] = __fmul_rn(dpd, ux[k]);
+        ty[k] = __fmul_rn(dpd, uy[k]);
+    }
+    float a = __fadd_rn(__fadd_rn(__fadd_rn(tx[0], tx[1]), __fadd_rn(tx[2], tx[3])),
+                        __fadd_rn(__fadd_rn(tx[4], tx[5]), __fadd_rn(tx[6], tx[7])));
+    float b = __fadd_rn(__fadd_rn(__fadd_rn(ty[0], ty[1]), __fadd_rn(ty[2], ty[3])),
+                        __fadd_rn(__fadd_rn(ty[4], ty[5]), __fadd_rn(ty[6], ty[7])));
+#pragma unroll
+    for (int o = 2; o <= 8; o <<= 1) {
+        a = __fadd_rn(a, __shfl_xor_sync(kFull, a, o));
+        b = __fadd_rn(b, __shfl_xor_sync(kFull, b, o));
+    }
+    sx = a;
+    sy = b;
+}
+
+// The state of the lane's block.
+struct Blk4 {
+    int dx, dy, iters, nlog;
+    unsigned cost;
+    float lastx, lasty;
+    P8 r8;
+    bool done;
+};
+
+// Pixel recursive search of the four blocks at once, each from the MB winner
+// (already in s), in the order of prs_run: proposal if strictly lower, else
+// the first strict minimum of the eight clamped neighbours, else stop; at
+// most K steps.  Positions go to the block's own log (blog) from its first
+// lane.  Control flow is uniform over the warp; blocks that have stopped
+// compute along and discard.
+__device__ __forceinline__ void prs_blocks(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
+                                           const P8& c8, const float (&ux)[8], const float (&uy)[8], int nxb, int nyb,
+                                           const VRange& V, Blk4& s, int* blog, int lane)
+{
+    const int h = m.h;
+    const bool first = (lane & 14) == 0;
+    for (int it = 0; it < m.K; ++it) {
+        if (!__any_sync(kFull, !s.done)) break;
+        float sx, sy;
+        blk_grad_sums(s.r8, c8, ux, uy, sx, sy);
+        const float ux_ = update_of(sx, nxb, m.eps), uy_ = update_of(sy, nyb, m.eps);
+        const int qx = clampi(s.dx + (int)roundf(__fmul_rn((float)h, ux_)), V.lox, V.hix);
+        const int qy = clampi(s.dy + (int)roundf(__fmul_rn((float)h, uy_)), V.loy, V.hiy);
+        const bool qmove = qx != s.dx || qy != s.dy;
+        const P8 q8 = ref8(win, pitch, lx, ly, qx, qy, h);
+        const unsigned cq = blk_sum(sad8(q8, c8));
+        bool moved = false, need_nb = false;
+        if (!s.done) {
+            ++s.iters;
+            s.lastx = ux_;
+            s.lasty = uy_;
+            if (qmove) {
+                if (first) blog[s.nlog] = pack_mv(qx, qy);
+                ++s.nlog;
+                moved = cq < s.cost;
+            }
+            need_nb = !moved;
+        }
+        if (moved) {
+            s.dx = qx;
+            s.dy = qy;
+            s.cost = cq;
+            s.r8 = q8;
+        }
+        if (__any_sync(kFull, need_nb)) {
+            unsigned bc = s.cost;
+            int bx = s.dx, by = s.dy;
+            P8 b8 = s.r8;
+#pragma unroll 1
+            for (int n = 1; n < 9; ++n) {
+                const int e = n < 5 ? n - 1 : n;  // 3x3 raster without its centre
+                const int ex = clampi(s.dx + e % 3 - 1, V.lox, V.hix), ey = clampi(s.dy + e / 3 - 1, V.loy, V.hiy);
+                const P8 e8 = ref8(win, pitch, lx, ly, ex, ey, h);
+                const unsigned ce = blk_sum(sad8(e8, c8));
+                if (need_nb && (ex != s.dx || ey != s.dy)) {
+                    if (first) blog[s.nlog] = pack_mv(ex, ey);
+                    ++s.nlog;
+                    if (ce < bc) {
+                        bc = ce;
+                        bx = ex;
+                        by = ey;
+                        b8 = e8;
+                    }
+                }
+            }
+            if (need_nb) {
+                if (bc < s.cost) {
+                    s.dx = bx;
+                    s.dy = by;
+                    s.cost = bc;
+                    s.r8 = b8;
+                } else {
+                    s.done = true;
+                }
+            }
+        }
+    }
+}
+
+// Alpha mismatches of the lane's quadrant at the full-pel part of key (the
+// boundary cost of one block), from the staged BABs as in shape_costs_smem.
+__device__ __forceinline__ unsigned shape_quadrant_smem(const uint32_t* acur, const uint32_t* aref, int arw, int S,
+                                                        int X0, int key, int h, int lane)
+{
+    const int r = lane & 15;
+    const unsigned cb = (acur[r * kAcurWords + (X0 >> 5) - ((X0 >> 5) & ~3)] >> (X0 & 31)) & 0xffffu;
+    const int xw0 = ((X0 - S) >> 5) & ~3;
+    const int fdx = mv_x(key) / h, fdy = mv_y(key) / h;  // trunc toward zero
+    const int xr = X0 + fdx, wr = (xr >> 5) - xw0;
+    const uint32_t* row = aref + (r + fdy + S) * arw;
+    const unsigned diff = (cb ^ __funnelshift_r(row[wr], row[wr + 1], xr & 31)) & 0xffffu;
+    unsigned lo = __popc(diff & 0xffu), hi = __popc(diff >> 8);
+    // sums over rows 0-7 (lanes 0-7) and 8-15 (lanes 8-15)
+#pragma unroll
+    for (int o = 1; o <= 4; o <<= 1) {
+        lo += __shfl_xor_sync(kFull, lo, o);
+        hi += __shfl_xor_sync(kFull, hi, o);
+    }
+    const int src = (lane >> 4) << 3;  // lane 0: rows 0-7, lane 8: rows 8-15
+    const unsigned qlo = __shfl_sync(kFull, lo, src), qhi = __shfl_sync(kFull, hi, src);
+    return (lane & 1) ? qhi : qlo;
+}
+
+// Distinct positions of the lane's block: its log (the MB candidates, then
+// its own PRS positions), counted by the block's 8 lanes.
+__device__ __forceinline__ unsigned blk_distinct(const int* blog, int n, int lane)
+{
+    unsigned first = 0;
+    for (int e = (lane >> 1) & 7; e < n; e += 8) {
+        const int kk = blog[e];
+        bool f = true;
+        for (int j = 0; j < e; ++j)
+            if (blog[j] == kk) {
+                f = false;
+                break;
+            }
+        first += f;
+    }
+    return blk_sum(first);
+}
+
+// Outputs of one MB in the four-vector mode ([M][4] arrays): the lane's block
+// state s, the MB's SSE from every lane's 8 pixels at its block's vector.
+__device__ __forceinline__ void finish_mb4(const SeqDesc* sd, int idx, int k, int cls, const Blk4& s, const P8& c8,
+                                           const int* blog, int lane, size_t FS, int W, int y, int x0)
+{
+    __syncwarp();
+    const unsigned npos = blk_distinct(blog, s.nlog, lane);
+    if ((lane & 14) == 0) {
+        const int o = 4 * idx + blk_of(lane);
+        sd->mv[o] = sme_mv{(int16_t)s.dx, (int16_t)s.dy};
+        if (sd->cost) sd->cost[o] = s.cost;
+        if (sd->iters) sd->iters[o] = (uint8_t)s.iters;
+        if (sd->npos) sd->npos[o] = (uint8_t)npos;
+        if (sd->disp) {
+            sd->disp[2 * o] = s.lastx;
+            sd->disp[2 * o + 1] = s.lasty;
+        }
+    }
+    if (lane == 0 && sd->out_cls) sd->out_cls[idx] = (uint8_t)cls;
+    const unsigned e = __reduce_add_sync(kFull, sq8(s.r8, c8));
+    if (lane == 0) {
+        if (sd->sse) atomicAdd(sd->sse + k, (unsigned long long)e);
+        if (sd->sse_mb) sd->sse_mb[idx] = e;
+    }
+    if (sd->pred)
+        *reinterpret_cast<uint2*>(sd->pred + (size_t)k * FS + (size_t)y * W + x0) = make_uint2(s.r8.lo, s.r8.hi);
+    __syncwarp();
+}
+
+// Fig. 1 at MB level (16x16 costs of the candidates A, B, C, T) and, on
+// opaque MBs, the block searches from the winner.  The candidates are in
+// cand[0..4); each block log starts with them.
+__device__ __forceinline__ Blk4 search_mb4(const Method& m, int cls, const uint8_t* win, int pitch, int lx, int ly,
+                                           const P8& c8, const float (&ux)[8], const float (&uy)[8],
+                                           const VRange& V, const int (&cand)[5], const uint32_t* acur,
+                                           const uint32_t* aref, int arw, int S, int X0, int* blog, int lane)
+{
+    const int h = m.h;
+    Blk4 s;
+    s.iters = 0;
+    s.nlog = 4;
+    s.lastx = s.lasty = 0.0f;
+    s.done = false;
+    if (cls == SME_BOUNDARY) {
+        unsigned sc[5];
+        shape_costs_smem(acur, aref, arw, S, X0, cand, 4, h, lane, sc);
+        int best = cand[0];
+        unsigned cost = sc[0];
+#pragma unroll
+        for (int c = 1; c < 4; ++c)
+            if (sc[c] < cost) {
+                cost = sc[c];
+                best = cand[c];
+            }
+        s.dx = mv_x(best);
+        s.dy = mv_y(best);
+        s.cost = shape_quadrant_smem(acur, aref, arw, S, X0, best, h, lane);
+        s.r8 = ref8(win, pitch, lx, ly, s.dx, s.dy, h);
+        return s;
+    }
+    P8 cs8[4];
+    unsigned part[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        cs8[c] = ref8(win, pitch, lx, ly, mv_x(cand[c]), mv_y(cand[c]), h);
+        part[c] = sad8(cs8[c], c8);
+    }
+    unsigned sad[4];
+    warp_sum2(part[0], part[1], sad[0], sad[1]);
+    warp_sum2(part[2], part[3], sad[2], sad[3]);
+    int best = 0;
+    unsigned cost = sad[0];
+#pragma unroll
+    for (int c = 1; c < 4; ++c)
+        if (sad[c] < cost) {
+            cost = sad[c];
+            best = c;
+        }
+    s.r8 = cs8[0];
+    s.dx = mv_x(cand[0]);
+    s.dy = mv_y(cand[0]);
+#pragma unroll
+    for (int c = 1; c < 4; ++c)
+        if (c == best) {
+            s.r8 = cs8[c];
+            s.dx = mv_x(cand[c]);
+            s.dy = mv_y(cand[c]);
+        }
+    s.cost = blk_sum(sad8(s.r8, c8));
+    unsigned cx = 0, cy = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cx += ux[k] != 0.0f;
+        cy += uy[k] != 0.0f;
+    }
+    prs_blocks(m, win, pitch, lx, ly, c8, ux, uy, (int)blk_sum(cx), (int)blk_sum(cy), V, s, blog, lane);
+    return s;
+}
+
 // kDirect: runs of transparent MBs (known from the classification launch)
 // are finished by transparent_run and only the other MBs are staged by TMA;
 // otherwise every MB is staged and classified from its staged BAB.  Two
 // instantiations rather than a runtime switch, so that each keeps only its
-// own code (the kernel is at its register limit).
-template <bool kDirect>
+// own code (the kernel is at its register limit).  kFourMv: four vectors per
+// MB (Sec. 3.2, 8x8 blocks; staged only): A is block 1 of the left MB (the
+// warp's previous MB), B and C block 2 of the MBs above (the row slots hold
+// block 2), T block 0 of the previous pair (the ready words hold block 0).
+template <bool kDirect, bool kFourMv>
 __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArgs a, const __grid_constant__ PairMaps maps0)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -1725,7 +1996,7 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
     const Method m = a.m;
     const int h = m.h, S = m.S, cs = ceil16(S), pitch = win_pitch(S), arw = aref_words(S);
     const unsigned tx = pair_tx_bytes(S);
-    const PairLayout L = pair_layout(S, nw, a.mbw_max);
+    const PairLayout L = pair_layout(S, nw, a.mbw_max, kFourMv);
     uint8_t* wbase = smem + (size_t)wid * L.warp_bytes;
     int* slog = reinterpret_cast<int*>(wbase + L.log_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + L.bar_off);
@@ -1863,9 +2134,22 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
                         rowmv[slot * a.mbw_max + u] = 0;
                         st_release_cta(&prog[slot], v * 1024 + u + 1);
                         if (gid != a.fault_ticket) st_ready(a.ready + gid, tag);
-                        sd->mv[idx] = sme_mv{0, 0};
+                        if (!kFourMv) sd->mv[idx] = sme_mv{0, 0};
                     }
                     akey = 0;
+                    if constexpr (kFourMv) {
+                        Blk4 s4;
+                        s4.dx = s4.dy = s4.iters = s4.nlog = 0;
+                        s4.cost = 0;
+                        s4.lastx = s4.lasty = 0.0f;
+                        s4.done = true;
+                        s4.r8 = ref8(win, pitch, lx, ly, 0, 0, h);
+                        finish_mb4(sd, idx, k, cls, s4, c8, slog, lane, FS, W, y, x0);
+                        cur = nb;
+                        nt = nn;
+                        ++u;
+                        continue;
+                    }
                     MbResult r;
                     r.dx = r.dy = r.iters = r.nlog = 0;
                     r.cost = 0;
@@ -1889,7 +2173,7 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
                                 ok = wait_ready(a.ready + gid - M, epoch, a.status, a.timeout_ns, val);
                             key = (int)val;
                         } else if (sd->temporal_in) {
-                            key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
+                            key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + (kFourMv ? 4 * mb : mb)));
                         }
                     }
                     if (__any_sync(kFull, !ok)) {
@@ -1902,11 +2186,34 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
                     if (lane == 1 && v > 0) key = rowmv[pslot * a.mbw_max + u];
                     if (lane == 2 && v > 0 && u + 1 < MBW) key = rowmv[pslot * a.mbw_max + u + 1];
                     if (lane < 4) key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
-                    if (lane == 4 && sd->seed) key = seed_key(sd, idx, h, V);
-                    const int nc = sd->seed ? 5 : 4;
+                    if (!kFourMv && lane == 4 && sd->seed) key = seed_key(sd, idx, h, V);
+                    const int nc = (!kFourMv && sd->seed) ? 5 : 4;
                     int cand[5];
 #pragma unroll
                     for (int c = 0; c < 5; ++c) cand[c] = __shfl_sync(kFull, key, c);
+                    if constexpr (kFourMv) {
+                        // every block's log starts with the MB candidates
+                        if (lane < 16) slog[(lane >> 2) * kMaxLog + (lane & 3)] = cand[lane & 3];
+                        __syncwarp();
+                        int* blog = slog + blk_of(lane) * kMaxLog;
+                        const Blk4 s4 = search_mb4(m, cls, win, pitch, lx, ly, c8, ux, uy, V, cand, acur,
+                                                   reinterpret_cast<const uint32_t*>(buf + L.o_aref), arw, S, X0, blog,
+                                                   lane);
+                        const int kb = pack_mv(s4.dx, s4.dy);
+                        const int k0 = __shfl_sync(kFull, kb, 0), k1 = __shfl_sync(kFull, kb, 1);
+                        const int k2 = __shfl_sync(kFull, kb, 16);
+                        if (lane == 0) {
+                            rowmv[slot * a.mbw_max + u] = k2;
+                            st_release_cta(&prog[slot], v * 1024 + u + 1);
+                            if (gid != a.fault_ticket) st_ready(a.ready + gid, tag | (unsigned)k0);
+                        }
+                        akey = k1;
+                        finish_mb4(sd, idx, k, cls, s4, c8, blog, lane, FS, W, y, x0);
+                        cur = nb;
+                        nt = nn;
+                        ++u;
+                        continue;
+                    }
                     if (lane < nc) slog[lane] = key;
                     MbResult r;
                     if (cls == SME_BOUNDARY) {
@@ -2177,15 +2484,17 @@ void pair_boxes(int S, unsigned (&box)[4][2])
     box[3][1] = 16;
 }
 
-size_t me_pair_smem_bytes(int S, int nwarps, int mbw_max)
+size_t me_pair_smem_bytes(int S, int nwarps, int mbw_max, bool four_mv)
 {
-    return (size_t)pair_layout(S, nwarps, mbw_max).total + 128;  // + alignment slack
+    return (size_t)pair_layout(S, nwarps, mbw_max, four_mv).total + 128;  // + alignment slack
 }
 
-cudaError_t me_pair_occupancy(int S, int nwarps, int mbw_max, bool direct, int* blocks_per_sm)
+cudaError_t me_pair_occupancy(int S, int nwarps, int mbw_max, bool direct, bool four_mv, int* blocks_per_sm)
 {
-    const size_t smem = me_pair_smem_bytes(S, nwarps, mbw_max);
-    const void* fn = direct ? (const void*)me_pair_kernel<true> : (const void*)me_pair_kernel<false>;
+    const size_t smem = me_pair_smem_bytes(S, nwarps, mbw_max, four_mv);
+    const void* fn = four_mv  ? (const void*)me_pair_kernel<false, true>
+                     : direct ? (const void*)me_pair_kernel<true, false>
+                              : (const void*)me_pair_kernel<false, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 32 * nwarps, smem);
@@ -2193,8 +2502,8 @@ cudaError_t me_pair_occupancy(int S, int nwarps, int mbw_max, bool direct, int* 
 
 cudaError_t launch_me_pair(const Method& m, const MeArgs& a, const void* maps, int nwarps, int grid, cudaStream_t s)
 {
-    const size_t smem = me_pair_smem_bytes(m.S, nwarps, a.mbw_max);
-    auto* fn = a.pair_direct ? me_pair_kernel<true> : me_pair_kernel<false>;
+    const size_t smem = me_pair_smem_bytes(m.S, nwarps, a.mbw_max, a.four_mv != 0);
+    auto* fn = a.four_mv ? me_pair_kernel<false, true> : a.pair_direct ? me_pair_kernel<true, false> : me_pair_kernel<false, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};

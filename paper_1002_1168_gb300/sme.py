@@ -19,6 +19,7 @@ SME_TRANSPARENT, SME_OPAQUE, SME_BOUNDARY = 0, 1, 2
 SME_OPT_SCHEDULE, SME_OPT_PAIR_WARPS, SME_OPT_MB_CTAS_PER_SM, SME_OPT_SPECULATE = 1, 2, 3, 4
 SME_OPT_CLUSTER_SIZE = 5
 SME_OPT_PAIR_DIRECT = 6
+SME_OPT_FOUR_MV = 7
 SCHEDULES = {"auto": 0, "mb": 1, "pair": 2, "cluster": 3}
 STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4: "SME_ERR_TIMEOUT",
           5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE", 8: "SME_ERR_SCRATCH"}
@@ -158,7 +159,7 @@ class Estimator:
     """One context of the library bound to the current CUDA device."""
 
     def __init__(self, width, height, search_range=16, subpel=1, theta=2.0, epsilon=1.0,
-                 max_iters=8, ref_distance=1):
+                 max_iters=8, ref_distance=1, four_mv=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -172,6 +173,10 @@ class Estimator:
         h = C.c_void_p()
         _check(lib.sme_create(C.byref(h), C.byref(self.params), self._stream()), "sme_create")
         self._h = h
+        # four vectors per MB (Sec. 3.2, 8x8 blocks): mv/cost/disp/iters/npos gain a block axis of 4
+        self.four_mv = bool(four_mv)
+        if self.four_mv:
+            self.set_option(SME_OPT_FOUR_MV, 1)
 
     # ------------------------------------------------------------ plumbing
     def _stream(self):
@@ -198,8 +203,10 @@ class Estimator:
     def _alloc_outputs(self, P, want, device):
         t = self.torch
         M, H, W = self.M, self.height, self.width
-        shapes = {"mv": ((P, M, 2), t.int16), "cost": ((P, M), t.int32), "disp": ((P, M, 2), t.float32),
-                  "iters": ((P, M), t.uint8), "npos": ((P, M), t.uint8), "mb_class": ((P, M), t.uint8),
+        B = (4,) if getattr(self, "four_mv", False) else ()
+        shapes = {"mv": ((P, M) + B + (2,), t.int16), "cost": ((P, M) + B, t.int32),
+                  "disp": ((P, M) + B + (2,), t.float32), "iters": ((P, M) + B, t.uint8),
+                  "npos": ((P, M) + B, t.uint8), "mb_class": ((P, M), t.uint8),
                   "sse_mb": ((P, M), t.int32), "sse": ((P,), t.int64), "pred": ((P, H, W), t.uint8)}
         out = {}
         for k in OUTPUT_FIELDS:

@@ -1,0 +1,121 @@
+"""GPU four-vector mode (Sec. 3.2: the recursive search on 8x8 blocks, four
+vectors per MB) against the oracle's: block vectors, costs, PRS steps,
+positions, classes and per-pair SSE bit-exact, the FP32 block updates
+bitwise; prediction images equal; through the device and host-buffer entry
+points, full- and half-pel, edge MBs, a temporal field, the degenerate
+alpha planes."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1002_1168_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sme():
+    from paper_1002_1168_gb300 import build as cuda_build
+    from paper_1002_1168_gb300 import sme as m
+
+    cuda_build.build()
+    return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+WANT = ("cost", "disp", "iters", "npos", "mb_class", "sse_mb", "sse", "pred")
+
+
+def run_both(sme, luma, alpha, S=16, h=2, K=8, rd=1, temporal4=None, warps=0, host=False):
+    F, H, W = luma.shape
+    est = sme.Estimator(W, H, search_range=S, subpel=h, max_iters=K, ref_distance=rd, four_mv=True)
+    if warps:
+        est.set_option(sme.SME_OPT_PAIR_WARPS, warps)
+    tmp = None if temporal4 is None else temporal4.astype(np.int16)
+    if host:
+        g = est.estimate_sequence_host(torch.from_numpy(luma), torch.from_numpy(alpha),
+                                       temporal_in=None if tmp is None else torch.from_numpy(tmp), want=WANT)
+    else:
+        g = est.estimate_sequence(cuda(luma), cuda(alpha), temporal_in=None if tmp is None else cuda(tmp), want=WANT)
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    est.close()
+    o = O.estimate_sequence4(O.OracleParams(W, H, S, h, max_iters=K), luma, alpha, ref_distance=rd,
+                             temporal_in4=temporal4, want_pred=True)
+    return g, o
+
+
+def assert_parity(g, o, luma, rd=1):
+    assert np.array_equal(g["mb_class"], o["mbclass"]), "MB classes"
+    assert np.array_equal(g["mv"], o["mv"]), "block vectors"
+    assert np.array_equal(g["cost"].view(np.uint32), o["cost"]), "block costs"
+    assert np.array_equal(g["iters"], o["iters"]), "block PRS steps"
+    assert np.array_equal(g["npos"], o["npos"]), "block positions"
+    assert np.array_equal(g["disp"].view(np.uint32), o["disp"].view(np.uint32)), "FP32 block updates (bitwise)"
+    assert np.array_equal(g["sse"].view(np.uint64), o["sse"]), "SSE"
+    assert np.array_equal(g["pred"], o["pred"]), "prediction"
+    H, W = luma.shape[1:]
+    for k in range(o["mv"].shape[0]):
+        e = (luma[k + rd].astype(np.int64) - o["pred"][k]) ** 2
+        per = e.reshape(H // 16, 16, W // 16, 16).sum(axis=(1, 3)).ravel()
+        assert np.array_equal(g["sse_mb"][k].view(np.uint32).astype(np.int64), per), "per-MB SSE"
+
+
+@pytest.mark.parametrize("h", [1, 2])
+def test_qcif_pair(sme, h):
+    seq = synth.qcif_pair()
+    g, o = run_both(sme, seq.luma, seq.alpha, S=16, h=h)
+    assert_parity(g, o, seq.luma)
+    assert (o["mv"][..., 0, :] != o["mv"][..., 3, :]).any()  # blocks do differ
+
+
+@pytest.mark.parametrize("warps", [0, 2, 5])
+def test_cif_sequence_halfpel(sme, warps):
+    seq = synth.cif_sequence(frames=6)
+    g, o = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, warps=warps)
+    assert_parity(g, o, seq.luma)
+
+
+def test_host_buffers(sme):
+    seq = synth.cif_sequence(frames=3)
+    g, o = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, host=True)
+    assert_parity(g, o, seq.luma)
+
+
+def test_temporal_field_and_ref_distance_two(sme):
+    seq = synth.cif_sequence(frames=5)
+    rng = np.random.default_rng(3)
+    tmp = rng.integers(-12, 13, (396, 4, 2))
+    g, o = run_both(sme, seq.luma, seq.alpha[0], S=8, h=2, rd=2, temporal4=tmp)
+    assert_parity(g, o, seq.luma, rd=2)
+
+
+@pytest.mark.parametrize("W,H,F,S,h,K", [(48, 48, 3, 4, 2, 8), (64, 32, 4, 7, 1, 16), (96, 64, 3, 32, 2, 3)])
+def test_edges_and_parameters_random_content(sme, W, H, F, S, h, K):
+    luma, alpha = synth.random_frames(W, H, F, seed=W * H + S)
+    g, o = run_both(sme, luma, alpha, S=S, h=h, K=K)
+    assert_parity(g, o, luma)
+
+
+@pytest.mark.parametrize("fill", [0, 255])
+def test_all_transparent_or_all_opaque(sme, fill):
+    seq = synth.cif_sequence(frames=3)
+    alpha = np.full_like(seq.alpha[0], fill)
+    g, o = run_both(sme, seq.luma, alpha, S=16, h=2)
+    assert_parity(g, o, seq.luma)
+    if fill == 0:
+        assert not g["mv"].any() and not g["npos"].any()
+
+
+def test_seeds_are_rejected(sme):
+    from paper_1002_1168_gb300.sme import SmeError
+
+    seq = synth.cif_sequence(frames=2)
+    est = sme.Estimator(352, 288, search_range=16, subpel=2, four_mv=True)
+    with pytest.raises(SmeError):
+        est.estimate_sequence(cuda(seq.luma), cuda(seq.alpha[0]),
+                              seed=cuda(np.zeros((1, 396, 2), np.float32)))
+    est.close()

@@ -38,7 +38,7 @@ def build_oracle(force: bool = False) -> str:
 class _Params(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("search_range", C.c_int),
                 ("subpel", C.c_int), ("theta", C.c_float), ("epsilon", C.c_float),
-                ("max_iters", C.c_int)]
+                ("max_iters", C.c_int), ("boundary_t_texture", C.c_int)]
 
 
 @dataclass
@@ -50,10 +50,11 @@ class OracleParams:
     theta: float = 2.0
     epsilon: float = 1.0
     max_iters: int = 8
+    boundary_t_texture: int = 0  # Sec. 3.1 variant: boundary T judged by texture (four-vector mode ignores it)
 
     def c(self) -> _Params:
         return _Params(self.width, self.height, self.search_range, self.subpel,
-                       self.theta, self.epsilon, self.max_iters)
+                       self.theta, self.epsilon, self.max_iters, self.boundary_t_texture)
 
     @property
     def mbs(self) -> int:

@@ -55,6 +55,7 @@ typedef struct {
     float theta;        /* Theta of Eq. 4 */
     float epsilon;      /* convergence factor of Eq. 2 */
     int max_iters;      /* cap on PRS iterations */
+    int boundary_t_texture; /* variant of Sec. 3.1 (see orc_estimate_pair); 0 = Fig. 1 */
 } orc_params;
 
 enum { ORC_TRANSPARENT = 0, ORC_OPAQUE = 1, ORC_BOUNDARY = 2 };
@@ -333,6 +334,20 @@ int orc_estimate_pair(const orc_params* P, const uint8_t* ref, const uint8_t* cu
                 costs[k] = c;
                 pos_note(&ps, cx[k], cy[k]);
                 if (best < 0 || c < bc) { best = k; bc = c; }
+            }
+            if (cls == ORC_BOUNDARY && P->boundary_t_texture) {
+                /* Sec. 3.1's prose for boundary MBs: the spatial candidates are
+                 * judged by shape, the temporal one by texture.  The winner of
+                 * the others by shape (first strict minimum) and T are compared
+                 * by texture SAD; T replaces it only if strictly lower.  The
+                 * cost stays the shape cost of the vector kept. */
+                int sb = -1;
+                for (int q = 0; q < nc; ++q)
+                    if (q != 3 && (sb < 0 || costs[q] < costs[sb])) sb = q;
+                uint32_t tex_s = orc_texture_sad(ref, cur, W, h, X0, Y0, cx[sb], cy[sb]);
+                uint32_t tex_t = orc_texture_sad(ref, cur, W, h, X0, Y0, cx[3], cy[3]);
+                best = tex_t < tex_s ? 3 : sb;
+                bc = costs[best];
             }
             int dx = cx[best], dy = cy[best];
             uint32_t c = bc;

@@ -93,6 +93,15 @@ MUTANTS = [
      "return 10.0 * log10(255.0 * (double)W * (double)H / (double)sse);"),
     ("distinct positions count repeats",
      "if (s->pos[k] == key) return;", "if (s->pos[k] == key) break;"),
+    ("boundary texture-T variant ignored",
+     "if (cls == ORC_BOUNDARY && P->boundary_t_texture) {", "if (0) {"),
+    ("boundary texture-T variant: T wins ties",
+     "best = tex_t < tex_s ? 3 : sb;", "best = tex_t <= tex_s ? 3 : sb;"),
+    ("boundary texture-T variant: T in the shape competition",
+     "if (q != 3 && (sb < 0 || costs[q] < costs[sb])) sb = q;", "if (sb < 0 || costs[q] < costs[sb]) sb = q;"),
+    ("boundary texture-T variant: cost is the texture SAD",
+     "best = tex_t < tex_s ? 3 : sb;\n                bc = costs[best];",
+     "best = tex_t < tex_s ? 3 : sb;\n                bc = best == 3 ? tex_t : tex_s;"),
 ]
 
 

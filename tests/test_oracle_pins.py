@@ -472,3 +472,59 @@ def test_seed_rounds_half_away_from_zero():
     seeded = _middle_mb(ref, cur, 2, seed_px=(-0.2, 0.0))
     for k in plain:
         assert np.array_equal(plain[k], seeded[k]), k
+
+
+# ------------------------------- Sec. 3.1 variant: boundary T judged by texture --
+def _boundary_case(move_texture, move_alpha, flat=False):
+    """48 x 48 frames, the middle MB a boundary MB (left half inside), every
+    other MB transparent, so A = B = C = (0, 0); T = (-2, 0) is given.  The
+    texture and/or the alpha move by +2 px (the displacement that matches
+    them is -2)."""
+    luma, _ = synth.translated_pair(48, 48, (2, 0) if move_texture else (0, 0), seed=4)
+    if flat:
+        luma = np.full_like(luma, 90)
+    a = np.zeros((2, 48, 48), np.uint8)
+    a[0, 16:32, 16:24] = 255
+    a[1, 16:32, 16 + (2 if move_alpha else 0):24 + (2 if move_alpha else 0)] = 255
+    tmp = np.zeros((9, 2), np.int16)
+    tmp[4] = (-2, 0)
+    return luma, a, tmp
+
+
+def _run_boundary(variant, **kw):
+    luma, a, tmp = _boundary_case(**kw)
+    p = O.OracleParams(48, 48, 16, 1, boundary_t_texture=variant)
+    o = O.estimate_pair(p, luma[0], luma[1], a[0], a[1], temporal=tmp)
+    assert o["mbclass"][4] == 2
+    return o, luma, a
+
+
+def test_boundary_temporal_by_texture_takes_t_when_texture_says_so():
+    """Texture moves, alpha does not: by shape (Fig. 1) A = (0,0) wins with 0
+    mismatches; with the variant, the spatial winner (0,0) and T = (-2,0) are
+    compared by texture SAD, T matches exactly and is kept, its cost being its
+    shape cost (16 rows x 4 columns of mismatches, 2 on each side = 64)."""
+    o, luma, a = _run_boundary(0, move_texture=True, move_alpha=False)
+    assert tuple(o["mv"][4]) == (0, 0) and o["cost"][4] == 0
+    o, luma, a = _run_boundary(1, move_texture=True, move_alpha=False)
+    assert tuple(o["mv"][4]) == (-2, 0)
+    assert o["cost"][4] == O.shape_sad(a[0], a[1], 1, 16, 16, -2, 0) == 64
+    assert O.texture_sad(luma[0], luma[1], 1, 16, 16, -2, 0) == 0
+    assert o["iters"][4] == 0 and o["npos"][4] == 2
+
+
+def test_boundary_temporal_by_texture_not_by_shape():
+    """Alpha moves, texture does not: by shape T = (-2,0) wins (0 mismatches
+    against 64); with the variant T must beat the spatial winner (0,0) on
+    texture, where (0,0) is exact, so (0,0) stays."""
+    o, _, a = _run_boundary(0, move_texture=False, move_alpha=True)
+    assert tuple(o["mv"][4]) == (-2, 0) and o["cost"][4] == 0
+    o, _, a = _run_boundary(1, move_texture=False, move_alpha=True)
+    assert tuple(o["mv"][4]) == (0, 0)
+    assert o["cost"][4] == O.shape_sad(a[0], a[1], 1, 16, 16, 0, 0) == 64
+
+
+def test_boundary_temporal_by_texture_tie_keeps_the_spatial_winner():
+    """Flat luma: both texture SADs are 0, T is not strictly lower."""
+    o, _, _ = _run_boundary(1, move_texture=True, move_alpha=False, flat=True)
+    assert tuple(o["mv"][4]) == (0, 0) and o["cost"][4] == 0

@@ -227,9 +227,15 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     [P][M][4] and disp [P][M][4][2] (block-major inside each MB);
  *     temporal_in becomes [M][4]; mb_class, sse_mb, sse, pred keep theirs.
  *     Runs on the pair schedule with every MB staged (whatever
- *     SME_OPT_SCHEDULE / SME_OPT_PAIR_DIRECT say); seeds are rejected
- *     (SME_ERR_ARG); sme_estimate_sequence* only.  0 (default) = one vector
- *     per MB.
+ *     SME_OPT_SCHEDULE / SME_OPT_PAIR_DIRECT say); seeds and
+ *     SME_OPT_BOUNDARY_T_TEXTURE are rejected (SME_ERR_ARG);
+ *     sme_estimate_sequence* only.  0 (default) = one vector per MB.
+ *   SME_OPT_BOUNDARY_T_TEXTURE: 1 = Sec. 3.1's prose for boundary MBs: the
+ *     spatial candidates (and a seed) are judged by shape, the temporal one
+ *     by texture -- the first strict minimum of the others by alpha
+ *     mismatches is compared with T by 16x16 texture SAD and T is kept only
+ *     if strictly lower; the reported cost is the alpha mismatch count of the
+ *     vector kept.  0 (default) = Fig. 1: all candidates by shape.
  * Returns SME_ERR_ARG for an unknown option or value. */
 enum {
     SME_OPT_SCHEDULE = 1,
@@ -238,7 +244,8 @@ enum {
     SME_OPT_SPECULATE = 4,
     SME_OPT_CLUSTER_SIZE = 5,
     SME_OPT_PAIR_DIRECT = 6,
-    SME_OPT_FOUR_MV = 7
+    SME_OPT_FOUR_MV = 7,
+    SME_OPT_BOUNDARY_T_TEXTURE = 8
 };
 enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2, SME_SCHED_CLUSTER = 3 };
 int sme_set_option(sme_ctx* ctx, int option, int value);

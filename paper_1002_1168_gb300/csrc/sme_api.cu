@@ -137,6 +137,7 @@ Method make_method(const sme_params& p)
     m.K = p.max_iters;
     m.theta = p.theta;
     m.eps = p.epsilon;
+    m.tt = 0;
     return m;
 }
 
@@ -292,7 +293,7 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     // The per-MB schedule is the faster one on single sequences (measured on
     // CIF x 30 frames: 130 us vs 193 us per launch); the pair schedule is
     // chosen only on request, and always in the four-vector mode.
-    if (c->four_mv && seed) return SME_ERR_ARG;
+    if (c->four_mv && (seed || c->m.tt)) return SME_ERR_ARG;
     const bool pair = c->schedule == kSchedPair || c->four_mv, cluster = !pair && c->schedule == kSchedCluster;
     MapSet maps;
     memset(&maps, 0, sizeof(maps));
@@ -839,6 +840,10 @@ int sme_set_option(sme_ctx* c, int option, int value)
         if (value != 0 && value != 1) return SME_ERR_ARG;
         c->four_mv = value;
         return SME_OK;
+    case SME_OPT_BOUNDARY_T_TEXTURE:
+        if (value != 0 && value != 1) return SME_ERR_ARG;
+        c->m.tt = value;
+        return SME_OK;
     default:
         return SME_ERR_ARG;
     }
@@ -864,6 +869,7 @@ int sme_get_option(sme_ctx* c, int option, int* value)
     case SME_OPT_CLUSTER_SIZE: *value = c->cluster; return SME_OK;
     case SME_OPT_PAIR_DIRECT: *value = c->pair_direct; return SME_OK;
     case SME_OPT_FOUR_MV: *value = c->four_mv; return SME_OK;
+    case SME_OPT_BOUNDARY_T_TEXTURE: *value = c->m.tt; return SME_OK;
     default: return SME_ERR_ARG;
     }
 }

@@ -40,6 +40,7 @@ struct DevStatus {
 struct Method {
     int S, h, K;
     float theta, eps;
+    int tt;  // boundary MBs: T judged by texture against the shape winner of the others (Sec. 3.1 variant)
 };
 
 // Per-frame geometry.

@@ -914,6 +914,29 @@ __device__ __forceinline__ MbResult search_mb(const Method& m, int cls, const ui
     return res;
 }
 
+// Sec. 3.1 variant for a boundary MB whose candidates carry shape costs:
+// the first strict minimum over the candidates other than T (index 3) is
+// compared with T by 16x16 texture SAD; T is kept only if strictly lower.
+// bi/cost become the index kept and its shape cost.
+__device__ __forceinline__ void boundary_t_by_texture(const uint8_t* win, int pitch, int lx, int ly, const P8& c8,
+                                                      const int (&cand)[5], const unsigned (&scost)[5], int nc, int h,
+                                                      int& bi, unsigned& cost)
+{
+    int sb = 0;
+#pragma unroll
+    for (int c = 1; c < 5; ++c)
+        if (c != 3 && c < nc && scost[c] < scost[sb]) sb = c;
+    int ks = cand[0];
+#pragma unroll
+    for (int c = 1; c < 5; ++c)
+        if (c == sb) ks = cand[c];
+    unsigned tex_s, tex_t;
+    warp_sum2(sad8(ref8(win, pitch, lx, ly, mv_x(ks), mv_y(ks), h), c8),
+              sad8(ref8(win, pitch, lx, ly, mv_x(cand[3]), mv_y(cand[3]), h), c8), tex_s, tex_t);
+    bi = tex_t < tex_s ? 3 : sb;
+    cost = sb == bi ? scost[sb] : scost[3];
+}
+
 // Shape cost of one candidate: lanes 0..15 take the 16 rows (lanes 16..31
 // repeat them); every lane gets the total.
 __device__ __forceinline__ unsigned shape_cost1(const uint32_t* pcur, const uint32_t* pref, int Wp, int X0, int Y0,
@@ -1251,6 +1274,7 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
             bcost = ccost[c];
             bi = c;
         }
+    if (cls == SME_BOUNDARY && m.tt) boundary_t_by_texture(win, pitch, lx, ly, c8, cand, ccost, nc, h, bi, bcost);
     int nlog = nc;
     if (cls == SME_OPAQUE) {
         // Sec. 3.2 (the first step may be the speculative one, taken at
@@ -2220,14 +2244,19 @@ __global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArg
                         unsigned sc[5];
                         shape_costs_smem(acur, reinterpret_cast<const uint32_t*>(buf + L.o_aref), arw, S, X0, cand, nc,
                                          h, lane, sc);
-                        int best = cand[0];
+                        int bi = 0;
                         unsigned cost = sc[0];
 #pragma unroll
                         for (int c = 1; c < 5; ++c)
                             if (c < nc && sc[c] < cost) {
                                 cost = sc[c];
-                                best = cand[c];
+                                bi = c;
                             }
+                        if (m.tt) boundary_t_by_texture(win, pitch, lx, ly, c8, cand, sc, nc, h, bi, cost);
+                        int best = cand[0];
+#pragma unroll
+                        for (int c = 1; c < 5; ++c)
+                            if (c == bi) best = cand[c];
                         r.dx = mv_x(best);
                         r.dy = mv_y(best);
                         r.cost = cost;

@@ -141,6 +141,7 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
     mth.K = p->max_iters;
     mth.theta = p->theta;
     mth.eps = p->epsilon;
+    mth.tt = 0;
     const int F = n_frames, P = n_frames - rd;
     const int T = (g.MBW - 1) + 2 * (g.MBH - 1) + P;  // wavefront steps
     const size_t PM = (size_t)P * g.M;

@@ -20,6 +20,7 @@ SME_OPT_SCHEDULE, SME_OPT_PAIR_WARPS, SME_OPT_MB_CTAS_PER_SM, SME_OPT_SPECULATE 
 SME_OPT_CLUSTER_SIZE = 5
 SME_OPT_PAIR_DIRECT = 6
 SME_OPT_FOUR_MV = 7
+SME_OPT_BOUNDARY_T_TEXTURE = 8
 SCHEDULES = {"auto": 0, "mb": 1, "pair": 2, "cluster": 3}
 STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4: "SME_ERR_TIMEOUT",
           5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE", 8: "SME_ERR_SCRATCH"}
@@ -159,7 +160,7 @@ class Estimator:
     """One context of the library bound to the current CUDA device."""
 
     def __init__(self, width, height, search_range=16, subpel=1, theta=2.0, epsilon=1.0,
-                 max_iters=8, ref_distance=1, four_mv=False):
+                 max_iters=8, ref_distance=1, four_mv=False, boundary_t_texture=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -177,6 +178,9 @@ class Estimator:
         self.four_mv = bool(four_mv)
         if self.four_mv:
             self.set_option(SME_OPT_FOUR_MV, 1)
+        # Sec. 3.1 variant: boundary MBs judge T by texture against the shape winner of the others
+        if boundary_t_texture:
+            self.set_option(SME_OPT_BOUNDARY_T_TEXTURE, 1)
 
     # ------------------------------------------------------------ plumbing
     def _stream(self):

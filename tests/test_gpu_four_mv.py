@@ -110,6 +110,16 @@ def test_all_transparent_or_all_opaque(sme, fill):
         assert not g["mv"].any() and not g["npos"].any()
 
 
+def test_boundary_texture_variant_is_rejected(sme):
+    from paper_1002_1168_gb300.sme import SmeError
+
+    seq = synth.cif_sequence(frames=2)
+    est = sme.Estimator(352, 288, search_range=16, subpel=2, four_mv=True, boundary_t_texture=True)
+    with pytest.raises(SmeError):
+        est.estimate_sequence(cuda(seq.luma), cuda(seq.alpha[0]))
+    est.close()
+
+
 def test_seeds_are_rejected(sme):
     from paper_1002_1168_gb300.sme import SmeError
 

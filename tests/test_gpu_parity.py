@@ -44,10 +44,10 @@ def set_schedule(sme, est, schedule, pair_warps=0):
 
 
 def run_both(sme, luma, alpha, S=16, h=1, K=8, theta=2.0, eps=1.0, rd=1, temporal=None, seed=None,
-             want_pred=True, schedule="pair", pair_warps=0):
+             want_pred=True, schedule="pair", pair_warps=0, tt=False):
     F, H, W = luma.shape
     est = sme.Estimator(W, H, search_range=S, subpel=h, theta=theta, epsilon=eps, max_iters=K,
-                        ref_distance=rd)
+                        ref_distance=rd, boundary_t_texture=tt)
     set_schedule(sme, est, schedule, pair_warps)
     want = ("cost", "disp", "iters", "npos", "mb_class", "sse_mb", "sse") + (("pred",) if want_pred else ())
     g = est.estimate_sequence(cuda(luma), cuda(alpha),
@@ -55,7 +55,7 @@ def run_both(sme, luma, alpha, S=16, h=1, K=8, theta=2.0, eps=1.0, rd=1, tempora
                               seed=None if seed is None else cuda(seed.astype(np.float32)), want=want)
     g = {k: v.cpu().numpy() for k, v in g.items()}
     est.close()
-    p = O.OracleParams(W, H, S, h, theta, eps, K)
+    p = O.OracleParams(W, H, S, h, theta, eps, K, boundary_t_texture=int(tt))
     o = O.estimate_sequence(p, luma, alpha, ref_distance=rd, temporal_in=temporal, seed=seed,
                             want_pred=want_pred)
     return g, o, p
@@ -232,6 +232,18 @@ def test_pair_row_slots_with_transparent_rows_below(sme, schedule, warps):
     g, o, p = run_both(sme, luma, alpha, S=8, h=2, schedule=schedule, pair_warps=warps)
     assert_parity(g, o, p, luma)
     assert (g["mv"][:, :64] != 0).any(axis=-1).mean() > 0.5  # the rows read below carry vectors
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+@pytest.mark.parametrize("h", [1, 2])
+def test_boundary_temporal_by_texture_variant(sme, schedule, h):
+    """Sec. 3.1 variant (boundary T judged by texture): bit-exact with the
+    oracle's variant on a VOP sequence where it changes the field."""
+    seq = synth.cif_sequence(frames=6)
+    g, o, p = run_both(sme, seq.luma, seq.alpha[0], S=16, h=h, schedule=schedule, tt=True)
+    assert_parity(g, o, p, seq.luma)
+    o0 = O.estimate_sequence(O.OracleParams(352, 288, 16, h), seq.luma, seq.alpha[0])
+    assert (o0["mv"] != o["mv"]).any()
 
 
 @pytest.mark.parametrize("schedule", SCHEDULES)

@@ -288,13 +288,15 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     int rc;
     if ((rc = ensure(c->packed, (size_t)F * g.H * g.Wp * sizeof(uint32_t)))) return rc;
     if ((rc = ensure(c->cls, (size_t)F * g.M))) return rc;
-    if ((rc = ensure(c->ready, total * sizeof(unsigned long long), true, c->stream))) return rc;
+    // the four-vector mode's per-MB schedule publishes three words per MB
+    if ((rc = ensure(c->ready, (c->four_mv ? 3 : 1) * total * sizeof(unsigned long long), true, c->stream))) return rc;
     if ((rc = ensure(c->desc, sizeof(SeqDesc)))) return rc;
     // The per-MB schedule is the faster one on single sequences (measured on
     // CIF x 30 frames: 130 us vs 193 us per launch); the pair schedule is
     // chosen only on request, and always in the four-vector mode.
     if (c->four_mv && (seed || c->m.tt)) return SME_ERR_ARG;
-    const bool pair = c->schedule == kSchedPair || c->four_mv, cluster = !pair && c->schedule == kSchedCluster;
+    // four-vector mode: the pair schedule on request, else the per-MB one
+    const bool pair = c->schedule == kSchedPair, cluster = !c->four_mv && c->schedule == kSchedCluster;
     MapSet maps;
     memset(&maps, 0, sizeof(maps));
     int C = 0;
@@ -364,6 +366,8 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     a.total_units = P;
     a.mbw_max = g.MBW;
     a.ready = (unsigned long long*)c->ready.p;
+    a.ready_a = c->four_mv ? a.ready + total : nullptr;
+    a.ready_bc = c->four_mv ? a.ready + 2 * total : nullptr;
     a.status = c->status;
     a.m = c->m;
     a.total = (int)total;
@@ -390,11 +394,14 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
         const int grid = std::max(1, std::min(c->num_sms * per_sm, P));
         if (launch_me_pair(c->m, a, &maps, nw, grid, c->stream) != cudaSuccess) return SME_ERR_CUDA;
     } else {
-        const int per_sm = c->mb_ctas_per_sm > 0 ? std::min(c->mb_ctas_per_sm, c->me_blocks_per_sm) : c->me_blocks_per_sm;
+        int resident = c->me_blocks_per_sm;
+        if (c->four_mv && (me4_occupancy(c->m.S, &resident) != cudaSuccess || resident < 1)) return SME_ERR_CUDA;
+        const int per_sm = c->mb_ctas_per_sm > 0 ? std::min(c->mb_ctas_per_sm, resident) : resident;
         const long long cap = (long long)c->num_sms * per_sm;
         const long long want = ((long long)total + kMeWarps - 1) / kMeWarps;
         const int grid = (int)std::max(1LL, std::min<long long>(cap, want));
-        if (launch_me(c->m, a, grid, c->stream) != cudaSuccess) return SME_ERR_CUDA;
+        if ((c->four_mv ? launch_me4(c->m, a, grid, c->stream) : launch_me(c->m, a, grid, c->stream)) != cudaSuccess)
+            return SME_ERR_CUDA;
     }
     if (ev && cudaEventRecord(ev[2], c->stream) != cudaSuccess) return SME_ERR_CUDA;
     return SME_OK;

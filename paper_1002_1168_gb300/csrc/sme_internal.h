@@ -102,7 +102,9 @@ struct MeArgs {
     const CUtensorMap* tmaps; // per-pair schedule: luma tensor map per sequence (NULL: kernel parameter)
     int total_units;
     int mbw_max;
-    unsigned long long* ready;  // [total] (epoch << 32) | packed vector
+    unsigned long long* ready;  // [total] (epoch << 32) | packed vector (four-vector mode: block 0)
+    unsigned long long* ready_a;   // four-vector mode, per-MB schedule: block 1 (for A)
+    unsigned long long* ready_bc;  // four-vector mode, per-MB schedule: block 2 (for B, C)
     DevStatus* status;
     Method m;
     int total;
@@ -144,6 +146,9 @@ struct QueryArgs {
 cudaError_t launch_classify(const Geom& g, const ClassifyArgs& a, cudaStream_t s);
 cudaError_t launch_classify_batch(const ClassifyBatchArgs& a, int max_mbh, int total_frames, cudaStream_t s);
 cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s);
+// Per-MB schedule in the four-vector mode (three ready arrays in MeArgs).
+cudaError_t launch_me4(const Method& m, const MeArgs& a, int grid, cudaStream_t s);
+cudaError_t me4_occupancy(int S, int* blocks_per_sm);
 // `maps` points to 4 CUtensorMaps (128-byte aligned): luma window box, current
 // block box, packed-alpha reference strip, packed-alpha current BAB.
 cudaError_t launch_me_pair(const Method& m, const MeArgs& a, const void* maps, int nwarps, int grid, cudaStream_t s);

@@ -1329,6 +1329,7 @@ __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
     }
 }
 
+
 // ============================================ ME, one cluster per sequence ==
 // The first cluster of the launch (the chain cluster) estimates every
 // non-transparent MB of one sequence; the other clusters (helpers) finish the
@@ -1933,6 +1934,10 @@ __device__ __forceinline__ void finish_mb4(const SeqDesc* sd, int idx, int k, in
     __syncwarp();
 }
 
+__device__ __forceinline__ Blk4 opaque_blocks4(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
+                                               const P8& c8, const float (&ux)[8], const float (&uy)[8],
+                                               const VRange& V, const int (&cand)[5], int* blog, int lane);
+
 // Fig. 1 at MB level (16x16 costs of the candidates A, B, C, T) and, on
 // opaque MBs, the block searches from the winner.  The candidates are in
 // cand[0..4); each block log starts with them.
@@ -1964,6 +1969,21 @@ __device__ __forceinline__ Blk4 search_mb4(const Method& m, int cls, const uint8
         s.r8 = ref8(win, pitch, lx, ly, s.dx, s.dy, h);
         return s;
     }
+    return opaque_blocks4(m, win, pitch, lx, ly, c8, ux, uy, V, cand, blog, lane);
+}
+
+// Opaque MB in the four-vector mode: 16x16 texture SADs of the candidates A,
+// B, C, T, first strict minimum, then the four block searches from it.
+__device__ __forceinline__ Blk4 opaque_blocks4(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
+                                               const P8& c8, const float (&ux)[8], const float (&uy)[8],
+                                               const VRange& V, const int (&cand)[5], int* blog, int lane)
+{
+    const int h = m.h;
+    Blk4 s;
+    s.iters = 0;
+    s.nlog = 4;
+    s.lastx = s.lasty = 0.0f;
+    s.done = false;
     P8 cs8[4];
     unsigned part[4];
 #pragma unroll
@@ -2002,6 +2022,193 @@ __device__ __forceinline__ Blk4 search_mb4(const Method& m, int cls, const uint8
     prs_blocks(m, win, pitch, lx, ly, c8, ux, uy, (int)blk_sum(cx), (int)blk_sum(cy), V, s, blog, lane);
     return s;
 }
+
+// ============================== ME, per-MB warps, four vectors per MB ==
+// The per-MB schedule of me_kernel with the four-vector mode (Sec. 3.2, 8x8
+// blocks; reading of the candidate layout as in the pair kernel).  A consumer
+// needs a different block of its producer by role, so every MB publishes
+// three ready words, each (epoch << 32) | vector: block 0 (for T), block 1
+// (for A), block 2 (for B and C).
+struct Links4 {
+    unsigned long long* rt;
+    unsigned long long* ra;
+    unsigned long long* rbc;
+    unsigned epoch;
+    int fault;
+    __device__ __forceinline__ void publish(int gid, int k0, int k1, int k2, int lane) const
+    {
+        if (lane == 0 && gid != fault) {
+            const unsigned long long t = (unsigned long long)epoch << 32;
+            st_ready(rt + gid, t | (unsigned)k0);
+            st_ready(ra + gid, t | (unsigned)k1);
+            st_ready(rbc + gid, t | (unsigned)k2);
+        }
+    }
+};
+
+__host__ __device__ __forceinline__ int warp_smem4(int S) { return win_bytes(S) + ceil16(4 * kMaxLog * 4); }
+
+// Alpha mismatches of the lane's quadrant at the full-pel part of key, from
+// the packed alpha in global memory (as shape_row).
+__device__ __forceinline__ unsigned shape_quadrant_g(const uint32_t* pcur, const uint32_t* pref, int Wp, int X0,
+                                                     int Y0, int key, int h, int lane)
+{
+    const int r = lane & 15, fdx = mv_x(key) / h, fdy = mv_y(key) / h;  // trunc toward zero
+    const uint32_t* rc = pcur + (size_t)(Y0 + r) * Wp;
+    const unsigned cb = (__ldg(rc + (X0 >> 5)) >> (X0 & 31)) & 0xffffu;
+    const int xr = X0 + fdx;
+    const uint32_t* rr = pref + (size_t)(Y0 + r + fdy) * Wp;
+    const unsigned diff = (cb ^ __funnelshift_r(__ldg(rr + (xr >> 5)), __ldg(rr + (xr >> 5) + 1), xr & 31)) & 0xffffu;
+    unsigned lo = __popc(diff & 0xffu), hi = __popc(diff >> 8);
+#pragma unroll
+    for (int o = 1; o <= 4; o <<= 1) {
+        lo += __shfl_xor_sync(kFull, lo, o);
+        hi += __shfl_xor_sync(kFull, hi, o);
+    }
+    const int src = (lane >> 4) << 3;
+    const unsigned qlo = __shfl_sync(kFull, lo, src), qhi = __shfl_sync(kFull, hi, src);
+    return (lane & 1) ? qhi : qlo;
+}
+
+__device__ __forceinline__ bool me_one_mb4(const MeArgs& a, const Method& m, int gid, const SeqDesc* sd,
+                                           uint8_t* win, int* slog, const float* s_rcp, const Links4& L, int lane,
+                                           int pitch)
+{
+    const int h = m.h;
+    const int W = sd->W, H = sd->H, M = sd->M, MBW = sd->MBW, rd = sd->rd;
+    const int idx = gid - sd->gid_base;
+    const int k = idx / M, mb = idx - k * M;
+    const int u = mb % MBW, v = mb / MBW;
+    const int X0 = 16 * u, Y0 = 16 * v;
+    const int x0 = X0 + 8 * (lane & 1), y = Y0 + (lane >> 1);
+    const size_t FS = (size_t)W * H;
+    const uint8_t* ref = sd->luma + (size_t)k * FS;
+    const uint8_t* cur = sd->luma + (size_t)(k + rd) * FS;
+    const int cls = __ldg(sd->cls + (size_t)(k + rd) * M + mb);
+    const P8 c8 = load8(cur + (size_t)y * W + x0);
+
+    if (cls == SME_TRANSPARENT) {
+        L.publish(gid, 0, 0, 0, lane);
+        Blk4 s4;
+        s4.dx = s4.dy = s4.iters = s4.nlog = 0;
+        s4.cost = 0;
+        s4.lastx = s4.lasty = 0.0f;
+        s4.done = true;
+        s4.r8 = load8(ref + (size_t)y * W + x0);
+        finish_mb4(sd, idx, k, cls, s4, c8, slog, lane, FS, W, y, x0);
+        return true;
+    }
+
+    int wx0, wy0;
+    stage_window(win, ref, W, H, m.S, X0, Y0, lane, wx0, wy0);
+    float ux[8], uy[8];
+    int nx = 0, ny = 0;
+    if (cls == SME_OPAQUE) mb_factors(cur, W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny);
+    const VRange V = valid_range(W, H, m, X0, Y0);
+    const int lx = x0 - wx0, ly = y - wy0;
+
+    // ---- candidates: A = block 1 of the left MB, B / C = block 2 of the MBs
+    // above / above-right, T = block 0 of the previous pair (reading c22) ----
+    int dep = -1;
+    const unsigned long long* src = L.rt;
+    if (lane == 0 && u > 0) { dep = gid - 1; src = L.ra; }
+    if (lane == 1 && v > 0) { dep = gid - MBW; src = L.rbc; }
+    if (lane == 2 && v > 0 && u < MBW - 1) { dep = gid - MBW + 1; src = L.rbc; }
+    if (lane == 3 && k > 0) dep = gid - M;
+    int key = 0;
+    if (lane == 3 && k == 0 && sd->temporal_in)
+        key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + 4 * mb));
+    if (lane < 4) key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
+    bool res = dep < 0;
+    unsigned long long t_start = 0;
+    for (unsigned it = 0;; ++it) {
+        if (lane < 4 && !res) {
+            const unsigned long long w = ld_ready(src + dep);
+            if ((unsigned)(w >> 32) == L.epoch) {
+                const int kk = (int)(unsigned)w;
+                key = pack_mv(clampi(mv_x(kk), V.lox, V.hix), clampi(mv_y(kk), V.loy, V.hiy));
+                res = true;
+            }
+        }
+        if (__all_sync(kFull, lane >= 4 || res)) break;
+        if ((it & 15u) == 15u) {
+            // Bounded wait: the launch's abort word, a time limit, an iteration cap.
+            int give_up = 0;
+            if (lane == 0) {
+                const unsigned long long now = globaltimer();
+                if (t_start == 0) t_start = now;
+                give_up = ld_relaxed(&a.status->abort) || (long long)(now - t_start) > a.timeout_ns ||
+                          it > (1u << 24);
+            }
+            if (__shfl_sync(kFull, give_up, 0)) {
+                if (lane == 0 && !ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
+                return false;
+            }
+        }
+    }
+    int cand[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) cand[c] = c < 4 ? __shfl_sync(kFull, key, c) : 0;
+    if (lane < 16) slog[(lane >> 2) * kMaxLog + (lane & 3)] = cand[lane & 3];
+    __syncwarp();
+    int* blog = slog + blk_of(lane) * kMaxLog;
+    Blk4 s4;
+    if (cls == SME_BOUNDARY) {
+        const uint32_t* pcur = sd->packed + (size_t)(k + rd) * H * sd->Wp;
+        const uint32_t* pref = sd->packed + (size_t)k * H * sd->Wp;
+        unsigned sc[5];
+        shape_costs(pcur, pref, sd->Wp, X0, Y0, cand, 4, h, lane, sc);
+        int best = cand[0];
+        unsigned cost = sc[0];
+#pragma unroll
+        for (int c = 1; c < 4; ++c)
+            if (sc[c] < cost) {
+                cost = sc[c];
+                best = cand[c];
+            }
+        s4.dx = mv_x(best);
+        s4.dy = mv_y(best);
+        s4.iters = 0;
+        s4.nlog = 4;
+        s4.lastx = s4.lasty = 0.0f;
+        s4.done = true;
+        s4.cost = shape_quadrant_g(pcur, pref, sd->Wp, X0, Y0, best, h, lane);
+        s4.r8 = ref8(win, pitch, lx, ly, s4.dx, s4.dy, h);
+    } else {
+        s4 = opaque_blocks4(m, win, pitch, lx, ly, c8, ux, uy, V, cand, blog, lane);
+    }
+    const int kb = pack_mv(s4.dx, s4.dy);
+    L.publish(gid, __shfl_sync(kFull, kb, 0), __shfl_sync(kFull, kb, 1), __shfl_sync(kFull, kb, 16), lane);
+    finish_mb4(sd, idx, k, cls, s4, c8, blog, lane, FS, W, y, x0);
+    return true;
+}
+
+__global__ void __launch_bounds__(32 * kMeWarps) me4_kernel(const MeArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const Method m = a.m;
+    const int pitch = win_pitch(m.S);
+    uint8_t* win = smem + (size_t)wid * warp_smem4(m.S);
+    int* slog = reinterpret_cast<int*>(win + win_bytes(m.S));
+    const Links4 L{a.ready, a.ready_a, a.ready_bc, ld_relaxed(&a.status->epoch), a.fault_ticket};
+    __shared__ float s_rcp[512];
+    fill_rcp(s_rcp);
+    __syncthreads();
+    for (;;) {
+        int t = 0;
+        if (lane == 0) {
+            t = (int)atomicAdd(&a.status->ticket, 1u);
+            if (ld_relaxed(&a.status->abort)) t = a.total;
+        }
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= a.total) break;
+        const int gid = __ldg(a.sched + t);
+        const SeqDesc* sd = a.seqs + (a.sched_seq ? __ldg(a.sched_seq + t) : 0);
+        if (!me_one_mb4(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) break;
+    }
+}
+
 
 // kDirect: runs of transparent MBs (known from the classification launch)
 // are finished by transparent_run and only the other MBs are staged by TMA;
@@ -2425,6 +2632,33 @@ cudaError_t me_occupancy(int S, int* blocks_per_sm)
         if (e != cudaSuccess) return e;
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, me_kernel, 32 * kMeWarps, smem);
+}
+
+cudaError_t me4_occupancy(int S, int* blocks_per_sm)
+{
+    const size_t smem = (size_t)kMeWarps * warp_smem4(S);
+    cudaError_t e = cudaFuncSetAttribute(me4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, me4_kernel, 32 * kMeWarps, smem);
+}
+
+cudaError_t launch_me4(const Method& m, const MeArgs& a, int grid, cudaStream_t s)
+{
+    // cooperative for the same reason as launch_me
+    const size_t smem = (size_t)kMeWarps * warp_smem4(m.S);
+    cudaError_t e = cudaFuncSetAttribute(me4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * kMeWarps);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, me4_kernel, a);
 }
 
 cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s)

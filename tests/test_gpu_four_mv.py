@@ -30,11 +30,13 @@ def cuda(a):
 WANT = ("cost", "disp", "iters", "npos", "mb_class", "sse_mb", "sse", "pred")
 
 
-def run_both(sme, luma, alpha, S=16, h=2, K=8, rd=1, temporal4=None, warps=0, host=False):
+SCHEDULES = ["mb", "pair"]  # the per-MB schedule (default) and the per-pair one
+
+
+def run_both(sme, luma, alpha, S=16, h=2, K=8, rd=1, temporal4=None, warps=0, host=False, schedule="mb"):
     F, H, W = luma.shape
     est = sme.Estimator(W, H, search_range=S, subpel=h, max_iters=K, ref_distance=rd, four_mv=True)
-    if warps:
-        est.set_option(sme.SME_OPT_PAIR_WARPS, warps)
+    est.set_schedule(schedule, pair_warps=warps if schedule == "pair" else 0)
     tmp = None if temporal4 is None else temporal4.astype(np.int16)
     if host:
         g = est.estimate_sequence_host(torch.from_numpy(luma), torch.from_numpy(alpha),
@@ -64,47 +66,52 @@ def assert_parity(g, o, luma, rd=1):
         assert np.array_equal(g["sse_mb"][k].view(np.uint32).astype(np.int64), per), "per-MB SSE"
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("h", [1, 2])
-def test_qcif_pair(sme, h):
+def test_qcif_pair(sme, h, schedule):
     seq = synth.qcif_pair()
-    g, o = run_both(sme, seq.luma, seq.alpha, S=16, h=h)
+    g, o = run_both(sme, seq.luma, seq.alpha, S=16, h=h, schedule=schedule)
     assert_parity(g, o, seq.luma)
     assert (o["mv"][..., 0, :] != o["mv"][..., 3, :]).any()  # blocks do differ
 
 
-@pytest.mark.parametrize("warps", [0, 2, 5])
-def test_cif_sequence_halfpel(sme, warps):
+@pytest.mark.parametrize("schedule,warps", [("mb", 0), ("pair", 0), ("pair", 2), ("pair", 5)])
+def test_cif_sequence_halfpel(sme, schedule, warps):
     seq = synth.cif_sequence(frames=6)
-    g, o = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, warps=warps)
+    g, o = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, warps=warps, schedule=schedule)
     assert_parity(g, o, seq.luma)
 
 
-def test_host_buffers(sme):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_host_buffers(sme, schedule):
     seq = synth.cif_sequence(frames=3)
-    g, o = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, host=True)
+    g, o = run_both(sme, seq.luma, seq.alpha[0], S=16, h=2, host=True, schedule=schedule)
     assert_parity(g, o, seq.luma)
 
 
-def test_temporal_field_and_ref_distance_two(sme):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_temporal_field_and_ref_distance_two(sme, schedule):
     seq = synth.cif_sequence(frames=5)
     rng = np.random.default_rng(3)
     tmp = rng.integers(-12, 13, (396, 4, 2))
-    g, o = run_both(sme, seq.luma, seq.alpha[0], S=8, h=2, rd=2, temporal4=tmp)
+    g, o = run_both(sme, seq.luma, seq.alpha[0], S=8, h=2, rd=2, temporal4=tmp, schedule=schedule)
     assert_parity(g, o, seq.luma, rd=2)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("W,H,F,S,h,K", [(48, 48, 3, 4, 2, 8), (64, 32, 4, 7, 1, 16), (96, 64, 3, 32, 2, 3)])
-def test_edges_and_parameters_random_content(sme, W, H, F, S, h, K):
+def test_edges_and_parameters_random_content(sme, W, H, F, S, h, K, schedule):
     luma, alpha = synth.random_frames(W, H, F, seed=W * H + S)
-    g, o = run_both(sme, luma, alpha, S=S, h=h, K=K)
+    g, o = run_both(sme, luma, alpha, S=S, h=h, K=K, schedule=schedule)
     assert_parity(g, o, luma)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("fill", [0, 255])
-def test_all_transparent_or_all_opaque(sme, fill):
+def test_all_transparent_or_all_opaque(sme, fill, schedule):
     seq = synth.cif_sequence(frames=3)
     alpha = np.full_like(seq.alpha[0], fill)
-    g, o = run_both(sme, seq.luma, alpha, S=16, h=2)
+    g, o = run_both(sme, seq.luma, alpha, S=16, h=2, schedule=schedule)
     assert_parity(g, o, seq.luma)
     if fill == 0:
         assert not g["mv"].any() and not g["npos"].any()
@@ -128,4 +135,27 @@ def test_seeds_are_rejected(sme):
     with pytest.raises(SmeError):
         est.estimate_sequence(cuda(seq.luma), cuda(seq.alpha[0]),
                               seed=cuda(np.zeros((1, 396, 2), np.float32)))
+    est.close()
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_bounded_wait_reports_timeout_and_context_recovers(sme, schedule):
+    """One MB's ready words are never published: its consumers give up after
+    a short limit, the host reads SME_ERR_TIMEOUT, and the next estimate on
+    the same context is correct."""
+    from paper_1002_1168_gb300.sme import SmeError
+
+    luma, alpha = synth.translated_pair(64, 64, (1, 0), seed=3)
+    luma = np.concatenate([luma, luma[:1]])
+    alpha = np.concatenate([alpha, alpha[:1]])
+    est = sme.Estimator(64, 64, search_range=8, subpel=1, four_mv=True)
+    est.set_schedule(schedule)
+    est.debug_set_fault(skip_ticket=0, timeout_ns=20_000_000)
+    with pytest.raises(SmeError) as e:
+        est.estimate_sequence(cuda(luma), cuda(alpha))
+    assert e.value.status == 4
+    est.debug_set_fault(-1, 0)
+    g = est.estimate_sequence(cuda(luma), cuda(alpha))
+    o = O.estimate_sequence4(O.OracleParams(64, 64, 8, 1), luma, alpha)
+    assert np.array_equal(g["mv"].cpu().numpy(), o["mv"])
     est.close()

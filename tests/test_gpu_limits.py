@@ -81,11 +81,13 @@ def test_limits_every_schedule(sme, case, schedule):
         assert o["iters"].max() > 1
 
 
+@pytest.mark.parametrize("schedule", ["mb", "pair"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_limits_four_vectors(sme, case):
+def test_limits_four_vectors(sme, case, schedule):
     W, H, F, S, h, K, eps = CASES[case]
     luma, alpha = synth.random_frames(W, H, F, seed=W + 5 * H + S)
     est = sme.Estimator(W, H, search_range=S, subpel=h, epsilon=eps, max_iters=K, four_mv=True)
+    est.set_schedule(schedule)
     g = est.estimate_sequence(cuda(luma), cuda(alpha), want=("cost", "disp", "iters", "npos", "mb_class", "sse"))
     g = {k: v.cpu().numpy() for k, v in g.items()}
     est.close()

@@ -396,6 +396,8 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     } else {
         int resident = c->me_blocks_per_sm;
         if (c->four_mv && (me4_occupancy(c->m.S, &resident) != cudaSuccess || resident < 1)) return SME_ERR_CUDA;
+        if (!c->four_mv && c->m.tt && (me_occupancy(c->m.S, &resident, true) != cudaSuccess || resident < 1))
+            return SME_ERR_CUDA;
         const int per_sm = c->mb_ctas_per_sm > 0 ? std::min(c->mb_ctas_per_sm, resident) : resident;
         const long long cap = (long long)c->num_sms * per_sm;
         const long long want = ((long long)total + kMeWarps - 1) / kMeWarps;

@@ -175,7 +175,7 @@ cudaError_t launch_es(const uint8_t* luma, int W, int H, int S, int h, int rd, i
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 cudaError_t launch_queries(const Geom& g, const Method& m, const QueryArgs& a, cudaStream_t s);
 // Resident CTAs per SM of the persistent ME kernel for search range S.
-cudaError_t me_occupancy(int S, int* blocks_per_sm);
+cudaError_t me_occupancy(int S, int* blocks_per_sm, bool variants = false);
 size_t me_smem_bytes(int S);
 
 }  // namespace sme

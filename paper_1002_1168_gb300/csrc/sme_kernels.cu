@@ -1113,7 +1113,10 @@ struct ClusterLinks {
 // One MB (global id gid of sequence sd) by one warp: Fig. 1 from the class
 // on, with the candidates of Fig. 3 taken from `L`.  Returns false when a
 // bounded wait gave up (the launch's error status is raised).
-template <class Links>
+// kVariants: the code of the Sec. 3.1 boundary variant is compiled in (taken
+// when m.tt); the default instantiation leaves it out, since even an untaken
+// branch after the wait loop measurably slowed the search.
+template <class Links, bool kVariants>
 __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int gid, const SeqDesc* sd, uint8_t* win,
                                           int* slog, const float* s_rcp, const Links& L, int lane, int pitch)
 {
@@ -1274,7 +1277,8 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
             bcost = ccost[c];
             bi = c;
         }
-    if (cls == SME_BOUNDARY && m.tt) boundary_t_by_texture(win, pitch, lx, ly, c8, cand, ccost, nc, h, bi, bcost);
+    if constexpr (kVariants)
+        if (cls == SME_BOUNDARY && m.tt) boundary_t_by_texture(win, pitch, lx, ly, c8, cand, ccost, nc, h, bi, bcost);
     int nlog = nc;
     if (cls == SME_OPAQUE) {
         // Sec. 3.2 (the first step may be the speculative one, taken at
@@ -1302,6 +1306,7 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
     return true;
 }
 
+template <bool kVariants>
 __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -1325,7 +1330,7 @@ __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
         if (t >= a.total) break;
         const int gid = __ldg(a.sched + t);
         const SeqDesc* sd = a.seqs + (a.sched_seq ? __ldg(a.sched_seq + t) : 0);
-        if (!me_one_mb(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) break;
+        if (!me_one_mb<GlobalLinks, kVariants>(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) break;
     }
 }
 
@@ -1445,7 +1450,7 @@ __global__ void __launch_bounds__(32 * kClusterWarps, 1) me_cluster_kernel(const
         // the consumer slots are fetched now; they are needed only at the end
         const int cons = lane < 4 ? __ldg(a.cl_consumers + 4 * (size_t)gid + lane) : -1;
         const ClusterLinks L{slots, i, cons, a.fault_ticket};
-        if (!me_one_mb(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) break;
+        if (!me_one_mb<ClusterLinks, true>(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) break;
     }
     // no CTA leaves while a peer may still store into its slots
     cluster_sync_all();
@@ -2624,14 +2629,15 @@ cudaError_t launch_classify_batch(const ClassifyBatchArgs& a, int max_mbh, int t
     return cudaGetLastError();
 }
 
-cudaError_t me_occupancy(int S, int* blocks_per_sm)
+cudaError_t me_occupancy(int S, int* blocks_per_sm, bool variants)
 {
     const size_t smem = me_smem_bytes(S);
+    const void* fn = variants ? (const void*)me_kernel<true> : (const void*)me_kernel<false>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(me_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, me_kernel, 32 * kMeWarps, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 32 * kMeWarps, smem);
 }
 
 cudaError_t me4_occupancy(int S, int* blocks_per_sm)
@@ -2667,7 +2673,8 @@ cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s
     // is cooperative: every block is resident at once.
     const size_t smem = me_smem_bytes(m.S);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(me_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(m.tt ? me_kernel<true> : me_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -2680,7 +2687,7 @@ cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, me_kernel, a);
+    return cudaLaunchKernelEx(&cfg, m.tt ? me_kernel<true> : me_kernel<false>, a);
 }
 
 size_t me_cluster_smem_bytes(int S, int cap, int warps)

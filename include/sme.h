@@ -138,9 +138,12 @@ int sme_estimate_sequence(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alph
                           const sme_mv* temporal_in, const float* seed, const sme_outputs* out);
 
 /* Same as sme_estimate_sequence with every pointer (inputs and outputs) in
- * HOST memory: copies inputs to context-owned device buffers, runs, copies
- * the requested outputs back and synchronises.  Pinned host memory gives the
- * fastest copies. */
+ * HOST memory, and synchronises before returning.  The luma frames are
+ * copied to a context-owned device buffer.  A pinned (page-locked) alpha is
+ * read in place by the classification, and pinned outputs other than sse are
+ * written in place by the kernels over the CPU-GPU link; pageable ones go
+ * through context-owned device buffers and copies.  The results are the same
+ * either way. */
 int sme_estimate_sequence_host(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha,
                                int n_frames, const sme_mv* temporal_in, const float* seed,
                                const sme_outputs* out);

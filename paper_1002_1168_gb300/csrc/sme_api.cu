@@ -71,6 +71,11 @@ struct sme_ctx {
     // host-buffer interface
     DevBuf h_luma, h_alpha, h_tmp, h_seed, h_mv, h_cost, h_disp, h_iters, h_npos, h_cls, h_ssemb,
         h_sse, h_pred;
+    int* h_err = nullptr;  // pinned host copy of the device error word (sme_synchronize)
+    // host-buffer interface: the luma copy runs on a second stream while the
+    // classification reads a pinned alpha in place
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_go = nullptr, copy_done = nullptr;
 };
 
 namespace {
@@ -275,8 +280,10 @@ int build_cluster_schedule(sme_ctx* c, int P, int* C_out)
     return SME_OK;
 }
 
+// before_me: an event the motion-estimation launch waits for (after the
+// classification has been queued), or NULL.
 int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, const sme_mv* temporal_in,
-                 const float* seed, const sme_outputs* out)
+                 const float* seed, const sme_outputs* out, cudaEvent_t before_me = nullptr)
 {
     const Geom& g = c->g;
     if (!luma || !alpha || !out || !out->mv) return SME_ERR_ARG;
@@ -355,6 +362,7 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     }
     if (launch_classify(g, ca, c->stream) != cudaSuccess) return SME_ERR_CUDA;
     if (ev && cudaEventRecord(ev[1], c->stream) != cudaSuccess) return SME_ERR_CUDA;
+    if (before_me && cudaStreamWaitEvent(c->stream, before_me, 0) != cudaSuccess) return SME_ERR_CUDA;
 
     MeArgs a{};
     a.seqs = (const SeqDesc*)c->desc.p;
@@ -414,6 +422,19 @@ void profile_free(sme_ctx* c)
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.clear();
     c->prof_max = c->prof_n = 0;
+}
+
+// The device-mapped address of a pinned (page-locked) host buffer, or NULL
+// for any other pointer.  Kernels read and write such buffers in place, over
+// the CPU-GPU link, instead of through a staging copy.
+void* mapped_host(const void* p)
+{
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 int read_status(sme_ctx* c)
@@ -520,9 +541,11 @@ int sme_create(sme_ctx** out, const sme_params* p, void* stream)
         return SME_ERR_CUDA;
     }
     if (cudaMalloc(&c->status, sizeof(DevStatus)) != cudaSuccess ||
-        cudaMemset(c->status, 0, sizeof(DevStatus)) != cudaSuccess) {
+        cudaMemset(c->status, 0, sizeof(DevStatus)) != cudaSuccess ||
+        cudaHostAlloc(&c->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         if (c->status) cudaFree(c->status);
+        if (c->h_err) cudaFreeHost(c->h_err);
         delete c;
         return SME_ERR_NOMEM;
     }
@@ -542,6 +565,13 @@ int sme_destroy(sme_ctx* c)
     for (DevBuf* b : bufs) release(*b);
     profile_free(c);
     if (c->status) cudaFree(c->status);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->copy_go) cudaEventDestroy(c->copy_go);
+    if (c->copy_done) cudaEventDestroy(c->copy_done);
     delete c;
     return SME_OK;
 }
@@ -556,8 +586,18 @@ int sme_set_stream(sme_ctx* c, void* stream)
 int sme_synchronize(sme_ctx* c)
 {
     if (!c) return SME_ERR_ARG;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SME_ERR_CUDA;
-    return read_status(c);
+    // the error word travels with the stream's work: one wait, not two
+    if (cudaMemcpyAsync(c->h_err, &c->status->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return SME_ERR_CUDA;
+    const int err = *c->h_err;
+    if (err) {
+        if (cudaMemsetAsync(&c->status->err, 0, sizeof(int), c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return SME_ERR_CUDA;
+        return err;
+    }
+    return SME_OK;
 }
 
 int sme_classify(sme_ctx* c, const uint8_t* alpha, int n_frames, uint8_t* mb_class, uint32_t* packed)
@@ -589,12 +629,30 @@ int sme_estimate_sequence_host(sme_ctx* c, const uint8_t* luma, const uint8_t* a
     const size_t NB = c->four_mv ? 4 : 1;  // vectors per MB
     const cudaStream_t s = c->stream;
     int rc;
-    if ((rc = ensure(c->h_luma, FS * n_frames)) || (rc = ensure(c->h_alpha, FS * n_frames)) ||
-        (rc = ensure(c->h_mv, NB * PM * sizeof(sme_mv))))
+    // Luma is read many times (search windows): always copied.  Alpha is read
+    // once, by the classification: read in place when it is pinned.  Outputs
+    // other than the per-pair SSE (accumulated with atomics) are written in
+    // place when pinned, else staged and copied back.
+    const uint8_t* dalpha = (const uint8_t*)mapped_host(alpha);
+    if ((rc = ensure(c->h_luma, FS * n_frames)) || (!dalpha && (rc = ensure(c->h_alpha, FS * n_frames))))
         return rc;
-    if (cudaMemcpyAsync(c->h_luma.p, luma, FS * n_frames, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(c->h_alpha.p, alpha, FS * n_frames, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    cudaEvent_t luma_ready = nullptr;
+    if (dalpha) {
+        if (!c->copy_stream && (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                                cudaEventCreateWithFlags(&c->copy_go, cudaEventDisableTiming) != cudaSuccess ||
+                                cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming) != cudaSuccess))
+            return SME_ERR_CUDA;
+        // the copy waits for earlier work on the context's stream (which may still read h_luma)
+        if (cudaEventRecord(c->copy_go, s) != cudaSuccess || cudaStreamWaitEvent(c->copy_stream, c->copy_go, 0) ||
+            cudaMemcpyAsync(c->h_luma.p, luma, FS * n_frames, cudaMemcpyHostToDevice, c->copy_stream) ||
+            cudaEventRecord(c->copy_done, c->copy_stream))
+            return SME_ERR_CUDA;
+        luma_ready = c->copy_done;
+    } else if (cudaMemcpyAsync(c->h_luma.p, luma, FS * n_frames, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+               cudaMemcpyAsync(c->h_alpha.p, alpha, FS * n_frames, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         return SME_ERR_CUDA;
+    }
+    if (!dalpha) dalpha = (const uint8_t*)c->h_alpha.p;
     const sme_mv* dtmp = nullptr;
     const float* dseed = nullptr;
     if (temporal_in) {
@@ -610,13 +668,14 @@ int sme_estimate_sequence_host(sme_ctx* c, const uint8_t* luma, const uint8_t* a
         dseed = (const float*)c->h_seed.p;
     }
     sme_outputs d{};
-    d.mv = (sme_mv*)c->h_mv.p;
     struct Opt {
         void* host;
         DevBuf* buf;
         size_t bytes;
         void** dev;
+        bool copy;  // staged (false: written in place)
     } opts[] = {
+        {out->mv, &c->h_mv, NB * PM * sizeof(sme_mv), (void**)&d.mv},
         {out->cost, &c->h_cost, NB * PM * 4, (void**)&d.cost},
         {out->disp, &c->h_disp, NB * PM * 8, (void**)&d.disp},
         {out->iters, &c->h_iters, NB * PM, (void**)&d.iters},
@@ -628,15 +687,19 @@ int sme_estimate_sequence_host(sme_ctx* c, const uint8_t* luma, const uint8_t* a
     };
     for (Opt& o : opts) {
         if (!o.host) continue;
+        void* in_place = o.buf == &c->h_sse ? nullptr : mapped_host(o.host);
+        o.copy = in_place == nullptr;
+        if (in_place) {
+            *o.dev = in_place;
+            continue;
+        }
         if ((rc = ensure(*o.buf, o.bytes))) return rc;
         *o.dev = o.buf->p;
     }
-    rc = run_sequence(c, (const uint8_t*)c->h_luma.p, (const uint8_t*)c->h_alpha.p, n_frames, dtmp, dseed, &d);
+    rc = run_sequence(c, (const uint8_t*)c->h_luma.p, dalpha, n_frames, dtmp, dseed, &d, luma_ready);
     if (rc) return rc;
-    if (cudaMemcpyAsync(out->mv, d.mv, NB * PM * sizeof(sme_mv), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return SME_ERR_CUDA;
     for (Opt& o : opts)
-        if (o.host && cudaMemcpyAsync(o.host, *o.dev, o.bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        if (o.host && o.copy && cudaMemcpyAsync(o.host, *o.dev, o.bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return SME_ERR_CUDA;
     return sme_synchronize(c);
 }

@@ -316,15 +316,27 @@ def test_compensate_given_field(sme, h):
     est.close()
 
 
-def test_host_buffers_match_device(sme):
+@pytest.mark.parametrize("pin_in,pin_out", [(True, False), (False, False), (True, True), (False, True)])
+def test_host_buffers_match_device(sme, pin_in, pin_out):
+    """Pinned inputs are read in place (alpha) or copied on a second stream
+    (luma), pinned outputs written in place; pageable ones are staged.  Every
+    combination gives the device results, twice in a row on one context."""
     seq = synth.cif_sequence(seed=1002, frames=6)
     est = sme.Estimator(352, 288, search_range=16, subpel=2)
-    dev = est.estimate_sequence(cuda(seq.luma), cuda(seq.alpha[0]))
-    hl = torch.from_numpy(seq.luma).pin_memory()
-    ha = torch.from_numpy(seq.alpha[0]).pin_memory()
-    host = est.estimate_sequence_host(hl, ha)
-    for k in ("mv", "cost", "disp", "iters", "npos", "mb_class", "sse"):
-        assert torch.equal(host[k], dev[k].cpu()), k
+    want = ("cost", "disp", "iters", "npos", "mb_class", "sse_mb", "sse", "pred")
+    dev = est.estimate_sequence(cuda(seq.luma), cuda(seq.alpha[0]), want=want)
+    hl, ha = torch.from_numpy(seq.luma), torch.from_numpy(seq.alpha[0])
+    if pin_in:
+        hl, ha = hl.pin_memory(), ha.pin_memory()
+    out = est._alloc_outputs(5, want, "cpu")
+    if pin_out:
+        out = {k: v.pin_memory() for k, v in out.items()}
+    for _ in range(2):
+        for v in out.values():
+            v.fill_(7)
+        host = est.estimate_sequence_host(hl, ha, want=want, out=out)
+        for k in ("mv",) + want:
+            assert torch.equal(host[k], dev[k].cpu()), k
     est.close()
 
 

@@ -1813,7 +1813,30 @@ __device__ __forceinline__ void prs_blocks(const Method& m, const uint8_t* win, 
         const int qx = clampi(s.dx + (int)roundf(__fmul_rn((float)h, ux_)), V.lox, V.hix);
         const int qy = clampi(s.dy + (int)roundf(__fmul_rn((float)h, uy_)), V.loy, V.hiy);
         const bool qmove = qx != s.dx || qy != s.dy;
-        const P8 q8 = ref8(win, pitch, lx, ly, qx, qy, h);
+        // The lane's samples at the 3x3 neighbourhood of its block's d (one
+        // staged read when d is inside V, so that clamping is the identity;
+        // clamped one by one on the edge of V), and at the proposal q.
+        P8 nb9[9];
+        const bool inner = s.dx > V.lox && s.dx < V.hix && s.dy > V.loy && s.dy < V.hiy;
+        if (inner) {
+            block3x3(win, pitch, lx, ly, s.dx, s.dy, h, nb9);
+        } else {
+#pragma unroll
+            for (int n = 0; n < 9; ++n)
+                nb9[n] = n == 4 ? s.r8
+                                : ref8(win, pitch, lx, ly, clampi(s.dx + n % 3 - 1, V.lox, V.hix),
+                                       clampi(s.dy + n / 3 - 1, V.loy, V.hiy), h);
+        }
+        P8 q8;
+        if (abs(qx - s.dx) <= 1 && abs(qy - s.dy) <= 1 && (inner || !qmove)) {
+            const int qi = (qy - s.dy + 1) * 3 + (qx - s.dx + 1);
+            q8 = nb9[4];
+#pragma unroll
+            for (int n = 0; n < 9; ++n)
+                if (n == qi) q8 = nb9[n];
+        } else {
+            q8 = ref8(win, pitch, lx, ly, qx, qy, h);
+        }
         const unsigned cq = blk_sum(sad8(q8, c8));
         bool moved = false, need_nb = false;
         if (!s.done) {
@@ -1834,23 +1857,23 @@ __device__ __forceinline__ void prs_blocks(const Method& m, const uint8_t* win, 
             s.r8 = q8;
         }
         if (__any_sync(kFull, need_nb)) {
+            const int cx = s.dx, cy = s.dy;  // unchanged where need_nb
             unsigned bc = s.cost;
-            int bx = s.dx, by = s.dy;
+            int bx = cx, by = cy;
             P8 b8 = s.r8;
-#pragma unroll 1
-            for (int n = 1; n < 9; ++n) {
-                const int e = n < 5 ? n - 1 : n;  // 3x3 raster without its centre
-                const int ex = clampi(s.dx + e % 3 - 1, V.lox, V.hix), ey = clampi(s.dy + e / 3 - 1, V.loy, V.hiy);
-                const P8 e8 = ref8(win, pitch, lx, ly, ex, ey, h);
-                const unsigned ce = blk_sum(sad8(e8, c8));
-                if (need_nb && (ex != s.dx || ey != s.dy)) {
+#pragma unroll
+            for (int n = 0; n < 9; ++n) {
+                if (n == 4) continue;  // 3x3 raster without its centre
+                const int ex = clampi(cx + n % 3 - 1, V.lox, V.hix), ey = clampi(cy + n / 3 - 1, V.loy, V.hiy);
+                const unsigned ce = blk_sum(sad8(nb9[n], c8));
+                if (need_nb && (ex != cx || ey != cy)) {
                     if (first) blog[s.nlog] = pack_mv(ex, ey);
                     ++s.nlog;
                     if (ce < bc) {
                         bc = ce;
                         bx = ex;
                         by = ey;
-                        b8 = e8;
+                        b8 = nb9[n];
                     }
                 }
             }

@@ -1758,6 +1758,15 @@ __device__ __forceinline__ unsigned blk_sum(unsigned v)
     return v;
 }
 
+// Two block sums of values whose block totals stay below 2^16 (SADs of an
+// 8x8 block: at most 64 * 255), in one pass of shuffles.
+__device__ __forceinline__ void blk_sum2(unsigned a, unsigned b, unsigned& sa, unsigned& sb)
+{
+    const unsigned t = blk_sum(a | (b << 16));
+    sa = t & 0xffffu;
+    sb = t >> 16;
+}
+
 // Eq. 3 sums over the block's 64 pixels: the lane's 8 terms pairwise, then
 // rows pairwise (xor 2, 4, 8): the contiguous pairwise tree in block raster
 // order (FP32 addition is commutative, so both lanes of a pair agree).
@@ -1861,11 +1870,16 @@ __device__ __forceinline__ void prs_blocks(const Method& m, const uint8_t* win, 
             unsigned bc = s.cost;
             int bx = cx, by = cy;
             P8 b8 = s.r8;
+            unsigned sad9[9];
+            blk_sum2(sad8(nb9[0], c8), sad8(nb9[1], c8), sad9[0], sad9[1]);
+            blk_sum2(sad8(nb9[2], c8), sad8(nb9[3], c8), sad9[2], sad9[3]);
+            blk_sum2(sad8(nb9[5], c8), sad8(nb9[6], c8), sad9[5], sad9[6]);
+            blk_sum2(sad8(nb9[7], c8), sad8(nb9[8], c8), sad9[7], sad9[8]);
 #pragma unroll
             for (int n = 0; n < 9; ++n) {
                 if (n == 4) continue;  // 3x3 raster without its centre
                 const int ex = clampi(cx + n % 3 - 1, V.lox, V.hix), ey = clampi(cy + n / 3 - 1, V.loy, V.hiy);
-                const unsigned ce = blk_sum(sad8(nb9[n], c8));
+                const unsigned ce = sad9[n];
                 if (need_nb && (ex != cx || ey != cy)) {
                     if (first) blog[s.nlog] = pack_mv(ex, ey);
                     ++s.nlog;
@@ -1966,6 +1980,31 @@ __device__ __forceinline__ Blk4 opaque_blocks4(const Method& m, const uint8_t* w
                                                const P8& c8, const float (&ux)[8], const float (&uy)[8],
                                                const VRange& V, const int (&cand)[5], int* blog, int lane);
 
+// The four block searches of an opaque MB from the MB winner `key` (r8: the
+// lane's reference samples there).
+__device__ __forceinline__ Blk4 blocks_from_winner(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
+                                                   const P8& c8, const float (&ux)[8], const float (&uy)[8],
+                                                   const VRange& V, int key, const P8& r8, int* blog, int lane)
+{
+    Blk4 s;
+    s.iters = 0;
+    s.nlog = 4;
+    s.lastx = s.lasty = 0.0f;
+    s.done = false;
+    s.dx = mv_x(key);
+    s.dy = mv_y(key);
+    s.r8 = r8;
+    s.cost = blk_sum(sad8(r8, c8));
+    unsigned cx = 0, cy = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cx += ux[k] != 0.0f;
+        cy += uy[k] != 0.0f;
+    }
+    prs_blocks(m, win, pitch, lx, ly, c8, ux, uy, (int)blk_sum(cx), (int)blk_sum(cy), V, s, blog, lane);
+    return s;
+}
+
 // Fig. 1 at MB level (16x16 costs of the candidates A, B, C, T) and, on
 // opaque MBs, the block searches from the winner.  The candidates are in
 // cand[0..4); each block log starts with them.
@@ -2030,25 +2069,15 @@ __device__ __forceinline__ Blk4 opaque_blocks4(const Method& m, const uint8_t* w
             cost = sad[c];
             best = c;
         }
-    s.r8 = cs8[0];
-    s.dx = mv_x(cand[0]);
-    s.dy = mv_y(cand[0]);
+    P8 r8 = cs8[0];
+    int key = cand[0];
 #pragma unroll
     for (int c = 1; c < 4; ++c)
         if (c == best) {
-            s.r8 = cs8[c];
-            s.dx = mv_x(cand[c]);
-            s.dy = mv_y(cand[c]);
+            r8 = cs8[c];
+            key = cand[c];
         }
-    s.cost = blk_sum(sad8(s.r8, c8));
-    unsigned cx = 0, cy = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        cx += ux[k] != 0.0f;
-        cy += uy[k] != 0.0f;
-    }
-    prs_blocks(m, win, pitch, lx, ly, c8, ux, uy, (int)blk_sum(cx), (int)blk_sum(cy), V, s, blog, lane);
-    return s;
+    return blocks_from_winner(m, win, pitch, lx, ly, c8, ux, uy, V, key, r8, blog, lane);
 }
 
 // ============================== ME, per-MB warps, four vectors per MB ==
@@ -2148,17 +2177,50 @@ __device__ __forceinline__ bool me_one_mb4(const MeArgs& a, const Method& m, int
         key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + 4 * mb));
     if (lane < 4) key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
     bool res = dep < 0;
+    const uint32_t* pcur = sd->packed + (size_t)(k + rd) * H * sd->Wp;
+    const uint32_t* pref = sd->packed + (size_t)k * H * sd->Wp;
+    // Every candidate is costed (16x16 shape or texture) as soon as its
+    // vector arrives, so after the last arrival only its own cost is left.
+    unsigned costed = 0;
+    unsigned ccost[4] = {0u, 0u, 0u, 0u};
+    int ckey[4] = {0, 0, 0, 0};
+    P8 cs8[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cs8[c] = c8;
     unsigned long long t_start = 0;
     for (unsigned it = 0;; ++it) {
-        if (lane < 4 && !res) {
-            const unsigned long long w = ld_ready(src + dep);
-            if ((unsigned)(w >> 32) == L.epoch) {
-                const int kk = (int)(unsigned)w;
-                key = pack_mv(clampi(mv_x(kk), V.lox, V.hix), clampi(mv_y(kk), V.loy, V.hiy));
-                res = true;
+        unsigned long long w = 0;
+        if (lane < 4 && !res) w = ld_ready(src + dep);  // issued first: its latency overlaps the costing
+        const unsigned fresh = __ballot_sync(kFull, lane < 4 && res) & 0xfu & ~costed;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (fresh & (1u << c)) {
+                const int kc = __shfl_sync(kFull, key, c);
+                ckey[c] = kc;
+                bool dup = false;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (e != c && !dup && (costed & (1u << e)) && ckey[e] == kc) {
+                        ccost[c] = ccost[e];
+                        cs8[c] = cs8[e];
+                        dup = true;
+                    }
+                if (!dup) {
+                    if (cls == SME_BOUNDARY) {
+                        ccost[c] = shape_cost1(pcur, pref, sd->Wp, X0, Y0, kc, h, lane);
+                    } else {
+                        cs8[c] = ref8(win, pitch, lx, ly, mv_x(kc), mv_y(kc), h);
+                        ccost[c] = __reduce_add_sync(kFull, sad8(cs8[c], c8));
+                    }
+                }
+                costed |= 1u << c;
             }
+        if (costed == 0xfu) break;
+        if (lane < 4 && !res && (unsigned)(w >> 32) == L.epoch) {
+            const int kk = (int)(unsigned)w;
+            key = pack_mv(clampi(mv_x(kk), V.lox, V.hix), clampi(mv_y(kk), V.loy, V.hiy));
+            res = true;
         }
-        if (__all_sync(kFull, lane >= 4 || res)) break;
         if ((it & 15u) == 15u) {
             // Bounded wait: the launch's abort word, a time limit, an iteration cap.
             int give_up = 0;
@@ -2174,36 +2236,34 @@ __device__ __forceinline__ bool me_one_mb4(const MeArgs& a, const Method& m, int
             }
         }
     }
-    int cand[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) cand[c] = c < 4 ? __shfl_sync(kFull, key, c) : 0;
-    if (lane < 16) slog[(lane >> 2) * kMaxLog + (lane & 3)] = cand[lane & 3];
+    if (lane < 16) slog[(lane >> 2) * kMaxLog + (lane & 3)] = ckey[lane & 3];
     __syncwarp();
     int* blog = slog + blk_of(lane) * kMaxLog;
+    // first strict minimum in the order A, B, C, T
+    int bi = 0;
+#pragma unroll
+    for (int c = 1; c < 4; ++c)
+        if (ccost[c] < ccost[bi]) bi = c;
+    int bk = ckey[0];
+    P8 br8 = cs8[0];
+#pragma unroll
+    for (int c = 1; c < 4; ++c)
+        if (c == bi) {
+            bk = ckey[c];
+            br8 = cs8[c];
+        }
     Blk4 s4;
     if (cls == SME_BOUNDARY) {
-        const uint32_t* pcur = sd->packed + (size_t)(k + rd) * H * sd->Wp;
-        const uint32_t* pref = sd->packed + (size_t)k * H * sd->Wp;
-        unsigned sc[5];
-        shape_costs(pcur, pref, sd->Wp, X0, Y0, cand, 4, h, lane, sc);
-        int best = cand[0];
-        unsigned cost = sc[0];
-#pragma unroll
-        for (int c = 1; c < 4; ++c)
-            if (sc[c] < cost) {
-                cost = sc[c];
-                best = cand[c];
-            }
-        s4.dx = mv_x(best);
-        s4.dy = mv_y(best);
+        s4.dx = mv_x(bk);
+        s4.dy = mv_y(bk);
         s4.iters = 0;
         s4.nlog = 4;
         s4.lastx = s4.lasty = 0.0f;
         s4.done = true;
-        s4.cost = shape_quadrant_g(pcur, pref, sd->Wp, X0, Y0, best, h, lane);
+        s4.cost = shape_quadrant_g(pcur, pref, sd->Wp, X0, Y0, bk, h, lane);
         s4.r8 = ref8(win, pitch, lx, ly, s4.dx, s4.dy, h);
     } else {
-        s4 = opaque_blocks4(m, win, pitch, lx, ly, c8, ux, uy, V, cand, blog, lane);
+        s4 = blocks_from_winner(m, win, pitch, lx, ly, c8, ux, uy, V, bk, br8, blog, lane);
     }
     const int kb = pack_mv(s4.dx, s4.dy);
     L.publish(gid, __shfl_sync(kFull, kb, 0), __shfl_sync(kFull, kb, 1), __shfl_sync(kFull, kb, 16), lane);

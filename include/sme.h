@@ -205,7 +205,8 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     more shared memory than a cluster has;
  *     SME_SCHED_AUTO (default) -- chosen per workload.
  *   SME_OPT_PAIR_WARPS: warps (MB rows in flight) per CTA of the pair
- *     schedule, 1..16; 0 (default) = automatic.
+ *     schedule, 1..16 (at most 8 used with SME_OPT_PAIR_DIRECT); 0
+ *     (default) = automatic.
  *   SME_OPT_MB_CTAS_PER_SM: resident CTAs (8 MBs each) per SM of the per-MB
  *     schedule, 1..32, capped by occupancy; 0 (default) = as many as fit.
  *   SME_OPT_SPECULATE: 1 (default) = in the per-MB schedule, cost each

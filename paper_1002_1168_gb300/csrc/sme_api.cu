@@ -394,6 +394,7 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
         if (launch_me_cluster(c->m, a, C, c->cl_warps, helpers, c->stream) != cudaSuccess) return SME_ERR_CUDA;
     } else if (pair) {
         int nw = c->pair_warps > 0 ? c->pair_warps : std::min(kPairWarpsMax, g.MBH);
+        if (a.pair_direct && !a.four_mv) nw = std::min(nw, 8);  // the direct instantiation's bound
         while (nw > 1 && me_pair_smem_bytes(c->m.S, nw, g.MBW, c->four_mv != 0) > (size_t)c->smem_optin) --nw;
         int per_sm = 0;
         if (me_pair_occupancy(c->m.S, nw, g.MBW, a.pair_direct != 0, a.four_mv != 0, &per_sm) != cudaSuccess ||
@@ -456,7 +457,7 @@ struct ExecCfg {
 const ExecCfg kTuneCandidates[] = {
     {kSchedMB, 0, 1, 1, 0, 1},       {kSchedMB, 0, 0, 1, 0, 1},       {kSchedMB, 0, 1, 0, 0, 1},
     {kSchedMB, 0, 0, 0, 0, 1},       {kSchedPair, 4, 0, 0, 0, 1},     {kSchedPair, 8, 0, 0, 0, 1},
-    {kSchedPair, 16, 0, 0, 0, 1},    {kSchedPair, 4, 0, 0, 0, 0},     {kSchedPair, 8, 0, 0, 0, 0},
+    {kSchedPair, 4, 0, 0, 0, 0},     {kSchedPair, 8, 0, 0, 0, 0},
     {kSchedPair, 16, 0, 0, 0, 0},    {kSchedCluster, 0, 0, 1, 16, 1}, {kSchedCluster, 0, 0, 0, 16, 1},
     {kSchedCluster, 0, 0, 1, 8, 1},
 };
@@ -1074,6 +1075,7 @@ int batch_enqueue(sme_batch* b, cudaStream_t s)
     a.timeout_ns = kDefaultTimeoutNs;
     if (b->cfg.schedule == kSchedPair) {
         int nw = b->cfg.pair_warps > 0 ? b->cfg.pair_warps : kPairWarpsMax;
+        if (a.pair_direct) nw = std::min(nw, 8);  // the direct instantiation's bound
         while (nw > 1 && me_pair_smem_bytes(b->m.S, nw, b->mbw_max) > (size_t)b->smem_optin) --nw;
         int per_sm = 0;
         if (me_pair_occupancy(b->m.S, nw, b->mbw_max, a.pair_direct != 0, false, &per_sm) != cudaSuccess || per_sm < 1)

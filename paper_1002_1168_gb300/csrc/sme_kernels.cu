@@ -2302,12 +2302,14 @@ __global__ void __launch_bounds__(32 * kMeWarps) me4_kernel(const MeArgs a)
 // are finished by transparent_run and only the other MBs are staged by TMA;
 // otherwise every MB is staged and classified from its staged BAB.  Two
 // instantiations rather than a runtime switch, so that each keeps only its
-// own code (the kernel is at its register limit).  kFourMv: four vectors per
+// own code.  The direct one is bounded at 8 warps per CTA, which lets it keep
+// its state in registers (at 16 warps it spilled and ran 18 % slower on
+// 3840x2160 VOPs).  kFourMv: four vectors per
 // MB (Sec. 3.2, 8x8 blocks; staged only): A is block 1 of the left MB (the
 // warp's previous MB), B and C block 2 of the MBs above (the row slots hold
 // block 2), T block 0 of the previous pair (the ready words hold block 0).
 template <bool kDirect, bool kFourMv>
-__global__ void __launch_bounds__(32 * kPairWarpsMax) me_pair_kernel(const MeArgs a, const __grid_constant__ PairMaps maps0)
+__global__ void __launch_bounds__(32 * (kDirect ? 8 : kPairWarpsMax)) me_pair_kernel(const MeArgs a, const __grid_constant__ PairMaps maps0)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);

@@ -207,13 +207,14 @@ def train_and_evaluate(n_pairs=200, steps=600, eval_luma=None, eval_alpha=None, 
 
 
 class LearnedBatch:
-    """The learned-seeded form of a batch.  For every luma sequence: the
-    classes of each of its VOPs, the features of all its pairs and one sparse
-    forward for the MBs visible in any of its VOPs (the VOPs of a sequence
-    share features, hence seeds); then every VOP in one persistent launch
-    (sme_batch) with those seeds.  The classification and network launches of
-    all sequences are captured in one CUDA graph, replayed before the batch's
-    own graph, on one stream.
+    """The learned-seeded form of a batch.  Sequences of one frame size are
+    gathered into chunks (as many as the network's capacity holds): per chunk
+    the classes of every VOP's current frames, the features of every pair and
+    one sparse forward for the MBs visible in any VOP of any of its sequences
+    (the VOPs of a sequence share features, hence seeds); then every VOP in
+    one persistent launch (sme_batch) with those seeds.  The classification
+    and network launches are captured in one CUDA graph, replayed before the
+    batch's own graph, on one stream.
 
     groups: list of (luma [F, H, W] CUDA uint8, [alpha [F, H, W] CUDA uint8, ...])."""
 
@@ -224,35 +225,57 @@ class LearnedBatch:
         self.torch, self.net, self.subpel, self.rd = torch, net, subpel, ref_distance
         self.stream = torch.cuda.Stream()
         self.graph = None
-        self.items, self.est = [], {}
-        lumas, alphas, seeds_list = [], [], []
+        self.chunks, self.est = [], {}
+        rd = ref_distance
+        # chunks: consecutive sequences of one size while the network holds their cells
+        order = {}
+        for i, (luma, alist) in enumerate(groups):
+            order.setdefault(tuple(luma.shape[1:]), []).append(i)
+        seeds_of = {}
         with torch.cuda.stream(self.stream):
-            for luma, alist in groups:
-                F, H, W = luma.shape
-                P = F - ref_distance
+            for (H, W), idx in order.items():
                 if (W, H) not in self.est:
                     self.est[(W, H)] = sme.Estimator(W, H, search_range=search_range, subpel=subpel,
-                                                     ref_distance=ref_distance)
-                est = self.est[(W, H)]
-                cls = torch.empty((len(alist), F, est.M), dtype=torch.uint8, device=luma.device)
-                feat = torch.empty((P, H // 4, W // 4, 16), dtype=torch.int16, device=luma.device)
-                seeds = torch.zeros((P, est.M, 2), dtype=torch.float32, device=luma.device)
-                self.items.append((luma, alist, est, cls, feat, seeds))
+                                                     ref_distance=rd)
+                est, cells = self.est[(W, H)], (H // 4) * (W // 4)
+                todo = list(idx)
+                while todo:
+                    members, n = [], 0
+                    while todo and (not members or (n + groups[todo[0]][0].shape[0] - rd) * cells <= net.max_cells):
+                        members.append(todo.pop(0))
+                        n += groups[members[-1]][0].shape[0] - rd
+                    V = max(len(groups[i][1]) for i in members)
+                    dev = groups[members[0]][0].device
+                    cls = torch.zeros((V, n, est.M), dtype=torch.uint8, device=dev)  # 0: transparent
+                    feat = torch.empty((n, H // 4, W // 4, 16), dtype=torch.int16, device=dev)
+                    seeds = torch.zeros((n, est.M, 2), dtype=torch.float32, device=dev)
+                    items, off = [], 0
+                    for i in members:
+                        luma, alist = groups[i]
+                        P = luma.shape[0] - rd
+                        items.append((luma, alist, off, P))
+                        seeds_of[i] = seeds[off:off + P]
+                        off += P
+                    self.chunks.append((est, items, cls, feat, seeds))
+            lumas, alphas, seeds_list = [], [], []
+            for i, (luma, alist) in enumerate(groups):  # VOP order = the caller's order
                 for a in alist:
                     lumas.append(luma)
                     alphas.append(a)
-                    seeds_list.append(seeds)
+                    seeds_list.append(seeds_of[i])
             self.batch = sme.Batch(lumas, alphas, search_range=search_range, subpel=subpel,
                                    ref_distance=ref_distance, want=want, seed_list=seeds_list)
         self.outputs = self.batch.outputs
         self.seeds = seeds_list
 
     def _seed_pass(self):
-        for luma, alist, est, cls, feat, seeds in self.items:
-            for k, a in enumerate(alist):
-                est.classify(a, want_packed=False, out=cls[k], sync=False)
-            self.net.features(luma, 0, self.rd, subpel=self.subpel, n_pairs=feat.shape[0], out=feat)
-            self.net.forward_active(feat, cls[:, self.rd:], out=seeds)
+        rd = self.rd
+        for est, items, cls, feat, seeds in self.chunks:
+            for luma, alist, off, P in items:
+                for k, a in enumerate(alist):  # classes of the current frames rd .. F-1
+                    est.classify(a[rd:], want_packed=False, out=cls[k, off:off + P], sync=False)
+                self.net.features(luma, 0, rd, subpel=self.subpel, n_pairs=P, out=feat[off:off + P])
+            self.net.forward_active(feat, cls, out=seeds)
 
     def tune(self, trials=3):
         """Seeds once, the batch's autotuner, then the capture of the seed pass."""

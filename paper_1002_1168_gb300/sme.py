@@ -459,6 +459,7 @@ class SeedNet:
 
         self.torch = torch
         lib = _lib()
+        self.max_cells = int(max_cells)
         self.n_params = lib.sme_seednet_param_count()
         h = C.c_void_p()
         _check(lib.sme_seednet_create(C.byref(h), int(max_cells), C.c_void_p(torch.cuda.current_stream().cuda_stream)),

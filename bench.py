@@ -558,7 +558,8 @@ def measure_four_mv(sme, torch, seq, luma, alpha, flush, steps):
                  ("sse", "sse"), ("disp", "disp")])
     cls = g["mb_class"]
     M = (W // 16) * (H // 16)
-    return {"mb_per_s": P * M / (ms / 1e3), "ms_per_step": ms, "config": {"pair_warps": cfg["pair_warps"]},
+    return {"mb_per_s": P * M / (ms / 1e3), "ms_per_step": ms,
+            "config": {"schedule": cfg["schedule"], "pair_warps": cfg["pair_warps"]},
             "psnr_db_mean": float(np.mean([sme.psnr(int(x), W, H) for x in g["sse"].view(np.uint64)])),
             "iters_per_opaque_block": float(g["iters"][cls == 1].mean()),
             "positions_per_block": float(g["npos"][cls > 0].mean()),

@@ -957,6 +957,7 @@ int sme_autotune(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_fr
     float best = -1.0f;
     ExecCfg pick = {c->schedule, c->pair_warps, c->mb_ctas_per_sm, c->speculate, c->cluster, c->pair_direct};
     for (const ExecCfg& e : kTuneCandidates) {
+        if (c->four_mv && e.schedule == kSchedCluster) continue;  // the mode runs those on the per-MB schedule
         c->schedule = e.schedule;
         c->pair_warps = e.pair_warps;
         c->mb_ctas_per_sm = e.mb_ctas_per_sm;

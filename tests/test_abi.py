@@ -69,3 +69,22 @@ def test_null_context_is_an_argument_error(lib):
     assert lib.sme_synchronize(None) == 1
     assert lib.sme_estimate(None, None) == 1
     assert lib.sme_debug_set_fault(None, 0, 0) == 1
+
+
+def header_enums():
+    """name -> value of every `SME_* = n` enumerator in include/sme.h."""
+    text = open(os.path.join(ROOT, "include", "sme.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(SME_[A-Z_0-9]+)\s*=\s*(\d+)", text)}
+
+
+def test_binding_constants_match_the_header():
+    """The binding's option, schedule and class constants are the header's."""
+    enums = header_enums()
+    names = [n for n in dir(sme) if n.startswith("SME_OPT_")]
+    assert len(names) >= 8
+    for n in names:
+        assert getattr(sme, n) == enums[n], n
+    for name, value in sme.SCHEDULES.items():
+        assert enums[f"SME_SCHED_{name.upper()}"] == value, name
+    assert set(n for n in enums if n.startswith("SME_OPT_")) == set(names)

@@ -121,6 +121,12 @@ int sme_synchronize(sme_ctx* ctx);
  *            (at least one, rows padded to a multiple of 4 words). */
 int sme_classify(sme_ctx* ctx, const uint8_t* alpha, int n_frames, uint8_t* mb_class,
                  uint32_t* packed);
+/* Fig. 1 Block_Type of n frames gathered from anywhere, in one launch:
+ * frames is a DEVICE array of n pointers to [height][width] alpha planes of
+ * the context's size (each 16-byte aligned; a NULL entry stands for an empty
+ * plane, every MB transparent); mb_class [n][M] (device out).  SME_ERR_ARG on
+ * bad arguments. */
+int sme_classify_table(sme_ctx* ctx, const uint8_t* const* frames, int n, uint8_t* mb_class);
 
 /* Words per row of the packed alpha layout above. */
 int sme_packed_words(int width);
@@ -374,6 +380,12 @@ int sme_seednet_get_params(sme_seednet* net, float* params /* host */);
 int sme_seednet_features(sme_seednet* net, const uint8_t* luma, int width, int height, int ref_frame,
                          int cur_frame, int n_pairs, const sme_mv* temporal /* [M] device or NULL */,
                          int subpel, uint16_t* feat);
+/* The same features for n_pairs pairs gathered from anywhere, in one launch:
+ * frames is a DEVICE array [n_pairs][2] of pointers to [height][width] luma
+ * frames (reference, current; each 4-byte aligned); feat as above (no
+ * temporal input). */
+int sme_seednet_features_table(sme_seednet* net, const uint8_t* const* frames, int n_pairs, int width,
+                               int height, int subpel, uint16_t* feat);
 int sme_seednet_forward(sme_seednet* net, const uint16_t* feat, int n, int width, int height, float* seeds,
                         float* out_cells);
 int sme_seednet_forward_active(sme_seednet* net, const uint16_t* feat, int n, int width, int height,

@@ -612,6 +612,16 @@ int sme_classify(sme_ctx* c, const uint8_t* alpha, int n_frames, uint8_t* mb_cla
     return cuda_status(launch_classify(c->g, ca, c->stream));
 }
 
+int sme_classify_table(sme_ctx* c, const uint8_t* const* frames, int n, uint8_t* mb_class)
+{
+    if (!c || !frames || !mb_class || n < 1 || n > 65535) return SME_ERR_ARG;
+    ClassifyArgs ca{};
+    ca.frames = frames;
+    ca.n_frames = n;
+    ca.cls = mb_class;
+    return cuda_status(launch_classify(c->g, ca, c->stream));
+}
+
 int sme_estimate_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_frames,
                           const sme_mv* temporal_in, const float* seed, const sme_outputs* out)
 {

@@ -74,6 +74,7 @@ struct SeqDesc {
 
 struct ClassifyArgs {
     const uint8_t* alpha;
+    const uint8_t* const* frames;  // when non-null: frame f is frames[f] (NULL: an empty plane)
     int n_frames;
     uint8_t* cls;        // [F][M]
     uint32_t* packed;    // [F][H][Wp]

@@ -539,7 +539,12 @@ __global__ void __launch_bounds__(256) classify_pack_kernel(const Geom g, const 
     for (int i = tid; i < g.MBW; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     const size_t FS = (size_t)g.W * g.H;
-    const uint8_t* al = a.alpha + (size_t)f * FS + (size_t)v * 16 * g.W;
+    const uint8_t* fr = a.frames ? a.frames[f] : a.alpha + (size_t)f * FS;
+    if (!fr) {  // an empty alpha plane: every MB transparent
+        for (int s = tid; s < g.MBW; s += blockDim.x) a.cls[(size_t)f * g.M + v * g.MBW + s] = SME_TRANSPARENT;
+        return;
+    }
+    const uint8_t* al = fr + (size_t)v * 16 * g.W;
     uint16_t* pk = a.packed ? reinterpret_cast<uint16_t*>(a.packed + ((size_t)f * g.H + v * 16) * g.Wp) : nullptr;
     const int segs = g.MBW, hw = 2 * g.Wp;  // 16-pixel segments per row; u16 slots per packed row
     for (int it = tid; it < 16 * hw; it += blockDim.x) {

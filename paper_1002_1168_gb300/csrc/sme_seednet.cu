@@ -58,8 +58,10 @@ __device__ __forceinline__ unsigned pack_bf2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 // Per 4x4 cell: current and reference mean luma (/255 - 0.5), their
 // difference, the temporal candidate of the cell's MB (pixels / 16).
 // Pair q of the launch (blockIdx.y) uses frames ref_f + q and cur_f + q.
-__global__ void features_kernel(const uint8_t* luma, int W, int H, int ref_f0, int cur_f0, const sme_mv* temporal,
-                                int subpel, __nv_bfloat16* out_all)
+// frames: when non-null, pair q reads frames[2q] (reference) and frames[2q + 1]
+// (current) instead of frames ref_f0 + q and cur_f0 + q of luma.
+__global__ void features_kernel(const uint8_t* luma, const uint8_t* const* frames, int W, int H, int ref_f0,
+                                int cur_f0, const sme_mv* temporal, int subpel, __nv_bfloat16* out_all)
 {
     const int Wc = W / 4, Hc = H / 4;
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -67,8 +69,10 @@ __global__ void features_kernel(const uint8_t* luma, int W, int H, int ref_f0, i
     const int q = blockIdx.y, ref_f = ref_f0 + q, cur_f = cur_f0 + q;
     const int ci = cell / Wc, cj = cell - ci * Wc;
     const size_t off = (size_t)(4 * ci) * W + 4 * cj;
-    const uint32_t* r = reinterpret_cast<const uint32_t*>(luma + (size_t)ref_f * W * H + off);
-    const uint32_t* c = reinterpret_cast<const uint32_t*>(luma + (size_t)cur_f * W * H + off);
+    const uint8_t* rf = frames ? frames[2 * q] : luma + (size_t)ref_f * W * H;
+    const uint8_t* cf = frames ? frames[2 * q + 1] : luma + (size_t)cur_f * W * H;
+    const uint32_t* r = reinterpret_cast<const uint32_t*>(rf + off);
+    const uint32_t* c = reinterpret_cast<const uint32_t*>(cf + off);
     unsigned sr = 0, sc = 0;  // exact byte sums of the 4 x 4 cell
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
@@ -942,7 +946,19 @@ int sme_seednet_features(sme_seednet* s, const uint8_t* luma, int width, int hei
         return SME_ERR_ARG;
     const int cells = (width / 4) * (height / 4);
     features_kernel<<<dim3((cells + 127) / 128, n_pairs), 128, 0, s->stream>>>(
-        luma, width, height, ref_frame, cur_frame, temporal, subpel, reinterpret_cast<__nv_bfloat16*>(feat));
+        luma, nullptr, width, height, ref_frame, cur_frame, temporal, subpel, reinterpret_cast<__nv_bfloat16*>(feat));
+    return cudaGetLastError() == cudaSuccess ? SME_OK : SME_ERR_CUDA;
+}
+
+int sme_seednet_features_table(sme_seednet* s, const uint8_t* const* frames, int n_pairs, int width, int height,
+                               int subpel, uint16_t* feat)
+{
+    if (!s || !frames || !feat || ((uintptr_t)feat & 15) || width % 16 || height % 16 || width <= 0 || height <= 0 ||
+        n_pairs < 1 || n_pairs > 65535 || (subpel != 1 && subpel != 2))
+        return SME_ERR_ARG;
+    const int cells = (width / 4) * (height / 4);
+    features_kernel<<<dim3((cells + 127) / 128, n_pairs), 128, 0, s->stream>>>(
+        nullptr, frames, width, height, 0, 0, nullptr, subpel, reinterpret_cast<__nv_bfloat16*>(feat));
     return cudaGetLastError() == cudaSuccess ? SME_OK : SME_ERR_CUDA;
 }
 

@@ -209,7 +209,8 @@ def train_and_evaluate(n_pairs=200, steps=600, eval_luma=None, eval_alpha=None, 
 class LearnedBatch:
     """The learned-seeded form of a batch.  Sequences of one frame size are
     gathered into chunks (as many as the network's capacity holds): per chunk
-    the classes of every VOP's current frames, the features of every pair and
+    one classification launch over the current frames of every VOP, one
+    features launch over every pair (both reading frame-address tables) and
     one sparse forward for the MBs visible in any VOP of any of its sequences
     (the VOPs of a sequence share features, hence seeds); then every VOP in
     one persistent launch (sme_batch) with those seeds.  The classification
@@ -246,17 +247,28 @@ class LearnedBatch:
                         n += groups[members[-1]][0].shape[0] - rd
                     V = max(len(groups[i][1]) for i in members)
                     dev = groups[members[0]][0].device
-                    cls = torch.zeros((V, n, est.M), dtype=torch.uint8, device=dev)  # 0: transparent
+                    cls = torch.zeros((V, n, est.M), dtype=torch.uint8, device=dev)
                     feat = torch.empty((n, H // 4, W // 4, 16), dtype=torch.int16, device=dev)
                     seeds = torch.zeros((n, est.M, 2), dtype=torch.float32, device=dev)
-                    items, off = [], 0
+                    # frame-address tables: class map row (VOP j, pair i) <- the current alpha
+                    # frame of pair i (0: the sequence has no VOP j, an empty plane); feature
+                    # row i <- the pair's reference and current luma frames
+                    FS = H * W
+                    cls_ptr = [[0] * n for _ in range(V)]
+                    feat_ptr = []
+                    off = 0
                     for i in members:
                         luma, alist = groups[i]
                         P = luma.shape[0] - rd
-                        items.append((luma, alist, off, P))
+                        for p in range(P):
+                            for j, a in enumerate(alist):
+                                cls_ptr[j][off + p] = a.data_ptr() + (p + rd) * FS
+                            feat_ptr.append((luma.data_ptr() + p * FS, luma.data_ptr() + (p + rd) * FS))
                         seeds_of[i] = seeds[off:off + P]
                         off += P
-                    self.chunks.append((est, items, cls, feat, seeds))
+                    cls_tab = torch.tensor(cls_ptr, dtype=torch.int64, device=dev).reshape(-1)
+                    feat_tab = torch.tensor(feat_ptr, dtype=torch.int64, device=dev)
+                    self.chunks.append((est, cls, feat, seeds, cls_tab, feat_tab, W, H))
             lumas, alphas, seeds_list = [], [], []
             for i, (luma, alist) in enumerate(groups):  # VOP order = the caller's order
                 for a in alist:
@@ -269,12 +281,9 @@ class LearnedBatch:
         self.seeds = seeds_list
 
     def _seed_pass(self):
-        rd = self.rd
-        for est, items, cls, feat, seeds in self.chunks:
-            for luma, alist, off, P in items:
-                for k, a in enumerate(alist):  # classes of the current frames rd .. F-1
-                    est.classify(a[rd:], want_packed=False, out=cls[k, off:off + P], sync=False)
-                self.net.features(luma, 0, rd, subpel=self.subpel, n_pairs=P, out=feat[off:off + P])
+        for est, cls, feat, seeds, cls_tab, feat_tab, W, H in self.chunks:
+            est.classify_table(cls_tab, out=cls.view(-1, est.M), sync=False)
+            self.net.features_table(feat_tab, W, H, subpel=self.subpel, out=feat)
             self.net.forward_active(feat, cls, out=seeds)
 
     def tune(self, trials=3):

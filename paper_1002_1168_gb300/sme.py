@@ -28,7 +28,7 @@ STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4
 # Every entry point declared in include/sme.h.
 EXPORTS = [
     "sme_default_params", "sme_strerror", "sme_create", "sme_destroy", "sme_set_stream",
-    "sme_synchronize", "sme_classify", "sme_packed_words", "sme_estimate_sequence",
+    "sme_synchronize", "sme_classify", "sme_classify_table", "sme_packed_words", "sme_estimate_sequence",
     "sme_estimate_sequence_host", "sme_set_reference", "sme_set_current", "sme_estimate",
     "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field",
     "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
@@ -36,7 +36,8 @@ EXPORTS = [
     "sme_full_search",
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
-    "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_forward",
+    "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_features_table",
+    "sme_seednet_forward",
     "sme_seednet_forward_active", "sme_seednet_set_stream", "sme_seednet_synchronize",
     "sme_seednet_gradients", "sme_seednet_train_step", "sme_debug_set_fault",
 ]
@@ -253,6 +254,18 @@ class Estimator:
                                                _ptr(temporal_in), _ptr(seed), C.byref(st))
         _check(rc, "sme_estimate_sequence_host")
         return out
+
+    def classify_table(self, frames, out=None, sync=True):
+        """MB classes [n, M] uint8 of the alpha planes whose device addresses
+        are in frames (int64 CUDA tensor [n]; 0 = an empty plane), in one launch."""
+        t = self.torch
+        n = frames.numel()
+        assert frames.is_cuda and frames.dtype == t.int64 and frames.is_contiguous()
+        cls = out if out is not None else t.empty((n, self.M), dtype=t.uint8, device=frames.device)
+        _check(_lib().sme_classify_table(self._bind(), _ptr(frames), n, _ptr(cls)), "sme_classify_table")
+        if sync:
+            self.synchronize()
+        return cls
 
     def classify(self, alpha, want_packed=True, out=None, sync=True):
         """MB classes [F, M] uint8 (into out if given) and, optionally, the
@@ -495,6 +508,19 @@ class SeedNet:
             out = t.empty(shape, dtype=t.int16, device=luma.device)
         _check(_lib().sme_seednet_features(self._bind(), _ptr(luma), W, H, int(ref_frame), int(cur_frame), int(n_pairs),
                                            _ptr(temporal), int(subpel), _ptr(out)), "sme_seednet_features")
+        return out
+
+    def features_table(self, frames, width, height, subpel=2, out=None):
+        """Input grids of the pairs whose (reference, current) luma frame
+        addresses are in frames (int64 CUDA tensor [n, 2]), in one launch:
+        [n, H/4, W/4, 16]."""
+        t = self.torch
+        n = frames.shape[0]
+        assert frames.is_cuda and frames.dtype == t.int64 and frames.is_contiguous() and frames.shape[1] == 2
+        if out is None:
+            out = t.empty((n, height // 4, width // 4, 16), dtype=t.int16, device=frames.device)
+        _check(_lib().sme_seednet_features_table(self._bind(), _ptr(frames), n, width, height, int(subpel),
+                                                 _ptr(out)), "sme_seednet_features_table")
         return out
 
     def forward(self, feat, want_cells=False):

@@ -63,6 +63,34 @@ def test_features_batched_pairs_match_single(sme):
     net.close()
 
 
+def test_table_launches_equal_per_sequence_launches(sme):
+    """Classes and features gathered through frame-address tables (frames of
+    two sequences in any order, empty planes for missing VOPs) equal the
+    per-sequence launches bit for bit."""
+    s1 = synth.cif_sequence(seed=1002, frames=4)
+    s2 = synth.cif_sequence(seed=1009, frames=3)
+    l1, l2 = torch.from_numpy(s1.luma).cuda(), torch.from_numpy(s2.luma).cuda()
+    a1, a2 = torch.from_numpy(s1.alpha[0]).cuda(), torch.from_numpy(s2.alpha[0]).cuda()
+    FS = 352 * 288
+    est = sme.Estimator(352, 288)
+    tab = torch.tensor([a2.data_ptr() + 2 * FS, 0, a1.data_ptr() + 1 * FS, a1.data_ptr() + 3 * FS],
+                       dtype=torch.int64, device="cuda")
+    got = est.classify_table(tab).cpu()
+    c1, _ = est.classify(a1, want_packed=False)
+    c2, _ = est.classify(a2, want_packed=False)
+    assert torch.equal(got[0], c2[2].cpu()) and torch.equal(got[2], c1[1].cpu()) and torch.equal(got[3], c1[3].cpu())
+    assert not got[1].any()  # an empty plane: every MB transparent
+    net = sme.SeedNet(max_cells=3 * 88 * 72)
+    ftab = torch.tensor([[l1.data_ptr(), l1.data_ptr() + 2 * FS], [l2.data_ptr() + FS, l2.data_ptr() + 2 * FS],
+                         [l1.data_ptr() + 3 * FS, l1.data_ptr()]], dtype=torch.int64, device="cuda")
+    many = net.features_table(ftab, 352, 288, subpel=2).cpu()
+    assert torch.equal(many[0], net.features(l1, 0, 2, subpel=2).cpu())
+    assert torch.equal(many[1], net.features(l2, 1, 2, subpel=2).cpu())
+    assert torch.equal(many[2], net.features(l1, 3, 0, subpel=2).cpu())
+    net.close()
+    est.close()
+
+
 def test_forward_active_equals_dense(sme):
     # the layers run only near non-transparent MBs; their seeds are those of
     # the dense pass bit for bit, transparent MBs get (0, 0)

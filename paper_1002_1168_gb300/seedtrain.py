@@ -206,6 +206,32 @@ def train_and_evaluate(n_pairs=200, steps=600, eval_luma=None, eval_alpha=None, 
     return report, raw
 
 
+def chunk_plan(shapes, max_cells, ref_distance=1):
+    """How LearnedBatch groups sequences for the seed network (host logic only).
+
+    shapes: per sequence (F, H, W, n_vops).  Sequences of one frame size, in
+    the caller's order, go into consecutive chunks while the chunk's pairs'
+    cells fit the network (max_cells); a sequence larger than that gets a
+    chunk of its own.  Returns [(H, W, [(sequence, pair offset, pairs)], pairs,
+    VOPs)] with sizes in the order they first appear."""
+    order = {}
+    for i, (F, H, W, _) in enumerate(shapes):
+        order.setdefault((H, W), []).append(i)
+    plan = []
+    for (H, W), idx in order.items():
+        cells = (H // 4) * (W // 4)
+        todo = list(idx)
+        while todo:
+            members, n = [], 0
+            while todo and (not members or (n + shapes[todo[0]][0] - ref_distance) * cells <= max_cells):
+                i = todo.pop(0)
+                P = shapes[i][0] - ref_distance
+                members.append((i, n, P))
+                n += P
+            plan.append((H, W, members, n, max(shapes[i][3] for i, _, _ in members)))
+    return plan
+
+
 class LearnedBatch:
     """The learned-seeded form of a batch.  Sequences of one frame size are
     gathered into chunks (as many as the network's capacity holds): per chunk
@@ -228,47 +254,34 @@ class LearnedBatch:
         self.graph = None
         self.chunks, self.est = [], {}
         rd = ref_distance
-        # chunks: consecutive sequences of one size while the network holds their cells
-        order = {}
-        for i, (luma, alist) in enumerate(groups):
-            order.setdefault(tuple(luma.shape[1:]), []).append(i)
+        plan = chunk_plan([tuple(luma.shape) + (len(alist),) for luma, alist in groups], net.max_cells, rd)
         seeds_of = {}
         with torch.cuda.stream(self.stream):
-            for (H, W), idx in order.items():
+            for H, W, members, n, V in plan:
                 if (W, H) not in self.est:
                     self.est[(W, H)] = sme.Estimator(W, H, search_range=search_range, subpel=subpel,
                                                      ref_distance=rd)
-                est, cells = self.est[(W, H)], (H // 4) * (W // 4)
-                todo = list(idx)
-                while todo:
-                    members, n = [], 0
-                    while todo and (not members or (n + groups[todo[0]][0].shape[0] - rd) * cells <= net.max_cells):
-                        members.append(todo.pop(0))
-                        n += groups[members[-1]][0].shape[0] - rd
-                    V = max(len(groups[i][1]) for i in members)
-                    dev = groups[members[0]][0].device
-                    cls = torch.zeros((V, n, est.M), dtype=torch.uint8, device=dev)
-                    feat = torch.empty((n, H // 4, W // 4, 16), dtype=torch.int16, device=dev)
-                    seeds = torch.zeros((n, est.M, 2), dtype=torch.float32, device=dev)
-                    # frame-address tables: class map row (VOP j, pair i) <- the current alpha
-                    # frame of pair i (0: the sequence has no VOP j, an empty plane); feature
-                    # row i <- the pair's reference and current luma frames
-                    FS = H * W
-                    cls_ptr = [[0] * n for _ in range(V)]
-                    feat_ptr = []
-                    off = 0
-                    for i in members:
-                        luma, alist = groups[i]
-                        P = luma.shape[0] - rd
-                        for p in range(P):
-                            for j, a in enumerate(alist):
-                                cls_ptr[j][off + p] = a.data_ptr() + (p + rd) * FS
-                            feat_ptr.append((luma.data_ptr() + p * FS, luma.data_ptr() + (p + rd) * FS))
-                        seeds_of[i] = seeds[off:off + P]
-                        off += P
-                    cls_tab = torch.tensor(cls_ptr, dtype=torch.int64, device=dev).reshape(-1)
-                    feat_tab = torch.tensor(feat_ptr, dtype=torch.int64, device=dev)
-                    self.chunks.append((est, cls, feat, seeds, cls_tab, feat_tab, W, H))
+                est = self.est[(W, H)]
+                dev = groups[members[0][0]][0].device
+                cls = torch.zeros((V, n, est.M), dtype=torch.uint8, device=dev)
+                feat = torch.empty((n, H // 4, W // 4, 16), dtype=torch.int16, device=dev)
+                seeds = torch.zeros((n, est.M, 2), dtype=torch.float32, device=dev)
+                # frame-address tables: class map row (VOP j, pair i) <- the current alpha
+                # frame of pair i (0: the sequence has no VOP j, an empty plane); feature
+                # row i <- the pair's reference and current luma frames
+                FS = H * W
+                cls_ptr = [[0] * n for _ in range(V)]
+                feat_ptr = []
+                for i, off, P in members:
+                    luma, alist = groups[i]
+                    for p in range(P):
+                        for j, a in enumerate(alist):
+                            cls_ptr[j][off + p] = a.data_ptr() + (p + rd) * FS
+                        feat_ptr.append((luma.data_ptr() + p * FS, luma.data_ptr() + (p + rd) * FS))
+                    seeds_of[i] = seeds[off:off + P]
+                cls_tab = torch.tensor(cls_ptr, dtype=torch.int64, device=dev).reshape(-1)
+                feat_tab = torch.tensor(feat_ptr, dtype=torch.int64, device=dev)
+                self.chunks.append((est, cls, feat, seeds, cls_tab, feat_tab, W, H))
             lumas, alphas, seeds_list = [], [], []
             for i, (luma, alist) in enumerate(groups):  # VOP order = the caller's order
                 for a in alist:

@@ -137,7 +137,11 @@ int sme_packed_words(int width);
  *   luma, alpha  [n_frames][H][W] device
  *   temporal_in  [M] device or NULL: temporal candidates of pair 0
  *   seed         [P][M][2] device FP32 pixels or NULL: an extra candidate per
- *                MB evaluated after T (rounded to the MV grid, clamped to V)
+ *                MB evaluated after T (rounded to the MV grid, clamped to V).
+ *                Accepted only with max_iters <= 8 (SME_ERR_ARG otherwise):
+ *                an MB whose seed wins runs two pixel-recursive searches, and
+ *                the per-MB record of evaluated positions holds both only up
+ *                to that cap.
  *   out          outputs as described in sme_outputs (device pointers)
  * Needs n_frames > ref_distance. */
 int sme_estimate_sequence(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha, int n_frames,
@@ -426,8 +430,12 @@ int sme_profile_end(sme_ctx* ctx, int* calls, double* classify_ms, double* me_ms
  * example more than 221 CIF frames, or more than 11 frames of 1920x1088) returns
  * SME_ERR_SCRATCH before any GPU work.
  * The first call on each device looks up the array's device address (with
- * that device current) and should come before any stream capture.  The call
- * synchronises the stream and returns the device-side status of its own
+ * that device current) and should come before any stream capture; the
+ * address is kept for the life of the device's primary context, so the call
+ * must not be used again after a cudaDeviceReset in the same process.
+ * cuda_stream must belong to the current device (SME_ERR_ARG otherwise).
+ * Seeds are accepted with max_iters <= 8, as for sme_estimate_sequence.  The
+ * call synchronises the stream and returns the device-side status of its own
  * work.  All calls share the array: calls that overlap on the GPU (e.g. on
  * two streams, or from two threads) race and must be serialised by the
  * caller. */

@@ -296,6 +296,10 @@ int orc_estimate_pair(const orc_params* P, const uint8_t* ref, const uint8_t* cu
     const int W = P->width, H = P->height, h = P->subpel, S = P->search_range;
     if (W <= 0 || H <= 0 || W % 16 || H % 16) return 1;
     if (h != 1 && h != 2) return 1;
+    /* With seeds an MB may run two searches of up to 1 + 8 positions per
+     * step; the distinct-position count (a byte) is guaranteed below 256 only
+     * up to 8 steps (5 + 2 * 9 * 8 = 149), so seeded runs cap the steps there. */
+    if (seed && P->max_iters > 8) return 1;
     const int mbw = W / 16, mbh = H / 16;
     for (int v = 0; v < mbh; ++v)
         for (int u = 0; u < mbw; ++u) {

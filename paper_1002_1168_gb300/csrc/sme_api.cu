@@ -288,6 +288,7 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     const Geom& g = c->g;
     if (!luma || !alpha || !out || !out->mv) return SME_ERR_ARG;
     if (!aligned16(luma) || !aligned16(alpha)) return SME_ERR_ARG;
+    if (seed && c->m.K > kMaxSeededIters) return SME_ERR_ARG;  // the position log's bound
     const int rd = c->prm.ref_distance;
     if (F <= rd) return SME_ERR_ARG;
     const int P = F - rd;
@@ -633,6 +634,7 @@ int sme_estimate_sequence_host(sme_ctx* c, const uint8_t* luma, const uint8_t* a
                                const sme_mv* temporal_in, const float* seed, const sme_outputs* out)
 {
     if (!c || !luma || !alpha || !out || !out->mv) return SME_ERR_ARG;
+    if (seed && c->m.K > kMaxSeededIters) return SME_ERR_ARG;
     const Geom& g = c->g;
     const int rd = c->prm.ref_distance;
     if (n_frames <= rd) return SME_ERR_ARG;
@@ -1167,6 +1169,7 @@ int sme_batch_create(sme_batch** out, const sme_params* p, const sme_sequence* s
             return SME_ERR_SIZE;
         if (!x.luma || !x.alpha || !x.out.mv || x.n_frames <= rd || !aligned16(x.luma) || !aligned16(x.alpha))
             return SME_ERR_ARG;
+        if (x.seed && p->max_iters > kMaxSeededIters) return SME_ERR_ARG;
     }
     sme_batch* b = new (std::nothrow) sme_batch();
     if (!b) return SME_ERR_NOMEM;

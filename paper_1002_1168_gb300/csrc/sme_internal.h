@@ -17,6 +17,18 @@ constexpr int kMaxDim = 8192;
 // Evaluated-position log per MB: 5 block-recursive candidates plus, per
 // pixel-recursive iteration, one proposal and eight neighbours.
 constexpr int kMaxLog = 5 + 9 * kMaxIters;
+// With seeds, an opaque MB whose seed wins runs two pixel-recursive searches
+// into the same log (the seeded one and its plain fallback): 5 + 2 * 9 * K
+// entries.  Seeds are therefore accepted only up to this iteration cap, at
+// which both searches fit the log exactly.
+constexpr int kMaxSeededIters = 8;
+static_assert(5 + 2 * 9 * kMaxSeededIters <= kMaxLog, "seeded searches overrun the position log");
+// Four vectors per MB: one log per 8x8 block, the 4 MB candidates plus the
+// block's own steps.
+static_assert(4 + 9 * kMaxIters <= kMaxLog, "block searches overrun the position log");
+// The distinct-position count is stored in a byte and carried in the top 8
+// bits of one 32-bit warp reduction: it must stay below 256.
+static_assert(kMaxLog < 256, "distinct-position count does not fit its byte");
 constexpr long long kDefaultTimeoutNs = 1000000000LL;
 constexpr int kMeWarps = 8;        // warps (one MB each) per CTA of the per-MB ME kernel
 constexpr int kClusterWarps = 12;  // warps (one MB each) per CTA of the cluster schedule

@@ -16,7 +16,10 @@
 // use the array's name as a device address (on the host it is only a
 // stand-in), so the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and caches it; that first
-// call should therefore come before any stream capture.  All calls share the
+// call should therefore come before any stream capture.  The cached address
+// belongs to the device's primary context: a caller that resets the device
+// (cudaDeviceReset) must not call this entry point again in the same process,
+// because the array may then sit at another address.  All calls share the
 // array and it keeps the previous call's contents: every part that must start
 // at zero is cleared here, and calls that overlap on the GPU (for example on
 // two streams at once) race on it.
@@ -125,6 +128,7 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
     if (rc) return rc;
     if (!luma || !alpha || !out || !out->mv) return SME_ERR_ARG;
     if (((uintptr_t)luma & 15u) || ((uintptr_t)alpha & 15u)) return SME_ERR_ARG;
+    if (seed && p->max_iters > kMaxSeededIters) return SME_ERR_ARG;
     const int rd = p->ref_distance;
     if (n_frames <= rd) return SME_ERR_ARG;
 
@@ -159,6 +163,14 @@ extern "C" int sme_estimate_sequence_noalloc(const sme_params* p, const uint8_t*
 
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SME_ERR_CUDA;
+    // The array used is the current device's: a stream of another device
+    // would run the kernels there against this device's address.
+    int sdev = -1;
+    if (cudaStreamGetDevice((cudaStream_t)cuda_stream, &sdev) != cudaSuccess) {
+        cudaGetLastError();
+        return SME_ERR_ARG;
+    }
+    if (sdev != dev) return SME_ERR_ARG;
     void* base = nullptr;
     if ((rc = setup(dev, &base, &sms))) return rc;
     int per_sm = 0;

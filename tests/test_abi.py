@@ -88,3 +88,51 @@ def test_binding_constants_match_the_header():
     for name, value in sme.SCHEDULES.items():
         assert enums[f"SME_SCHED_{name.upper()}"] == value, name
     assert set(n for n in enums if n.startswith("SME_OPT_")) == set(names)
+
+
+def _fake_device_ptr(n=0):
+    """A 16-byte aligned non-null address: the argument checks below return
+    before any CUDA call, so nothing ever dereferences it."""
+    return C.c_void_p(0x10000 + 256 * n)
+
+
+def test_seeded_runs_above_eight_steps_are_rejected_before_touching_cuda(lib):
+    """Seeds make an MB run up to two pixel-recursive searches, whose position
+    record holds 5 + 2*9*8 entries: max_iters > 8 with seeds is an argument
+    error in the batch and the allocation-free entry points."""
+    p = sme.Params()
+    lib.sme_default_params(C.byref(p), 176, 144)
+    p.max_iters = 9
+    out = sme.Outputs(_fake_device_ptr(3), *([None] * 8))
+    seq = sme.Sequence(176, 144, 3, _fake_device_ptr(1), _fake_device_ptr(2), None, _fake_device_ptr(4), out)
+    h = C.c_void_p()
+    assert lib.sme_batch_create(C.byref(h), C.byref(p), C.byref(seq), 1, None) == 1
+    assert not h.value
+    assert lib.sme_estimate_sequence_noalloc(C.byref(p), _fake_device_ptr(1), _fake_device_ptr(2), 3, None,
+                                             _fake_device_ptr(4), C.byref(out), None) == 1
+
+
+@pytest.mark.parametrize("case", ["null_luma", "null_mv", "misaligned", "frames", "size", "scratch"])
+def test_noalloc_argument_errors_before_touching_cuda(lib, case):
+    """The allocation-free entry point validates everything before its first
+    CUDA call: null or misaligned pointers, too few frames, bad sizes, and
+    problems larger than its fixed scratch."""
+    p = sme.Params()
+    lib.sme_default_params(C.byref(p), 176, 144)
+    luma, alpha, frames = _fake_device_ptr(1), _fake_device_ptr(2), 3
+    out = sme.Outputs(_fake_device_ptr(3), *([None] * 8))
+    want = 1
+    if case == "null_luma":
+        luma = None
+    elif case == "null_mv":
+        out.mv = None
+    elif case == "misaligned":
+        alpha = C.c_void_p(alpha.value + 4)
+    elif case == "frames":
+        frames = 1
+    elif case == "size":
+        p.width, want = 170, 2
+    elif case == "scratch":
+        lib.sme_default_params(C.byref(p), 1920, 1088)
+        frames, want = 12, 8
+    assert lib.sme_estimate_sequence_noalloc(C.byref(p), luma, alpha, frames, None, None, C.byref(out), None) == want

@@ -403,6 +403,27 @@ def test_perfect_seed_recovers_translation():
             assert (o["mv"][m] == tgt).all() and o["cost"][m] == 0
 
 
+def test_seeded_runs_are_capped_at_eight_steps():
+    """An opaque MB whose seed wins runs two pixel-recursive searches (reading
+    c21), up to 5 + 2 * 9 * K evaluated positions; the count is a byte, which
+    holds it only up to K = 8 (149).  Seeded runs above that cap are refused;
+    unseeded ones keep the full cap of 16 steps (4 + 9 * 16 = 148)."""
+    rng = np.random.default_rng(21)
+    W = H = 96
+    luma = rng.integers(0, 256, (2, H, W), dtype=np.uint8)
+    a = np.full((2, H, W), 255, np.uint8)
+    seed = rng.normal(0, 8, ((W // 16) * (H // 16), 2)).astype(np.float32)
+    with pytest.raises(ValueError):
+        O.estimate_pair(O.OracleParams(W, H, 16, 2, max_iters=9), luma[0], luma[1], a[0], a[1], seed=seed)
+    with pytest.raises(ValueError):
+        O.estimate_sequence(O.OracleParams(W, H, 16, 2, max_iters=16), luma, a, seed=seed[None])
+    o = O.estimate_pair(O.OracleParams(W, H, 16, 2, max_iters=8), luma[0], luma[1], a[0], a[1], seed=seed)
+    assert int(o["npos"].max()) <= 5 + 2 * 9 * 8
+    assert int(o["iters"].max()) <= 8
+    o = O.estimate_pair(O.OracleParams(W, H, 16, 2, max_iters=16), luma[0], luma[1], a[0], a[1])
+    assert int(o["npos"].max()) <= 4 + 9 * 16
+
+
 # ------------------------------------- one MB, hand-derived search paths --
 def _middle_mb(ref, cur, h, seed_px=None):
     """48 x 48 frames with only the middle MB opaque (its neighbours are

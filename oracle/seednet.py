@@ -135,6 +135,27 @@ def backward(acts, params, dout, round_bf16=True):
     return grads
 
 
+ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
+
+
+def adam_step(p, g, m, v, t, lr):
+    """One Adam update of the flat FP32 master parameters (Kingma and Ba,
+    "Adam: A Method for Stochastic Optimization", Algorithm 1, with
+    bias-corrected moments), every operation in float32 as the GPU applies it:
+        m <- b1 m + (1 - b1) g,   v <- b2 v + (1 - b2) g^2,
+        p <- p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+    t counts the updates from 1.  Returns the new (p, m, v)."""
+    f32 = np.float32
+    p, g, m, v = (np.asarray(a, f32) for a in (p, g, m, v))
+    b1, b2, eps, lr = f32(ADAM_B1), f32(ADAM_B2), f32(ADAM_EPS), f32(lr)
+    m = b1 * m + (f32(1) - b1) * g
+    v = b2 * v + (f32(1) - b2) * g * g
+    c1 = f32(1) - b1 ** f32(t)
+    c2 = f32(1) - b2 ** f32(t)
+    p = p - lr * (m / c1) / (np.sqrt(v / c2) + eps)
+    return p, m, v
+
+
 def init_params(seed):
     """He-normal weights and zero biases from numpy PCG64; the last layer starts
     at one tenth of that scale."""

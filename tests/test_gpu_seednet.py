@@ -163,3 +163,37 @@ def test_training_reduces_loss(sme):
         last = net.train_step(xt, labels, mask, 1e-3, want_loss=True)
     assert last < 0.5 * first
     net.close()
+
+
+def test_adam_update_matches_oracle(sme):
+    """Two sme_seednet_train_step updates from fresh moments against the
+    oracle's FP32 Adam step, fed with the gradients the GPU computes at each
+    point (sme_seednet_gradients).  The weight gradients are summed with
+    float atomics, so a recomputed gradient can differ in its last bits: the
+    comparison is tight (0.1 % of the update plus a few ulps) where the
+    gradient is well above that noise, and bounded by the step size
+    elsewhere."""
+    rng, params, x, net, xt = _setup(sme, seed=8)
+    N, Hc, Wc, _ = x.shape
+    M = (Hc // 4) * (Wc // 4)
+    labels = torch.from_numpy(rng.normal(0, 2, (N, M, 2)).astype(np.float32)).cuda()
+    mask = torch.ones((N, M), dtype=torch.uint8, device="cuda")
+    lr = 1e-3
+    p = net.get_params()
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    prev = p.copy()
+    for t in (1, 2):
+        _, g = net.gradients(xt, labels, mask)
+        net.train_step(xt, labels, mask, lr)
+        got = net.get_params()
+        p, m, v = SN.adam_step(p, g, m, v, t, lr)
+        firm = np.abs(g) >= 1e-3 * np.abs(g).max()
+        assert firm.sum() > 1000  # thousands of parameters are tested tightly
+        tol = 4 * np.spacing(np.abs(p)) + 1e-3 * lr
+        bad = np.abs(got - p) > tol
+        assert not np.any(bad & firm), (t, np.flatnonzero(bad & firm)[:8])
+        assert np.all(np.abs(got - p) <= 3 * lr)
+        assert np.any(got != prev)  # the parameters moved
+        prev = got
+    net.close()

@@ -33,6 +33,22 @@ MUTANTS = [
     ("loss averaged over all MBs", "n = max(float(m.sum()), 1.0)", "n = float(m.size)"),
     ("pooling over one cell row", "s = out[..., :2].reshape(N, Hc // 4, 4, Wc // 4, 4, 2).mean(axis=(2, 4))",
      "s = out[..., :2].reshape(N, Hc // 4, 4, Wc // 4, 4, 2)[:, :, 0].mean(axis=3)"),
+    ("current and reference swapped", "x[..., 0] = c / 255.0 - 0.5\n    x[..., 1] = r / 255.0 - 0.5",
+     "x[..., 0] = r / 255.0 - 0.5\n    x[..., 1] = c / 255.0 - 0.5"),
+    ("feature offset missing", "x[..., 0] = c / 255.0 - 0.5", "x[..., 0] = c / 255.0"),
+    ("difference reversed", "x[..., 2] = (c - r) / 255.0", "x[..., 2] = (r - c) / 255.0"),
+    ("temporal channel scaled by 16 only", "/ (16.0 * subpel)", "/ 16.0"),
+    ("temporal channel scaled by 16 * h * h", "/ (16.0 * subpel)", "/ (16.0 * subpel * subpel)"),
+    ("temporal axes swapped", "x[..., 3] = np.repeat(np.repeat(t[..., 0], 4, 0), 4, 1)",
+     "x[..., 3] = np.repeat(np.repeat(t[..., 1], 4, 0), 4, 1)"),
+    ("cell mean over 2x2 pixels", "c = cur.astype(np.float64).reshape(Hc, 4, Wc, 4).mean(axis=(1, 3))",
+     "c = cur.astype(np.float64).reshape(Hc, 4, Wc, 4)[:, :2, :, :2].mean(axis=(1, 3))"),
+    ("Adam without bias correction", "p = p - lr * (m / c1) / (np.sqrt(v / c2) + eps)",
+     "p = p - lr * m / (np.sqrt(v) + eps)"),
+    ("Adam moments' rates swapped", "m = b1 * m + (f32(1) - b1) * g\n    v = b2 * v + (f32(1) - b2) * g * g",
+     "m = b2 * m + (f32(1) - b2) * g\n    v = b1 * v + (f32(1) - b1) * g * g"),
+    ("Adam ascends", "p = p - lr * (m / c1)", "p = p + lr * (m / c1)"),
+    ("Adam epsilon inside the root", "(np.sqrt(v / c2) + eps)", "np.sqrt(v / c2 + eps)"),
 ]
 
 

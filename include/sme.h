@@ -213,6 +213,15 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     memory of the CTAs that consume it (distributed shared memory), so no
  *     dependency is polled through L2; SME_ERR_SIZE when the sequence needs
  *     more shared memory than a cluster has;
+ *     SME_SCHED_SPARSE -- for inputs where most MBs are transparent: one
+ *     streaming pass reads every alpha plane once, classifies and packs it
+ *     and finishes the transparent MBs (Fig. 1 gives them (0,0); their
+ *     co-located prediction error is computed once per luma plane shared
+ *     by several VOPs), then the per-MB search runs over a list of the
+ *     other MBs in wavefront order, taking a transparent neighbour's (0,0)
+ *     from the class map without waiting (never speculatively);
+ *     SME_OPT_MB_CTAS_PER_SM 2 selects the search kernel built for two
+ *     resident CTAs per SM, else one;
  *     SME_SCHED_AUTO (default) -- chosen per workload.
  *   SME_OPT_PAIR_WARPS: warps (MB rows in flight) per CTA of the pair
  *     schedule, 1..16 (at most 8 used with SME_OPT_PAIR_DIRECT); 0
@@ -261,7 +270,7 @@ enum {
     SME_OPT_FOUR_MV = 7,
     SME_OPT_BOUNDARY_T_TEXTURE = 8
 };
-enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2, SME_SCHED_CLUSTER = 3 };
+enum { SME_SCHED_AUTO = 0, SME_SCHED_MB = 1, SME_SCHED_PAIR = 2, SME_SCHED_CLUSTER = 3, SME_SCHED_SPARSE = 4 };
 int sme_set_option(sme_ctx* ctx, int option, int value);
 /* Exhaustive search (the ES of Sec. 1 / Table 1 / Table 2, the comparison
  * method of the paper's experiments; not part of the method): for every MB
@@ -303,8 +312,18 @@ int sme_autotune(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha, int n_
  *   sme_batch_synchronize  waits and reports a device-side failure.
  *   sme_batch_config   the configuration in use (schedule SME_SCHED_*,
  *                      its parameter: CTAs per SM for SME_SCHED_MB (0 = all
- *                      that fit) or warps for SME_SCHED_PAIR, speculation)
+ *                      that fit) and SME_SCHED_SPARSE, or warps for
+ *                      SME_SCHED_PAIR, speculation)
  *                      and the tuned time per run in ms (0 before tuning).
+ *   sme_batch_set_config  sets the configuration instead of tuning: schedule
+ *                      SME_SCHED_MB (param = CTAs per SM, 0..32, 0 = all that
+ *                      fit; flag = speculation), SME_SCHED_PAIR (param =
+ *                      warps per CTA, 0..16, 0 = automatic; flag = direct
+ *                      transparent runs) or SME_SCHED_SPARSE (param 0..2: 2 =
+ *                      the search kernel built for two CTAs per SM; flag
+ *                      0 or 1, unused); drops a captured graph (later runs
+ *                      launch directly until sme_batch_tune).  SME_ERR_ARG on
+ *                      other values.
  * Results per sequence are exactly those of sme_estimate_sequence on it. */
 typedef struct {
     int width, height, n_frames;
@@ -328,6 +347,7 @@ int sme_batch_synchronize(sme_batch* b);
  * SME_OPT_PAIR_DIRECT; per-MB schedule: SME_OPT_SPECULATE) and the tuned time
  * of one run in ms (0 before tuning).  Any output pointer may be NULL. */
 int sme_batch_config(sme_batch* b, int* schedule, int* param, int* flag, float* best_ms);
+int sme_batch_set_config(sme_batch* b, int schedule, int param, int flag);
 int sme_batch_destroy(sme_batch* b);
 
 /* Learned seed proposal (no counterpart in the paper, whose seeds are the

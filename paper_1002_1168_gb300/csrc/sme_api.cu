@@ -43,6 +43,17 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Scratch of the sparse schedule (SME_SCHED_SPARSE): the luma groups of the
+// streaming pass, the per-row counts, the per-step offsets and cursors, the
+// list of non-transparent MBs and its counters.
+struct SparseScratch {
+    DevBuf grp_first, grp_members, gf_group, gf_frame, row_base, rowcnt, hist, cursor, list, ctr, seq_base, first;
+    int n_gf = 0, max_mbh = 0, steps = 0, nseq = 0;
+    long long total_rows = 0;
+    const void* key = nullptr;  // single-sequence path: the set-up is reused while (luma, F) stay the same
+    int key_f = -1;
+};
+
 }  // namespace
 
 struct sme_ctx {
@@ -76,6 +87,7 @@ struct sme_ctx {
     // classification reads a pinned alpha in place
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_go = nullptr, copy_done = nullptr;
+    SparseScratch sp;
 };
 
 namespace {
@@ -106,6 +118,116 @@ void release(DevBuf& b)
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+void release_sparse(SparseScratch& sp)
+{
+    DevBuf* bufs[] = {&sp.grp_first, &sp.grp_members, &sp.gf_group, &sp.gf_frame, &sp.row_base, &sp.rowcnt,
+                      &sp.hist,      &sp.cursor,      &sp.list,     &sp.ctr,      &sp.seq_base, &sp.first};
+    for (DevBuf* b : bufs) release(*b);
+    sp = SparseScratch{};
+}
+
+template <class T>
+int upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s)
+{
+    int rc = ensure(b, v.size() * sizeof(T));
+    if (rc) return rc;
+    return cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s) == cudaSuccess
+               ? SME_OK
+               : SME_ERR_CUDA;
+}
+
+// Host set-up of the sparse schedule for sequences d (host copies of the
+// descriptors, in launch order): sequences sharing one luma plane, size and
+// frame count form a group (at most kGroupMax VOPs) whose co-located errors
+// the streaming pass computes once; one block row per (group, frame).
+int setup_sparse(SparseScratch& sp, const std::vector<SeqDesc>& d, cudaStream_t s)
+{
+    const int n = (int)d.size();
+    std::vector<int> first, members, gfg, gff, base(n);
+    std::vector<long long> rb(n);
+    std::vector<int> gid_of(n, -1);
+    long long rows = 0;
+    int steps = 0, max_mbh = 0;
+    for (int i = 0; i < n; ++i) {
+        rb[i] = rows;
+        rows += (long long)d[i].F * d[i].MBH;
+        base[i] = d[i].gid_base;
+        steps = std::max(steps, (d[i].MBW - 1) + 2 * (d[i].MBH - 1) + d[i].P);
+        max_mbh = std::max(max_mbh, d[i].MBH);
+    }
+    for (int i = 0; i < n; ++i) {
+        if (gid_of[i] >= 0) continue;
+        const int g = (int)first.size();
+        first.push_back((int)members.size());
+        for (int j = i; j < n && (int)members.size() - first.back() < kGroupMax; ++j)
+            if (gid_of[j] < 0 && d[j].luma == d[i].luma && d[j].W == d[i].W && d[j].H == d[i].H &&
+                d[j].F == d[i].F && d[j].rd == d[i].rd) {
+                gid_of[j] = g;
+                members.push_back(j);
+            }
+        for (int f = 0; f < d[i].F; ++f) {
+            gfg.push_back(g);
+            gff.push_back(f);
+        }
+    }
+    first.push_back((int)members.size());
+    if (gfg.size() > 65535u * 1024u) return SME_ERR_SIZE;
+    int rc;
+    const size_t total = (size_t)d.back().gid_base + (size_t)d.back().P * d.back().M;
+    if ((rc = upload(sp.grp_first, first, s)) || (rc = upload(sp.grp_members, members, s)) ||
+        (rc = upload(sp.gf_group, gfg, s)) || (rc = upload(sp.gf_frame, gff, s)) || (rc = upload(sp.row_base, rb, s)) ||
+        (rc = upload(sp.seq_base, base, s)) || (rc = ensure(sp.rowcnt, (size_t)rows * 4)) ||
+        (rc = ensure(sp.hist, ((size_t)steps + 1) * 32)) || (rc = ensure(sp.cursor, (size_t)steps * 32)) ||
+        (rc = ensure(sp.first, (size_t)n * 4)) ||
+        (rc = ensure(sp.list, total * 4)) || (rc = ensure(sp.ctr, sizeof(SparseCounters))))
+        return rc;
+    sp.n_gf = (int)gfg.size();
+    sp.max_mbh = max_mbh;
+    sp.steps = steps;
+    sp.nseq = n;
+    sp.total_rows = rows;
+    return SME_OK;
+}
+
+SparseArgs sparse_args(const SparseScratch& sp, SeqDesc* seqs, DevStatus* status)
+{
+    SparseArgs a{};
+    a.seqs = seqs;
+    a.desc_dst = seqs;
+    a.nseq = sp.nseq;
+    a.grp_first = (const int*)sp.grp_first.p;
+    a.grp_members = (const int*)sp.grp_members.p;
+    a.gf_group = (const int*)sp.gf_group.p;
+    a.gf_frame = (const int*)sp.gf_frame.p;
+    a.n_gf = sp.n_gf;
+    a.max_mbh = sp.max_mbh;
+    a.row_base = (const long long*)sp.row_base.p;
+    a.total_rows = sp.total_rows;
+    a.rowcnt = (unsigned*)sp.rowcnt.p;
+    a.hist = (unsigned*)sp.hist.p;
+    a.first_step = (int*)sp.first.p;
+    a.cursor = (unsigned*)sp.cursor.p;
+    a.steps = sp.steps;
+    a.list = (int*)sp.list.p;
+    a.ctr = (SparseCounters*)sp.ctr.p;
+    a.status = status;
+    return a;
+}
+
+// The search launch of the sparse schedule: every CTA resident (the warps
+// wait on each other), min_blocks selects the register budget.
+int launch_sparse_search(const Method& m, MeArgs a, const SparseScratch& sp, int num_sms, int min_blocks,
+                         cudaStream_t s)
+{
+    int per_sm = 0;
+    if (me_sparse_occupancy(m.S, min_blocks, &per_sm, m.tt != 0) != cudaSuccess || per_sm < 1) return SME_ERR_CUDA;
+    a.list = (const int*)sp.list.p;
+    a.seq_base = (const int*)sp.seq_base.p;
+    a.nseq = sp.nseq;
+    a.ctr = (SparseCounters*)sp.ctr.p;
+    return cuda_status(launch_me_sparse(m, a, num_sms * per_sm, min_blocks, s));
+}
 
 int check_params(const sme_params* p)
 {
@@ -305,6 +427,7 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     if (c->four_mv && (seed || c->m.tt)) return SME_ERR_ARG;
     // four-vector mode: the pair schedule on request, else the per-MB one
     const bool pair = c->schedule == kSchedPair, cluster = !c->four_mv && c->schedule == kSchedCluster;
+    const bool sparse = !c->four_mv && c->schedule == kSchedSparse;
     MapSet maps;
     memset(&maps, 0, sizeof(maps));
     int C = 0;
@@ -312,7 +435,7 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
         if ((rc = encode_pair_maps(&maps, luma, (const uint32_t*)c->packed.p, g, F, c->m.S))) return rc;
     } else if (cluster) {
         if ((rc = build_cluster_schedule(c, P, &C))) return rc;
-    } else if ((rc = build_schedule(c, P))) {
+    } else if (!sparse && (rc = build_schedule(c, P))) {
         return rc;
     }
 
@@ -361,9 +484,21 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
         ev = &c->prof_ev[3 * c->prof_n++];
         if (cudaEventRecord(ev[0], c->stream) != cudaSuccess) return SME_ERR_CUDA;
     }
-    if (launch_classify(g, ca, c->stream) != cudaSuccess) return SME_ERR_CUDA;
+    if (sparse) {
+        // one sequence, one group: the set-up depends on the frame count only
+        if (c->sp.key_f != F) {
+            std::vector<SeqDesc> one(1, d);
+            if ((rc = setup_sparse(c->sp, one, c->stream))) return rc;
+            c->sp.key_f = F;
+        }
+        if (before_me && cudaStreamWaitEvent(c->stream, before_me, 0) != cudaSuccess) return SME_ERR_CUDA;
+        if (launch_sparse_prep(sparse_args(c->sp, (SeqDesc*)c->desc.p, c->status), &d, c->stream) != cudaSuccess)
+            return SME_ERR_CUDA;
+    } else if (launch_classify(g, ca, c->stream) != cudaSuccess) {
+        return SME_ERR_CUDA;
+    }
     if (ev && cudaEventRecord(ev[1], c->stream) != cudaSuccess) return SME_ERR_CUDA;
-    if (before_me && cudaStreamWaitEvent(c->stream, before_me, 0) != cudaSuccess) return SME_ERR_CUDA;
+    if (!sparse && before_me && cudaStreamWaitEvent(c->stream, before_me, 0) != cudaSuccess) return SME_ERR_CUDA;
 
     MeArgs a{};
     a.seqs = (const SeqDesc*)c->desc.p;
@@ -385,7 +520,9 @@ int run_sequence(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int F, c
     a.pair_direct = c->four_mv ? 0 : c->pair_direct;
     a.four_mv = c->four_mv;
     a.timeout_ns = c->timeout_ns;
-    if (cluster) {
+    if (sparse) {
+        if ((rc = launch_sparse_search(c->m, a, c->sp, c->num_sms, c->mb_ctas_per_sm, c->stream))) return rc;
+    } else if (cluster) {
         a.cl_items = (const int*)c->cl_items.p;
         a.cl_count = (const int*)c->cl_count.p;
         a.cl_consumers = (const int*)c->cl_cons.p;
@@ -460,7 +597,7 @@ const ExecCfg kTuneCandidates[] = {
     {kSchedMB, 0, 0, 0, 0, 1},       {kSchedPair, 4, 0, 0, 0, 1},     {kSchedPair, 8, 0, 0, 0, 1},
     {kSchedPair, 4, 0, 0, 0, 0},     {kSchedPair, 8, 0, 0, 0, 0},
     {kSchedPair, 16, 0, 0, 0, 0},    {kSchedCluster, 0, 0, 1, 16, 1}, {kSchedCluster, 0, 0, 0, 16, 1},
-    {kSchedCluster, 0, 0, 1, 8, 1},
+    {kSchedCluster, 0, 0, 1, 8, 1},  {kSchedSparse, 0, 1, 0, 0, 1},   {kSchedSparse, 0, 2, 0, 0, 1},
 };
 
 // Device time of `trials` back-to-back runs of `enqueue` (the minimum), ms;
@@ -565,6 +702,7 @@ int sme_destroy(sme_ctx* c)
                       &c->h_disp, &c->h_iters, &c->h_npos, &c->h_cls, &c->h_ssemb, &c->h_sse,
                       &c->h_pred, &c->cl_items, &c->cl_count, &c->cl_cons};
     for (DevBuf* b : bufs) release(*b);
+    release_sparse(c->sp);
     profile_free(c);
     if (c->status) cudaFree(c->status);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -897,7 +1035,7 @@ int sme_set_option(sme_ctx* c, int option, int value)
     switch (option) {
     case SME_OPT_SCHEDULE:
         if (value != SME_SCHED_AUTO && value != SME_SCHED_MB && value != SME_SCHED_PAIR &&
-            value != SME_SCHED_CLUSTER)
+            value != SME_SCHED_CLUSTER && value != SME_SCHED_SPARSE)
             return SME_ERR_ARG;
         c->schedule = value;
         return SME_OK;
@@ -969,7 +1107,8 @@ int sme_autotune(sme_ctx* c, const uint8_t* luma, const uint8_t* alpha, int n_fr
     float best = -1.0f;
     ExecCfg pick = {c->schedule, c->pair_warps, c->mb_ctas_per_sm, c->speculate, c->cluster, c->pair_direct};
     for (const ExecCfg& e : kTuneCandidates) {
-        if (c->four_mv && e.schedule == kSchedCluster) continue;  // the mode runs those on the per-MB schedule
+        // the four-vector mode runs those on the per-MB schedule
+        if (c->four_mv && (e.schedule == kSchedCluster || e.schedule == kSchedSparse)) continue;
         c->schedule = e.schedule;
         c->pair_warps = e.pair_warps;
         c->mb_ctas_per_sm = e.mb_ctas_per_sm;
@@ -1056,6 +1195,7 @@ struct sme_batch {
     long long total_mbs = 0;
     DevStatus* status = nullptr;
     DevBuf descs, packed, cls, ready, sched, sched_seq, unit_seq, unit_pair, fseq, ffrm, maps;
+    SparseScratch sp;
     ExecCfg cfg = {kSchedMB, 0, 0, 1, 0, 1};
     float tuned_ms = 0.0f;
     cudaGraph_t graph = nullptr;
@@ -1067,6 +1207,20 @@ namespace {
 int batch_enqueue(sme_batch* b, cudaStream_t s)
 {
     if (b->cfg.schedule == kSchedCluster) return SME_ERR_ARG;  // single sequences only
+    if (b->cfg.schedule == kSchedSparse) {
+        if (launch_sparse_prep(sparse_args(b->sp, (SeqDesc*)b->descs.p, b->status), nullptr, s) != cudaSuccess)
+            return SME_ERR_CUDA;
+        MeArgs a{};
+        a.seqs = (const SeqDesc*)b->descs.p;
+        a.ready = (unsigned long long*)b->ready.p;
+        a.status = b->status;
+        a.m = b->m;
+        a.total = (int)b->total_mbs;
+        a.fault_ticket = -1;
+        a.speculate = b->cfg.speculate;
+        a.timeout_ns = kDefaultTimeoutNs;
+        return launch_sparse_search(b->m, a, b->sp, b->num_sms, b->cfg.mb_ctas_per_sm, s);
+    }
     ClassifyBatchArgs ca{(const SeqDesc*)b->descs.p, (const int*)b->fseq.p, (const int*)b->ffrm.p, b->status};
     if (launch_classify_batch(ca, b->max_mbh, b->total_frames, s) != cudaSuccess) return SME_ERR_CUDA;
     MeArgs a{};
@@ -1279,6 +1433,7 @@ int sme_batch_create(sme_batch** out, const sme_params* p, const sme_sequence* s
                 }
         }
     if (k != (size_t)gid) return fail(SME_ERR_STATE);
+    if ((rc = setup_sparse(b->sp, d, nullptr))) return fail(rc);
     // Per-pair schedule: pair k of every sequence before pair k+1 of any.
     std::vector<int> useq, upair;
     int max_p = 0;
@@ -1357,6 +1512,37 @@ int sme_batch_config(sme_batch* b, int* schedule, int* param, int* flag, float* 
     return SME_OK;
 }
 
+int sme_batch_set_config(sme_batch* b, int schedule, int param, int flag)
+{
+    if (!b) return SME_ERR_ARG;
+    ExecCfg e = {schedule, 0, 0, 1, 0, 1};
+    if (flag != 0 && flag != 1) return SME_ERR_ARG;
+    switch (schedule) {
+    case kSchedMB:
+        if (param < 0 || param > 32) return SME_ERR_ARG;
+        e.mb_ctas_per_sm = param;
+        e.speculate = flag;
+        break;
+    case kSchedSparse:
+        if (param < 0 || param > 2) return SME_ERR_ARG;
+        e.mb_ctas_per_sm = param;
+        e.speculate = flag;
+        break;
+    case kSchedPair:
+        if (param < 0 || param > kPairWarpsMax) return SME_ERR_ARG;
+        e.pair_warps = param;
+        e.pair_direct = flag;
+        e.speculate = 0;
+        break;
+    default:
+        return SME_ERR_ARG;  // the cluster schedule runs single sequences only
+    }
+    batch_drop_graph(b);
+    b->cfg = e;
+    b->tuned_ms = 0.0f;
+    return SME_OK;
+}
+
 int sme_batch_destroy(sme_batch* b)
 {
     if (!b) return SME_ERR_ARG;
@@ -1365,6 +1551,7 @@ int sme_batch_destroy(sme_batch* b)
     DevBuf* bufs[] = {&b->descs, &b->packed, &b->cls, &b->ready, &b->sched, &b->sched_seq, &b->unit_seq,
                       &b->unit_pair, &b->fseq, &b->ffrm, &b->maps};
     for (DevBuf* x : bufs) release(*x);
+    release_sparse(b->sp);
     if (b->status) cudaFree(b->status);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;

@@ -36,7 +36,10 @@ constexpr int kPairWarpsMax = 16;  // warps (MB rows) per CTA of the per-pair ME
 
 // ME schedules: one warp per MB with tickets in wavefront order, or one CTA
 // per frame pair with one warp per MB row.
-enum Schedule { kSchedAuto = 0, kSchedMB = 1, kSchedPair = 2, kSchedCluster = 3 };
+// kSchedSparse: a streaming pass finishes the transparent MBs, the per-MB
+// search runs over a wavefront-ordered list of the others.
+enum Schedule { kSchedAuto = 0, kSchedMB = 1, kSchedPair = 2, kSchedCluster = 3, kSchedSparse = 4 };
+constexpr int kGroupMax = 64;     // VOPs sharing one luma in one streaming pass of the sparse schedule
 
 // Device status words (scratch).  `err` is sticky until read by
 // sme_synchronize; `abort` and `ticket` are reset by the classify kernel at
@@ -84,6 +87,12 @@ struct SeqDesc {
     int gid_base;
 };
 
+// Counters of the sparse schedule's list (scratch).
+struct SparseCounters {
+    unsigned total;   // non-transparent MBs listed (written by the scan launch)
+    unsigned ticket;  // next list entry of the search launch
+};
+
 struct ClassifyArgs {
     const uint8_t* alpha;
     const uint8_t* const* frames;  // when non-null: frame f is frames[f] (NULL: an empty plane)
@@ -103,6 +112,29 @@ struct ClassifyBatchArgs {
     const SeqDesc* seqs;
     const int* fseq;
     const int* ffrm;
+    DevStatus* status;
+};
+
+// The sparse schedule's preparation launches (reset, streaming pass, scan,
+// scatter) over `nseq` sequences grouped by shared luma.
+struct SparseArgs {
+    SeqDesc* seqs;             // [nseq] (device)
+    SeqDesc* desc_dst;         // single-sequence path: where the reset launch stores the descriptor
+    int nseq;
+    const int* grp_first;      // [ngrp + 1]: group g = grp_members[grp_first[g] .. grp_first[g + 1]) (<= kGroupMax)
+    const int* grp_members;    // sequence indices; the members of a group share luma, size and frames
+    const int* gf_group;       // per (group, frame) block row of the streaming pass: its group
+    const int* gf_frame;       //   and frame
+    int n_gf, max_mbh;
+    const long long* row_base; // [nseq]: rows (frame, MB row) of sequence q start here in rowcnt
+    long long total_rows;
+    unsigned* rowcnt;          // non-transparent MBs per row (0 for frames < ref_distance)
+    int* first_step;           // [nseq]: first wavefront step with a non-transparent MB of each sequence
+    unsigned* hist;            // [8 * (steps + 1)]: MBs per list key (one 32-byte sector each)
+    unsigned* cursor;          // [8 * steps]: scatter cursor of each key
+    int steps;
+    int* list;                 // global MB ids of the non-transparent MBs, by step
+    SparseCounters* ctr;
     DevStatus* status;
 };
 
@@ -131,6 +163,11 @@ struct MeArgs {
     const int* cl_count;      // [cluster] items per CTA
     const int* cl_consumers;  // [total][4] consumer slot of each MB in the roles A, B, C, T (or -1)
     int cl_cap;
+    // sparse schedule
+    const int* list;          // global MB ids by wavefront step (sparse_scatter_kernel)
+    const int* seq_base;      // [nseq] first global MB id of each sequence (ascending)
+    int nseq;
+    SparseCounters* ctr;
 };
 
 struct CompArgs {
@@ -178,6 +215,12 @@ size_t me_cluster_smem_bytes(int S, int cap, int warps);
 int me_cluster_fits(int S, int cap, int cluster, int warps);
 cudaError_t launch_me_cluster(const Method& m, const MeArgs& a, int cluster, int warps, int helpers, cudaStream_t s);
 cudaError_t launch_compensate(const Geom& g, const Method& m, const CompArgs& a, cudaStream_t s);
+// Sparse schedule: preparation (desc: single-sequence descriptor stored by the
+// reset launch, or NULL when a.seqs already holds the descriptors) and the search.
+cudaError_t launch_sparse_prep(const SparseArgs& a, const SeqDesc* desc, cudaStream_t s);
+// min_blocks selects the register budget of the search kernel (1 or 2 CTAs per SM).
+cudaError_t me_sparse_occupancy(int S, int min_blocks, int* blocks_per_sm, bool variants);
+cudaError_t launch_me_sparse(const Method& m, const MeArgs& a, int grid, int min_blocks, cudaStream_t s);
 
 // Exhaustive search over V for every MB of `pairs` frame pairs (sme_es.cu).
 size_t es_smem_bytes(int S, int h);

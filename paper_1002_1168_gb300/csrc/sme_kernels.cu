@@ -20,6 +20,8 @@
 // row-major pixel order: a lane's 8 terms, then the lanes.
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sme_internal.h"
 
 namespace sme {
@@ -130,11 +132,20 @@ __device__ __forceinline__ void stage_window(uint8_t* win, const uint8_t* ref, i
     wx0 = max(0, X0 - cs);
     const int wx1 = min(W, X0 + 16 + cs);
     const int nch = (wx1 - wx0) >> 4, n = (wy1 - wy0 + 1) * nch;
+    // c / nch by a multiply and a shift: exact for nch <= 9 and c < 4000
+    // (windows hold at most 144 rows of 9 chunks).
+    const unsigned inv = (65536u + (unsigned)nch - 1u) / (unsigned)nch;
+    // Asynchronous 16-byte copies straight into shared memory: every chunk of
+    // the lane is in flight at once, and one wait covers them all.
+    const uint8_t* src0 = ref + (size_t)wy0 * W + wx0;
+    const unsigned dst0 = (unsigned)__cvta_generic_to_shared(win);
     for (int c = lane; c < n; c += 32) {
-        const int r = c / nch, ch = c - r * nch;
-        const uint4 val = __ldg(reinterpret_cast<const uint4*>(ref + (size_t)(wy0 + r) * W + wx0 + 16 * ch));
-        *reinterpret_cast<uint4*>(win + r * pitch + 16 * ch) = val;
+        const int r = (int)(((unsigned)c * inv) >> 16), ch = c - r * nch;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + (unsigned)(r * pitch + 16 * ch)),
+                     "l"(src0 + (size_t)r * W + 16 * ch)
+                     : "memory");
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
 }
 
@@ -1121,7 +1132,13 @@ struct ClusterLinks {
 // kVariants: the code of the Sec. 3.1 boundary variant is compiled in (taken
 // when m.tt); the default instantiation leaves it out, since even an untaken
 // branch after the wait loop measurably slowed the search.
-template <class Links, bool kVariants>
+// kSparse: transparent MBs publish nothing (the sparse schedule finishes them
+// in its streaming pass); a candidate whose MB is transparent is (0,0) by
+// Fig. 1 and is taken from the class map without a wait.  The speculative
+// first step is compiled out: in that throughput form the candidates have
+// mostly arrived already, and the extra code cost more than it saved.
+
+template <class Links, bool kVariants, bool kSparse = false>
 __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int gid, const SeqDesc* sd, uint8_t* win,
                                           int* slog, const float* s_rcp, const Links& L, int lane, int pitch)
 {
@@ -1163,6 +1180,13 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
     if (lane == 1 && v > 0) dep = gid - MBW;                     // B
     if (lane == 2 && v > 0 && u < MBW - 1) dep = gid - MBW + 1;  // C
     if (lane == 3 && k > 0) dep = gid - M;                       // T
+    if constexpr (kSparse) {
+        if (dep >= 0) {
+            const int dmb = lane == 3 ? mb : (lane == 0 ? mb - 1 : (lane == 1 ? mb - MBW : mb - MBW + 1));
+            const int dfr = lane == 3 ? k - 1 + rd : k + rd;
+            if (__ldg(sd->cls + (size_t)dfr * M + dmb) == SME_TRANSPARENT) dep = -1;
+        }
+    }
     int key = 0;
     if (lane == 3 && k == 0 && sd->temporal_in)
         key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
@@ -1191,7 +1215,7 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
         // costing below; its result is consumed at the end of the pass.
         unsigned long long w = 0;
         if (lane < 4 && !res_l) w = L.poll(dep, lane);
-        const unsigned fresh = (a.speculate || have == all) ? (have & ~costed) : 0u;
+        const unsigned fresh = (kSparse || a.speculate || have == all) ? (have & ~costed) : 0u;
 #pragma unroll
         for (int c = 0; c < 5; ++c)
             if (fresh & (1u << c)) {
@@ -1217,7 +1241,7 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
                 costed |= 1u << c;
             }
         if (costed == all) break;
-        if (a.speculate && cls == SME_OPAQUE && costed && m.K > 0) {
+        if (!kSparse && a.speculate && cls == SME_OPAQUE && costed && m.K > 0) {
             // The first pixel-recursive step at the provisional winner
             // (first strict minimum among the candidates costed so far).
             int pb = -1;
@@ -1336,6 +1360,307 @@ __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
         const int gid = __ldg(a.sched + t);
         const SeqDesc* sd = a.seqs + (a.sched_seq ? __ldg(a.sched_seq + t) : 0);
         if (!me_one_mb<GlobalLinks, kVariants>(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) break;
+    }
+}
+
+
+// ===================================================== sparse schedule ==
+// Throughput form for batches where most MBs are transparent.  Fig. 1 gives
+// a transparent MB the vector (0,0) without any evaluation, so its outputs
+// need only its class and the co-located prediction error; the dependency
+// ordered search is needed only for the other MBs.
+//   sparse_reset_kernel    zeroes the per-pair SSE, the step counts and the
+//                          counters, starts a new epoch of ready words;
+//   sparse_stream_kernel   one pass over every (luma group, frame, MB row):
+//                          the co-located SSE of every MB once per shared
+//                          luma, then for each VOP of the group the class and
+//                          packed alpha rows of every MB, the outputs of its
+//                          transparent MBs, the count of the other MBs per
+//                          row and the VOP's first wavefront step;
+//   sparse_count_kernel    MBs per list key (step relative to the VOP's first);
+//   sparse_scan_kernel     key counts -> list offsets;
+//   sparse_scatter_kernel  lists every non-transparent MB by key;
+//   me_sparse_kernel       the per-MB search over that list only.
+__global__ void __launch_bounds__(256) sparse_reset_kernel(const SparseArgs a, const SeqDesc desc, int use_desc)
+{
+    const int tid = threadIdx.x;
+    if (blockIdx.x == 0) {
+        if (tid == 0) {
+            if (use_desc) *a.desc_dst = desc;
+            a.status->ticket = 0;
+            a.status->abort = 0;
+            const unsigned e = a.status->epoch + 1u;
+            a.status->epoch = e ? e : 1u;
+            a.ctr->total = 0;
+            a.ctr->ticket = 0;
+        }
+        for (int i = tid; i <= a.steps; i += blockDim.x) a.hist[8 * (size_t)i] = 0;
+    }
+    for (int q = blockIdx.x; q < a.nseq; q += gridDim.x) {
+        if (tid == 0) a.first_step[q] = 0x7fffffff;
+        const SeqDesc& d = use_desc ? desc : a.seqs[q];
+        if (d.sse)
+            for (int i = tid; i < d.P; i += blockDim.x) d.sse[i] = 0ull;
+    }
+}
+
+// The sequence that holds flat row r (rows of sequence q start at row_base[q]).
+__device__ __forceinline__ int seq_of_row(const long long* row_base, int n, long long r)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(row_base + mid) <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Sum of squared differences of 16 packed pixels (exact integer).
+__device__ __forceinline__ unsigned sq16(const uint4& x, const uint4& y)
+{
+    unsigned d = __vabsdiffu4(x.x, y.x), acc = __dp4a(d, d, 0u);
+    d = __vabsdiffu4(x.y, y.y);
+    acc = __dp4a(d, d, acc);
+    d = __vabsdiffu4(x.z, y.z);
+    acc = __dp4a(d, d, acc);
+    d = __vabsdiffu4(x.w, y.w);
+    return __dp4a(d, d, acc);
+}
+
+__global__ void __launch_bounds__(256) sparse_stream_kernel(const SparseArgs a)
+{
+    __shared__ unsigned long long s_sse[kGroupMax];
+    __shared__ unsigned s_cnt[kGroupMax];
+    __shared__ int s_umin[kGroupMax];
+    const int v = blockIdx.x, gf = blockIdx.y, tid = threadIdx.x;
+    const int grp = __ldg(a.gf_group + gf), f = __ldg(a.gf_frame + gf);
+    const int m0 = __ldg(a.grp_first + grp), nm = __ldg(a.grp_first + grp + 1) - m0;
+    const SeqDesc* s0 = a.seqs + __ldg(a.grp_members + m0);
+    const int W = s0->W, H = s0->H, MBW = s0->MBW, MBH = s0->MBH, M = s0->M, Wp = s0->Wp, rd = s0->rd;
+    if (v >= MBH) return;
+    const int k = f - rd;  // the pair whose current frame is f (none when negative)
+    for (int j = tid; j < nm; j += blockDim.x) {
+        s_sse[j] = 0ull;
+        s_cnt[j] = 0u;
+        s_umin[j] = 0x7fffffff;
+    }
+    __syncthreads();
+    const size_t FS = (size_t)W * H;
+    const int hw = 2 * Wp;  // u16 slots per packed row
+    for (int u = tid; u < hw; u += blockDim.x) {
+        if (u >= MBW) {  // the zero words that end every packed row
+            for (int j = 0; j < nm; ++j) {
+                const SeqDesc* sd = a.seqs + __ldg(a.grp_members + m0 + j);
+                uint16_t* pk = reinterpret_cast<uint16_t*>(sd->packed_w + ((size_t)f * H + 16 * v) * Wp);
+#pragma unroll
+                for (int r = 0; r < 16; ++r) pk[(size_t)r * hw + u] = 0;
+            }
+            continue;
+        }
+        const size_t px = (size_t)(16 * v) * W + 16 * u;
+        // Sec. 4: the co-located prediction error of the MB, shared by every
+        // VOP of the group (a transparent MB predicts from (0,0)).
+        unsigned sse0 = 0;
+        if (k >= 0) {
+            const uint8_t* cur = s0->luma + (size_t)f * FS + px;
+            const uint8_t* ref = s0->luma + (size_t)k * FS + px;
+#pragma unroll 4
+            for (int r = 0; r < 16; ++r)
+                sse0 += sq16(__ldg(reinterpret_cast<const uint4*>(cur + (size_t)r * W)),
+                             __ldg(reinterpret_cast<const uint4*>(ref + (size_t)r * W)));
+        }
+        for (int j = 0; j < nm; ++j) {
+            const SeqDesc* sd = a.seqs + __ldg(a.grp_members + m0 + j);
+            const uint8_t* al = sd->alpha + (size_t)f * FS + px;
+            uint16_t* pk = reinterpret_cast<uint16_t*>(sd->packed_w + ((size_t)f * H + 16 * v) * Wp);
+            unsigned n = 0;
+#pragma unroll 8
+            for (int r = 0; r < 16; ++r) {
+                const unsigned bits = bab_bits16(al + (size_t)r * W);
+                n += __popc(bits);
+                pk[(size_t)r * hw + u] = (uint16_t)bits;
+            }
+            const int cls = n == 0 ? SME_TRANSPARENT : (n == 256 ? SME_OPAQUE : SME_BOUNDARY);
+            const int mb = v * MBW + u;
+            sd->cls_w[(size_t)f * M + mb] = (uint8_t)cls;
+            if (k < 0) continue;
+            if (cls != SME_TRANSPARENT) {
+                atomicAdd(&s_cnt[j], 1u);
+                atomicMin(&s_umin[j], u);
+                continue;
+            }
+            // Fig. 1: no vector is computed for a transparent MB.
+            const size_t idx = (size_t)k * M + mb;
+            sd->mv[idx] = sme_mv{0, 0};
+            if (sd->cost) sd->cost[idx] = 0;
+            if (sd->disp) {
+                sd->disp[2 * idx] = 0.0f;
+                sd->disp[2 * idx + 1] = 0.0f;
+            }
+            if (sd->iters) sd->iters[idx] = 0;
+            if (sd->npos) sd->npos[idx] = 0;
+            if (sd->out_cls) sd->out_cls[idx] = (uint8_t)SME_TRANSPARENT;
+            if (sd->sse_mb) sd->sse_mb[idx] = sse0;
+            if (sd->sse) atomicAdd(&s_sse[j], (unsigned long long)sse0);
+            if (sd->pred) {
+                const uint8_t* ref = sd->luma + (size_t)k * FS + px;
+                uint8_t* pr = sd->pred + (size_t)k * FS + px;
+#pragma unroll 4
+                for (int r = 0; r < 16; ++r) {  // 8-byte stores, as every kernel writes the prediction
+                    const uint4 q = __ldg(reinterpret_cast<const uint4*>(ref + (size_t)r * W));
+                    *reinterpret_cast<uint2*>(pr + (size_t)r * W) = make_uint2(q.x, q.y);
+                    *reinterpret_cast<uint2*>(pr + (size_t)r * W + 8) = make_uint2(q.z, q.w);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int j = tid; j < nm; j += blockDim.x) {
+        const int q = __ldg(a.grp_members + m0 + j);
+        const SeqDesc* sd = a.seqs + q;
+        a.rowcnt[__ldg(a.row_base + q) + (long long)f * MBH + v] = s_cnt[j];
+        if (k >= 0 && sd->sse && s_sse[j]) atomicAdd(sd->sse + k, s_sse[j]);
+        // the VOP's first wavefront step t = u + 2v + k with a listed MB
+        if (s_cnt[j]) atomicMin(a.first_step + q, s_umin[j] + 2 * v + k);
+    }
+}
+
+// The list key of a non-transparent MB: its wavefront step t = u + 2v + k
+// minus its VOP's first such step.  The shift is constant within a VOP, so
+// every dependency (A, B, C of the same pair, T of the previous pair: steps
+// t - 1 and t - 2) keeps a smaller key; VOPs have no dependencies on each
+// other, so aligning their first steps lets all of them start at once
+// instead of waiting for the work of other VOPs at smaller absolute steps.
+__device__ __forceinline__ int list_key(const SparseArgs& a, int q, int u, int v, int k)
+{
+    return u + 2 * v + k - __ldg(a.first_step + q);
+}
+
+// Shared by the counting and the scattering pass: warps walk the row counts
+// 32 at a time and visit every non-transparent MB of the rows that have any.
+template <class Visit>
+__device__ __forceinline__ void sparse_walk(const SparseArgs& a, Visit visit)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < a.total_rows;
+         r0 += nw * 32) {
+        const long long r = r0 + lane;
+        const unsigned c = r < a.total_rows ? a.rowcnt[r] : 0u;
+        unsigned todo = __ballot_sync(kFull, c != 0);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const long long rr = r0 + l;
+            const int q = seq_of_row(a.row_base, a.nseq, rr);
+            const SeqDesc* sd = a.seqs + q;
+            const long long loc = rr - __ldg(a.row_base + q);
+            const int f = (int)(loc / sd->MBH), v = (int)(loc - (long long)f * sd->MBH);
+            const int k = f - sd->rd, MBW = sd->MBW;
+            for (int u = lane; u < MBW; u += 32) {
+                const int mb = v * MBW + u;
+                if (sd->cls[(size_t)f * sd->M + mb] != SME_TRANSPARENT)
+                    visit(list_key(a, q, u, v, k), sd->gid_base + k * sd->M + mb);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) sparse_count_kernel(const SparseArgs a)
+{
+    sparse_walk(a, [&](int key, int) { atomicAdd(a.hist + 8 * (size_t)key, 1u); });
+}
+
+// One CTA: exclusive prefix sums of the step counts (list offsets), the
+// cursors of the scatter, and the list length.
+__global__ void __launch_bounds__(1024) sparse_scan_kernel(const SparseArgs a)
+{
+    __shared__ unsigned wsum[32];
+    __shared__ unsigned carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < a.steps; base += 1024) {
+        const int i = base + tid;
+        const unsigned x = i < a.steps ? a.hist[8 * (size_t)i] : 0u;
+        unsigned inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned w = wsum[lane], wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(kFull, wi, o);
+                if (lane >= o) wi += y;
+            }
+            wsum[lane] = wi - w;  // exclusive prefix of the warps
+        }
+        __syncthreads();
+        const unsigned excl = carry + wsum[wid] + inc - x;
+        if (i < a.steps) a.cursor[8 * (size_t)i] = excl;
+        __syncthreads();
+        if (tid == 1023) carry = excl + x;
+        __syncthreads();
+    }
+    if (tid == 0) a.ctr->total = carry;
+}
+
+// Every non-transparent MB goes to the next slot of its key.
+__global__ void __launch_bounds__(256) sparse_scatter_kernel(const SparseArgs a)
+{
+    sparse_walk(a, [&](int key, int gid) { a.list[atomicAdd(a.cursor + 8 * (size_t)key, 1u)] = gid; });
+}
+
+// The sequence of global MB id gid (sequences' ids start at seq_base[q]).
+__device__ __forceinline__ int seq_of_gid(const int* seq_base, int n, int gid)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(seq_base + mid) <= gid) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The per-MB search over the list of non-transparent MBs.  Every dependency
+// of an MB has a smaller key, hence an earlier ticket, so the warps (all
+// resident) can always make progress, as in me_kernel.
+// kMinBlocks: CTAs per SM the register budget is cut for (1: no spills, one
+// 8-warp CTA per SM; 2: twice the warps with a few spills), chosen by tuning.
+template <bool kVariants, int kMinBlocks>
+__global__ void __launch_bounds__(32 * kMeWarps, kMinBlocks) me_sparse_kernel(const MeArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const Method m = a.m;
+    const int pitch = win_pitch(m.S);
+    uint8_t* win = smem + (size_t)wid * warp_smem(m.S);
+    int* slog = reinterpret_cast<int*>(win + win_bytes(m.S));
+    const GlobalLinks L{a.ready, ld_relaxed(&a.status->epoch), a.fault_ticket};
+    __shared__ float s_rcp[512];
+    fill_rcp(s_rcp);
+    __syncthreads();
+    const unsigned total = ld_relaxed(&a.ctr->total);
+    // The next ticket is taken while the current MB is searched (a warp holds
+    // at most one ticket it has not started, later than its current one,
+    // which keeps the progress argument above).
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(&a.ctr->ticket, 1u);
+    t = __shfl_sync(kFull, t, 0);
+    while (t < total) {
+        unsigned next = 0;
+        if (lane == 0) next = ld_relaxed(&a.status->abort) ? total : atomicAdd(&a.ctr->ticket, 1u);
+        const int gid = __ldg(a.list + t);
+        const SeqDesc* sd = a.seqs + seq_of_gid(a.seq_base, a.nseq, gid);
+        if (!me_one_mb<GlobalLinks, kVariants, true>(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) return;
+        t = __shfl_sync(kFull, next, 0);
     }
 }
 
@@ -2778,6 +3103,64 @@ cudaError_t launch_me(const Method& m, const MeArgs& a, int grid, cudaStream_t s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, m.tt ? me_kernel<true> : me_kernel<false>, a);
+}
+
+cudaError_t launch_sparse_prep(const SparseArgs& a, const SeqDesc* desc, cudaStream_t s)
+{
+    SeqDesc d{};
+    if (desc) d = *desc;
+    sparse_reset_kernel<<<std::max(1, std::min(a.nseq, 1024)), 256, 0, s>>>(a, d, desc ? 1 : 0);
+    sparse_stream_kernel<<<dim3(a.max_mbh, a.n_gf), 256, 0, s>>>(a);
+    const long long warps = (a.total_rows + 31) / 32;
+    const int grid = (int)std::max(1LL, std::min<long long>((warps + 7) / 8, 152 * 16));
+    sparse_count_kernel<<<grid, 256, 0, s>>>(a);
+    sparse_scan_kernel<<<1, 1024, 0, s>>>(a);
+    sparse_scatter_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool kVariants, int kMinBlocks>
+cudaError_t sparse_attr(const void** fn, size_t smem)
+{
+    *fn = (const void*)me_sparse_kernel<kVariants, kMinBlocks>;
+    if (smem > 48 * 1024) return cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+cudaError_t sparse_kernel(bool variants, int min_blocks, size_t smem, const void** fn)
+{
+    if (variants) return min_blocks >= 2 ? sparse_attr<true, 2>(fn, smem) : sparse_attr<true, 1>(fn, smem);
+    return min_blocks >= 2 ? sparse_attr<false, 2>(fn, smem) : sparse_attr<false, 1>(fn, smem);
+}
+
+cudaError_t me_sparse_occupancy(int S, int min_blocks, int* blocks_per_sm, bool variants)
+{
+    const size_t smem = me_smem_bytes(S);
+    const void* fn = nullptr;
+    cudaError_t e = sparse_kernel(variants, min_blocks, smem, &fn);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 32 * kMeWarps, smem);
+}
+
+cudaError_t launch_me_sparse(const Method& m, const MeArgs& a, int grid, int min_blocks, cudaStream_t s)
+{
+    // cooperative for the same reason as launch_me: warps wait on each other
+    const size_t smem = me_smem_bytes(m.S);
+    const void* fn = nullptr;
+    cudaError_t e = sparse_kernel(m.tt != 0, min_blocks, smem, &fn);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * kMeWarps);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {const_cast<MeArgs*>(&a)};
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 size_t me_cluster_smem_bytes(int S, int cap, int warps)

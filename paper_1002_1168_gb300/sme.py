@@ -21,7 +21,7 @@ SME_OPT_CLUSTER_SIZE = 5
 SME_OPT_PAIR_DIRECT = 6
 SME_OPT_FOUR_MV = 7
 SME_OPT_BOUNDARY_T_TEXTURE = 8
-SCHEDULES = {"auto": 0, "mb": 1, "pair": 2, "cluster": 3}
+SCHEDULES = {"auto": 0, "mb": 1, "pair": 2, "cluster": 3, "sparse": 4}
 STATUS = {0: "SME_OK", 1: "SME_ERR_ARG", 2: "SME_ERR_SIZE", 3: "SME_ERR_CUDA", 4: "SME_ERR_TIMEOUT",
           5: "SME_ERR_STATE", 6: "SME_ERR_NOMEM", 7: "SME_ERR_RANGE", 8: "SME_ERR_SCRATCH"}
 
@@ -35,6 +35,7 @@ EXPORTS = [
     "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_get_option", "sme_autotune",
     "sme_full_search",
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
+    "sme_batch_set_config",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_features_table",
     "sme_seednet_forward",
@@ -117,6 +118,7 @@ def _lib():
             "sme_batch_synchronize": (i, [vp]),
             "sme_batch_config": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_float)]),
+            "sme_batch_set_config": (i, [vp, i, i, i]),
             "sme_batch_destroy": (i, [vp]),
             "sme_seednet_param_count": (i, []),
             "sme_seednet_create": (i, [ip, i, vp]),
@@ -451,6 +453,12 @@ class Batch:
                "sme_batch_config")
         name = {v: k for k, v in SCHEDULES.items()}[s_.value]
         return {"schedule": name, "param": p_.value, "flag": sp_.value, "tuned_ms": ms.value}
+
+    def set_config(self, schedule, param=0, flag=1):
+        """Use one execution configuration instead of tuning ('mb', 'pair' or
+        'sparse'; see sme_batch_set_config)."""
+        _check(_lib().sme_batch_set_config(self._h, SCHEDULES[schedule], int(param), int(flag)),
+               "sme_batch_set_config")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -55,7 +55,7 @@ def test_batch_uneven_sequences_match_oracle(sme):
             v.zero_()
     b.tune(trials=2)                    # every configuration, then a captured graph
     cfg = b.config()
-    assert cfg["tuned_ms"] > 0 and cfg["schedule"] in ("mb", "pair")
+    assert cfg["tuned_ms"] > 0 and cfg["schedule"] in ("mb", "pair", "sparse")
     outs = b.run()
     _check_all(outs, seqs)
     outs = b.run()                      # graph replay keeps the same results
@@ -73,3 +73,43 @@ def test_autotune_context_keeps_results(sme):
     assert np.array_equal(g["mv"].cpu().numpy(), o["mv"])
     assert np.array_equal(g["sse"].cpu().numpy().view(np.uint64), o["sse"])
     est.close()
+
+
+@pytest.mark.parametrize("schedule,param,flag", [("sparse", 1, 1), ("sparse", 2, 0), ("sparse", 2, 1), ("mb", 0, 1),
+                                                 ("pair", 8, 1), ("pair", 4, 0)])
+def test_batch_each_configuration_matches_oracle(sme, schedule, param, flag):
+    """Every execution configuration of a batch, set explicitly, gives the
+    oracle's results on every sequence, on two runs in a row (the second
+    run reuses every scratch buffer of the first)."""
+    seqs = _batch_inputs()
+    lumas = [torch.from_numpy(l).cuda() for l, _ in seqs]
+    alphas = [torch.from_numpy(a).cuda() for _, a in seqs]
+    b = sme.Batch(lumas, alphas, search_range=16, subpel=2,
+                  want=("cost", "disp", "iters", "npos", "mb_class", "sse", "sse_mb", "pred"))
+    b.set_config(schedule, param, flag)
+    assert b.config()["schedule"] == schedule
+    for _ in range(2):
+        outs = b.run()
+        _check_all(outs, seqs)
+        for (luma, alpha), g in zip(seqs, outs):
+            F, H, W = luma.shape
+            o = O.estimate_sequence(O.OracleParams(W, H, 16, 2), luma, alpha, want_pred=True)
+            assert np.array_equal(g["pred"].cpu().numpy(), o["pred"])
+            per = ((luma[1:].astype(np.int64) - o["pred"]) ** 2).reshape(F - 1, H // 16, 16, W // 16, 16)
+            assert np.array_equal(g["sse_mb"].cpu().numpy().astype(np.int64), per.sum(axis=(2, 4)).reshape(F - 1, -1))
+        for o_ in outs:
+            for v in o_.values():
+                v.fill_(0x55) if v.dtype != torch.float32 else v.fill_(float("nan"))
+    b.close()
+
+
+def test_batch_set_config_rejects_bad_values(sme):
+    seqs = _batch_inputs()[:2]
+    b = sme.Batch([torch.from_numpy(l).cuda() for l, _ in seqs], [torch.from_numpy(a).cuda() for _, a in seqs])
+    with pytest.raises(sme.SmeError):
+        b.set_config("cluster")
+    with pytest.raises(sme.SmeError):
+        b.set_config("sparse", 3)
+    with pytest.raises(sme.SmeError):
+        b.set_config("pair", 17)
+    b.close()

@@ -32,13 +32,18 @@ def cuda(a):
 
 # "pair_staged": the pair schedule with every MB staged by TMA (transparent
 # MBs included) instead of finishing transparent runs from global memory.
-SCHEDULES = ["pair", "pair_staged", "mb", "cluster"]
+# "sparse2": the sparse schedule with its search kernel built for two CTAs
+# per SM.
+SCHEDULES = ["pair", "pair_staged", "mb", "cluster", "sparse", "sparse2"]
 
 
 def set_schedule(sme, est, schedule, pair_warps=0):
     if schedule == "pair_staged":
         est.set_schedule("pair", pair_warps=pair_warps)
         est.set_option(sme.SME_OPT_PAIR_DIRECT, 0)
+    elif schedule == "sparse2":
+        est.set_schedule("sparse")
+        est.set_option(sme.SME_OPT_MB_CTAS_PER_SM, 2)
     else:
         est.set_schedule(schedule, pair_warps=pair_warps if schedule == "pair" else 0)
 

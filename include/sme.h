@@ -348,6 +348,18 @@ int sme_batch_synchronize(sme_batch* b);
  * of one run in ms (0 before tuning).  Any output pointer may be NULL. */
 int sme_batch_config(sme_batch* b, int* schedule, int* param, int* flag, float* best_ms);
 int sme_batch_set_config(sme_batch* b, int schedule, int param, int flag);
+/* Two-stage run, for callers that compute seeds from the batch's own MB
+ * classes (the learned proposal): sme_batch_run_stage(b, 1) enqueues the
+ * classification (and, in the sparse schedule, the transparent MBs' results
+ * and the list of the others); afterwards the class map of sequence `seq`,
+ * [n_frames][M] uint8 on the device (classes of every frame, as sme_classify
+ * writes them), is at the address sme_batch_class_map returns, valid until
+ * the next run; seeds written before sme_batch_run_stage(b, 2), which
+ * enqueues the search, are used by it.  Both launch directly on the batch's
+ * stream (no graph; a caller may capture them).  SME_ERR_ARG on a bad stage
+ * or sequence index. */
+int sme_batch_run_stage(sme_batch* b, int stage);
+int sme_batch_class_map(sme_batch* b, int seq, const uint8_t** mb_class);
 int sme_batch_destroy(sme_batch* b);
 
 /* Learned seed proposal (no counterpart in the paper, whose seeds are the
@@ -387,6 +399,11 @@ int sme_batch_destroy(sme_batch* b);
  *                         layers are evaluated only on MBs within one MB of
  *                         such an MB (five 3x3 layers reach 5 cells: one MB
  *                         is 4 cells and the MB's own cells are the fifth).
+ *   sme_seednet_forward_active_table  the same with the class maps given
+ *                         as a DEVICE table rows [n_maps][n] of pointers to
+ *                         [M] class rows (a NULL entry: every MB transparent),
+ *                         so maps written elsewhere (sme_batch_class_map) are
+ *                         read in place.
  *   sme_seednet_set_stream  stream of the network's later calls.
  *   sme_seednet_synchronize waits for the network's stream; SME_ERR_TIMEOUT
  *                         if a device-side wait of an earlier call gave up
@@ -414,6 +431,8 @@ int sme_seednet_forward(sme_seednet* net, const uint16_t* feat, int n, int width
                         float* out_cells);
 int sme_seednet_forward_active(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
                                const uint8_t* mb_class, int n_maps, long long map_stride, float* seeds);
+int sme_seednet_forward_active_table(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
+                                     const uint8_t* const* rows, int n_maps, float* seeds);
 int sme_seednet_set_stream(sme_seednet* net, void* cuda_stream);
 int sme_seednet_synchronize(sme_seednet* net);
 int sme_seednet_gradients(sme_seednet* net, const uint16_t* feat, int n, int width, int height,

@@ -1196,6 +1196,7 @@ struct sme_batch {
     DevStatus* status = nullptr;
     DevBuf descs, packed, cls, ready, sched, sched_seq, unit_seq, unit_pair, fseq, ffrm, maps;
     SparseScratch sp;
+    std::vector<size_t> cls_off;  // byte offset of each sequence's class map [F][M] in cls
     ExecCfg cfg = {kSchedMB, 0, 0, 1, 0, 1};
     float tuned_ms = 0.0f;
     cudaGraph_t graph = nullptr;
@@ -1204,12 +1205,16 @@ struct sme_batch {
 
 namespace {
 
-int batch_enqueue(sme_batch* b, cudaStream_t s)
+// stage 1: the classification launch(es); stage 2: the motion search;
+// 0: both.
+int batch_enqueue(sme_batch* b, cudaStream_t s, int stage = 0)
 {
     if (b->cfg.schedule == kSchedCluster) return SME_ERR_ARG;  // single sequences only
     if (b->cfg.schedule == kSchedSparse) {
-        if (launch_sparse_prep(sparse_args(b->sp, (SeqDesc*)b->descs.p, b->status), nullptr, s) != cudaSuccess)
+        if (stage != 2 &&
+            launch_sparse_prep(sparse_args(b->sp, (SeqDesc*)b->descs.p, b->status), nullptr, s) != cudaSuccess)
             return SME_ERR_CUDA;
+        if (stage == 1) return SME_OK;
         MeArgs a{};
         a.seqs = (const SeqDesc*)b->descs.p;
         a.ready = (unsigned long long*)b->ready.p;
@@ -1222,7 +1227,8 @@ int batch_enqueue(sme_batch* b, cudaStream_t s)
         return launch_sparse_search(b->m, a, b->sp, b->num_sms, b->cfg.mb_ctas_per_sm, s);
     }
     ClassifyBatchArgs ca{(const SeqDesc*)b->descs.p, (const int*)b->fseq.p, (const int*)b->ffrm.p, b->status};
-    if (launch_classify_batch(ca, b->max_mbh, b->total_frames, s) != cudaSuccess) return SME_ERR_CUDA;
+    if (stage != 2 && launch_classify_batch(ca, b->max_mbh, b->total_frames, s) != cudaSuccess) return SME_ERR_CUDA;
+    if (stage == 1) return SME_OK;
     MeArgs a{};
     a.seqs = (const SeqDesc*)b->descs.p;
     a.sched = (const int*)b->sched.p;
@@ -1399,6 +1405,7 @@ int sme_batch_create(sme_batch** out, const sme_params* p, const sme_sequence* s
         e.cls_w = (uint8_t*)b->cls.p + co;
         e.packed = e.packed_w;
         e.cls = e.cls_w;
+        b->cls_off.push_back(co);
         e.temporal_in = x.temporal_in;
         e.seed = x.seed;
         e.mv = x.out.mv;
@@ -1493,6 +1500,19 @@ int sme_batch_run(sme_batch* b)
     if (!b) return SME_ERR_ARG;
     if (b->exec) return cuda_status(cudaGraphLaunch(b->exec, b->stream));
     return batch_enqueue(b, b->stream);
+}
+
+int sme_batch_run_stage(sme_batch* b, int stage)
+{
+    if (!b || (stage != 1 && stage != 2)) return SME_ERR_ARG;
+    return batch_enqueue(b, b->stream, stage);
+}
+
+int sme_batch_class_map(sme_batch* b, int seq, const uint8_t** mb_class)
+{
+    if (!b || !mb_class || seq < 0 || seq >= b->n) return SME_ERR_ARG;
+    *mb_class = (const uint8_t*)b->cls.p + b->cls_off[seq];
+    return SME_OK;
 }
 
 int sme_batch_synchronize(sme_batch* b)

@@ -100,12 +100,30 @@ __global__ void features_kernel(const uint8_t* luma, const uint8_t* const* frame
     dst[1] = o[1];
 }
 
-// An MB counts as non-transparent if it is so in any of n_maps class maps
-// (VOPs over the same frames, maps `stride` bytes apart).
-__device__ __forceinline__ bool any_visible(const uint8_t* cls, int n_maps, long long stride, size_t i)
+// Class maps deciding which MBs use a seed: an MB counts as non-transparent
+// if it is so in any of n_maps maps.  Either `cls`: maps `stride` bytes apart,
+// each [N][M] (pair-major); or `rows`: a device table [n_maps][N] of pointers
+// to [M] class rows (a NULL entry is an empty plane), so the maps can stay
+// wherever another launch wrote them (e.g. a batch's own classification).
+struct ClsMaps {
+    const uint8_t* cls;
+    const uint8_t* const* rows;
+    int n_maps;
+    long long stride;
+    int N, M;
+};
+__device__ __forceinline__ bool any_visible(const ClsMaps& c, size_t i)
 {
-    for (int k = 0; k < n_maps; ++k)
-        if (cls[k * stride + i] != 0) return true;
+    if (c.rows) {
+        const int p = (int)(i / c.M), mb = (int)(i - (size_t)p * c.M);
+        for (int k = 0; k < c.n_maps; ++k) {
+            const uint8_t* r = c.rows[(size_t)k * c.N + p];
+            if (r && r[mb] != 0) return true;
+        }
+        return false;
+    }
+    for (int k = 0; k < c.n_maps; ++k)
+        if (c.cls[k * c.stride + i] != 0) return true;
     return false;
 }
 
@@ -287,8 +305,7 @@ template <int CIN, int COUT>
 __global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(
     const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
     const __nv_bfloat16* __restrict__ mask, int relu, int N, int Hc, int Wc, const int* __restrict__ units,
-    __nv_bfloat16* y16, float* y32, float* seeds, const uint8_t* __restrict__ cls, int n_maps, long long map_stride,
-    int* err)
+    __nv_bfloat16* y16, float* y32, float* seeds, const ClsMaps cm, int* err)
 {
     static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= kAccCols, "tile shape");
     using L = ConvLayout<CIN, COUT>;
@@ -435,7 +452,7 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(
                 if ((lane & 0x1B) == 0 && inside) {
                     const int mbw = Wc >> 2, mb = (i_cell >> 2) * mbw + (j_cell >> 2);
                     const size_t id = (size_t)n * mbw * (Hc >> 2) + mb;
-                    if (!cls || any_visible(cls, n_maps, map_stride, id)) {
+                    if ((!cm.cls && !cm.rows) || any_visible(cm, id)) {
                         seeds[2 * id] = kSeedScale * s0 / 16.0f;
                         seeds[2 * id + 1] = kSeedScale * s1 / 16.0f;
                     }
@@ -493,8 +510,7 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(
 // MB columns 2tc, 2tc+1.
 // units[0] = count (zeroed by the caller), units[1..] = tile indices in no
 // particular order (a tile's arithmetic does not depend on it).
-__global__ void active_tiles_kernel(const uint8_t* __restrict__ cls, int n_maps, long long stride, int N, int mbw,
-                                    int mbh, int TR, int TC, int* units)
+__global__ void active_tiles_kernel(const ClsMaps cm, int N, int mbw, int mbh, int TR, int TC, int* units)
 {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= N * TR * TC) return;
@@ -503,7 +519,7 @@ __global__ void active_tiles_kernel(const uint8_t* __restrict__ cls, int n_maps,
     bool act = false;
     for (int v = 4 * tr - 1; v <= 4 * tr + 4 && !act; ++v)
         for (int u = 2 * tc - 1; u <= 2 * tc + 2; ++u)
-            if (v >= 0 && v < mbh && u >= 0 && u < mbw && any_visible(cls, n_maps, stride, n * M + v * mbw + u)) {
+            if (v >= 0 && v < mbh && u >= 0 && u < mbw && any_visible(cm, n * M + v * mbw + u)) {
                 act = true;
                 break;
             }
@@ -706,7 +722,7 @@ int resident_ctas(const void* f, int threads, int dyn_smem)
 template <int CIN, int COUT>
 cudaError_t conv(const __nv_bfloat16* x, const __nv_bfloat16* w, const float* b, const __nv_bfloat16* mask, int relu,
                  int N, int Hc, int Wc, const int* units, __nv_bfloat16* y16, float* y32, float* seeds,
-                 const uint8_t* cls, int n_maps, long long map_stride, int* err, cudaStream_t s)
+                 const ClsMaps& cm, int* err, cudaStream_t s)
 {
     using L = ConvLayout<CIN, COUT>;
     static int per_sm = 0;  // CTAs per SM of this instance
@@ -733,7 +749,7 @@ cudaError_t conv(const __nv_bfloat16* x, const __nv_bfloat16* w, const float* b,
     int grid = (int)std::min(tiles, (long long)per_sm * g_conv_sms);
     if (grid < 1) grid = 1;
     conv3x3_tc_kernel<CIN, COUT><<<grid, kConvThreads, L::bytes, s>>>(map, w, b, mask, relu, N, Hc, Wc, units, y16,
-                                                                       y32, seeds, cls, n_maps, map_stride, err);
+                                                                       y32, seeds, cm, err);
     return cudaGetLastError();
 }
 
@@ -780,11 +796,12 @@ int woff_of(int l)
 }
 
 // Layers 0..4.  With seeds the last layer's epilogue pools the per-MB seeds
-// (cls: only MBs visible in one of the n_maps class maps); otherwise its
-// output goes to out32.
+// (with class maps: only MBs visible in one of them); otherwise its output
+// goes to out32.
 int forward(sme_seednet* s, const __nv_bfloat16* feat, int N, int Hc, int Wc, const int* units = nullptr,
-            float* seeds = nullptr, const uint8_t* cls = nullptr, int n_maps = 0, long long map_stride = 0)
+            float* seeds = nullptr, const ClsMaps& cm = ClsMaps{})
 {
+    const ClsMaps none{};
     cudaStream_t st = s->stream;
     const float* b[kLayers];
     const __nv_bfloat16* w[kLayers];
@@ -793,16 +810,12 @@ int forward(sme_seednet* s, const __nv_bfloat16* feat, int N, int Hc, int Wc, co
         b[l] = s->master + loff(l) + wsize(l);
     }
     int* e = s->err;
-    if (conv<16, 32>(feat, w[0], b[0], nullptr, 1, N, Hc, Wc, units, s->act[1], nullptr, nullptr, nullptr, 0, 0, e,
-                     st) ||
-        conv<32, 32>(s->act[1], w[1], b[1], nullptr, 1, N, Hc, Wc, units, s->act[2], nullptr, nullptr, nullptr, 0, 0,
-                     e, st) ||
-        conv<32, 32>(s->act[2], w[2], b[2], nullptr, 1, N, Hc, Wc, units, s->act[3], nullptr, nullptr, nullptr, 0, 0,
-                     e, st) ||
-        conv<32, 32>(s->act[3], w[3], b[3], nullptr, 1, N, Hc, Wc, units, s->act[4], nullptr, nullptr, nullptr, 0, 0,
-                     e, st) ||
+    if (conv<16, 32>(feat, w[0], b[0], nullptr, 1, N, Hc, Wc, units, s->act[1], nullptr, nullptr, none, e, st) ||
+        conv<32, 32>(s->act[1], w[1], b[1], nullptr, 1, N, Hc, Wc, units, s->act[2], nullptr, nullptr, none, e, st) ||
+        conv<32, 32>(s->act[2], w[2], b[2], nullptr, 1, N, Hc, Wc, units, s->act[3], nullptr, nullptr, none, e, st) ||
+        conv<32, 32>(s->act[3], w[3], b[3], nullptr, 1, N, Hc, Wc, units, s->act[4], nullptr, nullptr, none, e, st) ||
         conv<32, 16>(s->act[4], w[4], b[4], nullptr, 0, N, Hc, Wc, units, nullptr, seeds ? nullptr : s->out32, seeds,
-                     cls, n_maps, map_stride, e, st))
+                     cm, e, st))
         return SME_ERR_CUDA;
     return SME_OK;
 }
@@ -835,15 +848,16 @@ int backward(sme_seednet* s, const __nv_bfloat16* feat, int N, int Hc, int Wc, c
         dw[l] = s->grad + loff(l);
         db[l] = s->grad + loff(l) + wsize(l);
     }
+    const ClsMaps none{};
     // layer 4 (32 -> 16): weights from act[4] and d0; input gradient into d1 (masked by act[4])
     if (wgrad<32, 16>(s->act[4], s->d0, N, Hc, Wc, dw[4], db[4], s->sms, st) ||
-        conv<16, 32>(s->d0, wt[4], nullptr, s->act[4], 0, N, Hc, Wc, nullptr, s->d1, nullptr, nullptr, nullptr, 0, 0, s->err, st) ||
+        conv<16, 32>(s->d0, wt[4], nullptr, s->act[4], 0, N, Hc, Wc, nullptr, s->d1, nullptr, nullptr, none, s->err, st) ||
         wgrad<32, 32>(s->act[3], s->d1, N, Hc, Wc, dw[3], db[3], s->sms, st) ||
-        conv<32, 32>(s->d1, wt[3], nullptr, s->act[3], 0, N, Hc, Wc, nullptr, s->d0, nullptr, nullptr, nullptr, 0, 0, s->err, st) ||
+        conv<32, 32>(s->d1, wt[3], nullptr, s->act[3], 0, N, Hc, Wc, nullptr, s->d0, nullptr, nullptr, none, s->err, st) ||
         wgrad<32, 32>(s->act[2], s->d0, N, Hc, Wc, dw[2], db[2], s->sms, st) ||
-        conv<32, 32>(s->d0, wt[2], nullptr, s->act[2], 0, N, Hc, Wc, nullptr, s->d1, nullptr, nullptr, nullptr, 0, 0, s->err, st) ||
+        conv<32, 32>(s->d0, wt[2], nullptr, s->act[2], 0, N, Hc, Wc, nullptr, s->d1, nullptr, nullptr, none, s->err, st) ||
         wgrad<32, 32>(s->act[1], s->d1, N, Hc, Wc, dw[1], db[1], s->sms, st) ||
-        conv<32, 32>(s->d1, wt[1], nullptr, s->act[1], 0, N, Hc, Wc, nullptr, s->d0, nullptr, nullptr, nullptr, 0, 0, s->err, st) ||
+        conv<32, 32>(s->d1, wt[1], nullptr, s->act[1], 0, N, Hc, Wc, nullptr, s->d0, nullptr, nullptr, none, s->err, st) ||
         wgrad<16, 32>(feat, s->d0, N, Hc, Wc, dw[0], db[0], s->sms, st))
         return SME_ERR_CUDA;
     if (loss_host) {
@@ -984,22 +998,48 @@ int sme_seednet_forward(sme_seednet* s, const uint16_t* feat, int n, int width, 
     return SME_OK;
 }
 
+// The sparse forward for class maps given either way (see ClsMaps).
+static int forward_active(sme_seednet* s, const uint16_t* feat, int n, int width, int height, const ClsMaps& cm,
+                          float* seeds)
+{
+    const int Hc = height / 4, Wc = width / 4, M = n * (Hc / 4) * (Wc / 4);
+    const int TR = (Hc + kTileH - 1) / kTileH, TC = (Wc + kTileW - 1) / kTileW, T = n * TR * TC;
+    if (cudaMemsetAsync(s->units, 0, sizeof(int), s->stream) != cudaSuccess) return SME_ERR_CUDA;
+    active_tiles_kernel<<<(T + 127) / 128, 128, 0, s->stream>>>(cm, n, Wc / 4, Hc / 4, TR, TC, s->units);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemsetAsync(seeds, 0, sizeof(float) * 2 * (size_t)M, s->stream) != cudaSuccess)
+        return SME_ERR_CUDA;
+    return forward(s, reinterpret_cast<const __nv_bfloat16*>(feat), n, Hc, Wc, s->units, seeds, cm);
+}
+
 int sme_seednet_forward_active(sme_seednet* s, const uint16_t* feat, int n, int width, int height,
                                const uint8_t* mb_class, int n_maps, long long map_stride, float* seeds)
 {
     int rc = check_geom(s, feat, n, width, height);
     if (rc) return rc;
-    const int Hc = height / 4, Wc = width / 4, M = n * (Hc / 4) * (Wc / 4);
+    const int M = n * (height / 16) * (width / 16);
     if (!mb_class || !seeds || n_maps < 1 || (n_maps > 1 && map_stride < M)) return SME_ERR_ARG;
-    const int TR = (Hc + kTileH - 1) / kTileH, TC = (Wc + kTileW - 1) / kTileW, T = n * TR * TC;
-    if (cudaMemsetAsync(s->units, 0, sizeof(int), s->stream) != cudaSuccess) return SME_ERR_CUDA;
-    active_tiles_kernel<<<(T + 127) / 128, 128, 0, s->stream>>>(mb_class, n_maps, map_stride, n, Wc / 4, Hc / 4, TR,
-                                                                TC, s->units);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemsetAsync(seeds, 0, sizeof(float) * 2 * (size_t)M, s->stream) != cudaSuccess)
-        return SME_ERR_CUDA;
-    return forward(s, reinterpret_cast<const __nv_bfloat16*>(feat), n, Hc, Wc, s->units, seeds, mb_class, n_maps,
-                   map_stride);
+    ClsMaps cm{};
+    cm.cls = mb_class;
+    cm.n_maps = n_maps;
+    cm.stride = map_stride;
+    cm.N = n;
+    cm.M = (height / 16) * (width / 16);
+    return forward_active(s, feat, n, width, height, cm, seeds);
+}
+
+int sme_seednet_forward_active_table(sme_seednet* s, const uint16_t* feat, int n, int width, int height,
+                                     const uint8_t* const* rows, int n_maps, float* seeds)
+{
+    int rc = check_geom(s, feat, n, width, height);
+    if (rc) return rc;
+    if (!rows || !seeds || n_maps < 1) return SME_ERR_ARG;
+    ClsMaps cm{};
+    cm.rows = rows;
+    cm.n_maps = n_maps;
+    cm.N = n;
+    cm.M = (height / 16) * (width / 16);
+    return forward_active(s, feat, n, width, height, cm, seeds);
 }
 
 int sme_seednet_synchronize(sme_seednet* s)

@@ -234,14 +234,14 @@ def chunk_plan(shapes, max_cells, ref_distance=1):
 
 class LearnedBatch:
     """The learned-seeded form of a batch.  Sequences of one frame size are
-    gathered into chunks (as many as the network's capacity holds): per chunk
-    one classification launch over the current frames of every VOP, one
-    features launch over every pair (both reading frame-address tables) and
-    one sparse forward for the MBs visible in any VOP of any of its sequences
-    (the VOPs of a sequence share features, hence seeds); then every VOP in
-    one persistent launch (sme_batch) with those seeds.  The classification
-    and network launches are captured in one CUDA graph, replayed before the
-    batch's own graph, on one stream.
+    gathered into chunks (as many as the network's capacity holds).  A run
+    is: the batch's classification stage (sme_batch_run_stage 1), then per
+    chunk one features launch over every pair (reading a frame-address
+    table) and one sparse forward for the MBs visible in any VOP of any of
+    its sequences, reading the batch's own class maps in place through a
+    table of class-row addresses (the VOPs of a sequence share features,
+    hence seeds), then the batch's search stage with those seeds.  Once
+    tuned, the whole run is one CUDA graph on one stream.
 
     groups: list of (luma [F, H, W] CUDA uint8, [alpha [F, H, W] CUDA uint8, ...])."""
 
@@ -252,63 +252,70 @@ class LearnedBatch:
         self.torch, self.net, self.subpel, self.rd = torch, net, subpel, ref_distance
         self.stream = torch.cuda.Stream()
         self.graph = None
-        self.chunks, self.est = [], {}
+        self.chunks = []
         rd = ref_distance
         plan = chunk_plan([tuple(luma.shape) + (len(alist),) for luma, alist in groups], net.max_cells, rd)
-        seeds_of = {}
+        seeds_of, chunk_rows = {}, []
         with torch.cuda.stream(self.stream):
             for H, W, members, n, V in plan:
-                if (W, H) not in self.est:
-                    self.est[(W, H)] = sme.Estimator(W, H, search_range=search_range, subpel=subpel,
-                                                     ref_distance=rd)
-                est = self.est[(W, H)]
                 dev = groups[members[0][0]][0].device
-                cls = torch.zeros((V, n, est.M), dtype=torch.uint8, device=dev)
+                M = (W // 16) * (H // 16)
                 feat = torch.empty((n, H // 4, W // 4, 16), dtype=torch.int16, device=dev)
-                seeds = torch.zeros((n, est.M, 2), dtype=torch.float32, device=dev)
-                # frame-address tables: class map row (VOP j, pair i) <- the current alpha
-                # frame of pair i (0: the sequence has no VOP j, an empty plane); feature
-                # row i <- the pair's reference and current luma frames
+                seeds = torch.zeros((n, M, 2), dtype=torch.float32, device=dev)
                 FS = H * W
-                cls_ptr = [[0] * n for _ in range(V)]
                 feat_ptr = []
                 for i, off, P in members:
-                    luma, alist = groups[i]
+                    luma, _ = groups[i]
                     for p in range(P):
-                        for j, a in enumerate(alist):
-                            cls_ptr[j][off + p] = a.data_ptr() + (p + rd) * FS
                         feat_ptr.append((luma.data_ptr() + p * FS, luma.data_ptr() + (p + rd) * FS))
                     seeds_of[i] = seeds[off:off + P]
-                cls_tab = torch.tensor(cls_ptr, dtype=torch.int64, device=dev).reshape(-1)
                 feat_tab = torch.tensor(feat_ptr, dtype=torch.int64, device=dev)
-                self.chunks.append((est, cls, feat, seeds, cls_tab, feat_tab, W, H))
-            lumas, alphas, seeds_list = [], [], []
+                self.chunks.append([feat, seeds, feat_tab, None, V, W, H])
+                chunk_rows.append((members, n, V, M))
+            lumas, alphas, seeds_list, vop_index = [], [], [], {}
             for i, (luma, alist) in enumerate(groups):  # VOP order = the caller's order
-                for a in alist:
+                for j, a in enumerate(alist):
+                    vop_index[(i, j)] = len(lumas)
                     lumas.append(luma)
                     alphas.append(a)
                     seeds_list.append(seeds_of[i])
             self.batch = sme.Batch(lumas, alphas, search_range=search_range, subpel=subpel,
                                    ref_distance=ref_distance, want=want, seed_list=seeds_list)
+            # class-row table of each chunk: row (VOP j, pair i) <- the batch's class
+            # map of that VOP at the pair's current frame (0: the sequence has no VOP j)
+            for c, (members, n, V, M) in zip(self.chunks, chunk_rows):
+                rows = [[0] * n for _ in range(V)]
+                for i, off, P in members:
+                    for j in range(len(groups[i][1])):
+                        base = self.batch.class_map_ptr(vop_index[(i, j)])
+                        for p in range(P):
+                            rows[j][off + p] = base + (p + rd) * M
+                c[3] = torch.tensor(rows, dtype=torch.int64, device=c[0].device).reshape(-1)
         self.outputs = self.batch.outputs
         self.seeds = seeds_list
 
     def _seed_pass(self):
-        for est, cls, feat, seeds, cls_tab, feat_tab, W, H in self.chunks:
-            est.classify_table(cls_tab, out=cls.view(-1, est.M), sync=False)
+        for feat, seeds, feat_tab, rows, V, W, H in self.chunks:
             self.net.features_table(feat_tab, W, H, subpel=self.subpel, out=feat)
-            self.net.forward_active(feat, cls, out=seeds)
+            self.net.forward_active_table(feat, rows, V, out=seeds)
+
+    def _run_direct(self):
+        self.batch.run_stage(1)
+        self._seed_pass()
+        self.batch.run_stage(2)
 
     def tune(self, trials=3):
-        """Seeds once, the batch's autotuner, then the capture of the seed pass."""
+        """Seeds once, the batch's autotuner, then the capture of a whole run
+        (classification stage, seed pass, search stage) in one graph."""
         t = self.torch
         with t.cuda.stream(self.stream):
+            self.batch.run_stage(1)
             self._seed_pass()
             self.batch.tune(trials)
             self.stream.synchronize()
             g = t.cuda.CUDAGraph()
             with t.cuda.graph(g, stream=self.stream):
-                self._seed_pass()
+                self._run_direct()
             self.graph = g
 
     def run(self, sync=True):
@@ -316,8 +323,7 @@ class LearnedBatch:
             if self.graph is not None:
                 self.graph.replay()
             else:
-                self._seed_pass()
-            self.batch.run(sync=False)
+                self._run_direct()
         if sync:
             self.batch.synchronize()
         return self.outputs
@@ -330,6 +336,3 @@ class LearnedBatch:
 
     def close(self):
         self.batch.close()
-        for e in self.est.values():
-            e.close()
-        self.est = {}

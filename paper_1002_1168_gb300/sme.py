@@ -35,7 +35,7 @@ EXPORTS = [
     "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_get_option", "sme_autotune",
     "sme_full_search",
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
-    "sme_batch_set_config",
+    "sme_batch_set_config", "sme_batch_run_stage", "sme_batch_class_map", "sme_seednet_forward_active_table",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_features_table",
     "sme_seednet_forward",
@@ -119,6 +119,9 @@ def _lib():
             "sme_batch_config": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_float)]),
             "sme_batch_set_config": (i, [vp, i, i, i]),
+            "sme_batch_run_stage": (i, [vp, i]),
+            "sme_batch_class_map": (i, [vp, i, C.POINTER(C.c_void_p)]),
+            "sme_seednet_forward_active_table": (i, [vp, vp, i, i, i, vp, i, vp]),
             "sme_batch_destroy": (i, [vp]),
             "sme_seednet_param_count": (i, []),
             "sme_seednet_create": (i, [ip, i, vp]),
@@ -454,6 +457,16 @@ class Batch:
         name = {v: k for k, v in SCHEDULES.items()}[s_.value]
         return {"schedule": name, "param": p_.value, "flag": sp_.value, "tuned_ms": ms.value}
 
+    def run_stage(self, stage):
+        """Enqueue stage 1 (classification) or 2 (search) of one run."""
+        _check(_lib().sme_batch_run_stage(self._h, int(stage)), "sme_batch_run_stage")
+
+    def class_map_ptr(self, i):
+        """Device address of sequence i's class map [F, M] (uint8)."""
+        p = C.c_void_p()
+        _check(_lib().sme_batch_class_map(self._h, int(i), C.byref(p)), "sme_batch_class_map")
+        return p.value
+
     def set_config(self, schedule, param=0, flag=1):
         """Use one execution configuration instead of tuning ('mb', 'pair' or
         'sparse'; see sme_batch_set_config)."""
@@ -540,6 +553,17 @@ class SeedNet:
         _check(_lib().sme_seednet_forward(self._bind(), _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(seeds), _ptr(cells)),
                "sme_seednet_forward")
         return (seeds, cells) if want_cells else seeds
+
+    def forward_active_table(self, feat, rows, n_maps, out=None):
+        """forward_active with the class maps as a device table [n_maps, n]
+        (int64 CUDA tensor) of row addresses; 0 = an empty plane."""
+        n, Hc, Wc, _ = feat.shape
+        t = self.torch
+        M = (Hc // 4) * (Wc // 4)
+        out = out if out is not None else t.empty((n, M, 2), dtype=t.float32, device=feat.device)
+        _check(_lib().sme_seednet_forward_active_table(self._bind(), _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(rows),
+                                                        int(n_maps), _ptr(out)), "sme_seednet_forward_active_table")
+        return out
 
     def forward_active(self, feat, mb_class, out=None):
         """Seeds of the non-transparent MBs, (0, 0) on the others; the layers

@@ -113,3 +113,45 @@ def test_batch_set_config_rejects_bad_values(sme):
     with pytest.raises(sme.SmeError):
         b.set_config("pair", 17)
     b.close()
+
+
+def _read_device(ptr, nbytes):
+    """Bytes at a raw device address (the CUDA runtime's cudaMemcpy through
+    ctypes; the library hands out addresses it owns, not tensors)."""
+    import ctypes as C
+
+    rt = None
+    for name in ("/usr/local/cuda/lib64/libcudart.so", "libcudart.so"):
+        try:
+            rt = C.CDLL(name)
+            break
+        except OSError:
+            pass
+    if rt is None:
+        pytest.skip("CUDA runtime library not found")
+    out = np.empty(nbytes, np.uint8)
+    torch.cuda.synchronize()
+    assert rt.cudaMemcpy(C.c_void_p(out.ctypes.data), C.c_void_p(ptr), C.c_size_t(nbytes), 2) == 0
+    return out
+
+
+@pytest.mark.parametrize("schedule,param,flag", [("sparse", 2, 0), ("mb", 0, 1), ("pair", 8, 1)])
+def test_batch_two_stage_run_and_class_maps(sme, schedule, param, flag):
+    """Stage 1 then stage 2 equals a whole run; after stage 1 each sequence's
+    class map [F, M] holds the oracle's class of every MB of every frame."""
+    seqs = _batch_inputs()
+    lumas = [torch.from_numpy(l).cuda() for l, _ in seqs]
+    alphas = [torch.from_numpy(a).cuda() for _, a in seqs]
+    b = sme.Batch(lumas, alphas, search_range=16, subpel=2)
+    b.set_config(schedule, param, flag)
+    b.run_stage(1)
+    for i, (luma, alpha) in enumerate(seqs):
+        F, H, W = luma.shape
+        M = (W // 16) * (H // 16)
+        got = _read_device(b.class_map_ptr(i), F * M).reshape(F, M)
+        want = np.stack([O.classify_frame(alpha[f]) for f in range(F)])
+        assert np.array_equal(got, want), i
+    b.run_stage(2)
+    b.synchronize()
+    _check_all(b.outputs, seqs)
+    b.close()

@@ -197,3 +197,30 @@ def test_adam_update_matches_oracle(sme):
         assert np.any(got != prev)  # the parameters moved
         prev = got
     net.close()
+
+
+def test_forward_active_table_equals_strided_maps(sme):
+    """The class maps given as a table of class-row addresses (some rows
+    absent: an empty plane) select the same MBs, hence the same seeds, as the
+    same maps given as one strided tensor."""
+    _, params, x, net, xt = _setup(sme, N=3)
+    N, Hc, Wc, _ = x.shape
+    M = (Hc // 4) * (Wc // 4)
+    rng = np.random.default_rng(12)
+    cls = np.zeros((2, N, M), np.uint8)
+    cls[0, 0, rng.choice(M, 5, replace=False)] = 1
+    cls[1, 1, rng.choice(M, 4, replace=False)] = 2
+    cls[0, 2, :] = 1
+    ct = torch.from_numpy(cls).cuda()
+    want = net.forward_active(xt, ct).cpu().numpy()
+    rows = torch.tensor([[ct[j, i].data_ptr() for i in range(N)] for j in range(2)], dtype=torch.int64).cuda()
+    got = net.forward_active_table(xt, rows.reshape(-1), 2).cpu().numpy()
+    assert np.array_equal(got, want)
+    # an absent row (0) is an empty plane: map 1 of pair 1 dropped
+    rows[1, 1] = 0
+    cls2 = cls.copy()
+    cls2[1, 1] = 0
+    want2 = net.forward_active(xt, torch.from_numpy(cls2).cuda()).cpu().numpy()
+    got2 = net.forward_active_table(xt, rows.reshape(-1), 2).cpu().numpy()
+    assert np.array_equal(got2, want2)
+    net.close()

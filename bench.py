@@ -1,22 +1,33 @@
 """Benchmark of the shape-adaptive motion estimation pass on one GB300.
 
 One step = the whole per-MB pass (classification, block recursive search,
-pixel recursive search, motion compensation + SSE) over one synthetic CIF
-352x288 sequence of 30 frames (29 frame pairs, one video object, half-pel,
-search range 16), with inputs resident in device memory.  The metric is
-macroblocks per second over all frame-grid MBs of all pairs.
+pixel recursive search, motion compensation + SSE) over the largest
+workload that fits one GPU: 16 synthetic sequences of 3840x2160, 60 frames,
+8 video objects (VOPs) each -- 128 VOPs, 244.7 M macroblock estimates --
+search range 32, half-pel, rendered on the device (inputs 72 GB, far above
+L2).  `value` is the learned-seeded form (a seed network trained here on the
+GPU, seeds as a fifth candidate with the plain search as fallback) in
+macroblocks per second over all frame-grid MBs; the plain batched form is
+timed beside it in the same line.  Both are one persistent batch replayed
+from a CUDA graph.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-The same line carries the learned-seeded form: a seed network trained here
-on the GPU (2000 CIF VOP pairs, labelled by the plain method), then the
-learned-seeded pass on the same workload (quality.learned_seeded) and on the
-batched workload (batched.learned_seeded), each checked against the oracle
-given the same seeds.
+The same line carries: the device time of each stage and the roofline of the
+dominant kernel; the end-to-end rate through the host-buffer calls
+(sme_batch_upload / sme_batch_download); the CPU oracle on the first two
+pairs of every VOP on all host cores, with the plain field checked against
+it; sampled pairs of the learned field against the oracle given the same
+seeds.  Secondary keys: the CIF 352x288 x 30-frame single sequence (cif30:
+plain, end to end, exhaustive search, four vectors per MB, learned), the
+64-sequence batch of uneven sizes (batched), the 1920x1088 x 300-frame,
+4-VOP learned evaluation (hd_learned_eval) and the paper's QCIF setting
+(paper_setup).
 
---impl reference times the CPU oracle (single-threaded C) on the same workload.
+--impl reference times the CPU oracle on a bounded sample of the headline
+workload (the first two pairs of every VOP), one VOP per host thread.
 Under torchrun (N > 1) every rank runs an independent replica (its own
-sequence); the data path has no collective, so scaling is weak.
+scenes); the data path has no collective, so scaling is weak.
 """
 from __future__ import annotations
 
@@ -38,6 +49,7 @@ METRIC = "macroblocks/s (MV field matches oracle) learned-seeded vs plain; iters
 UNIT = "MB/s"
 W, H, FRAMES, S, SUBPEL = 352, 288, 30, 16, 2
 WORKLOAD = "CIF 352x288, 30 frames (29 pairs), 1 VOP, half-pel, S=16"
+UHD_W, UHD_H, UHD_S = 3840, 2160, 32  # the headline workload's frame size and search range
 OUT_FIELDS = ("cost", "disp", "iters", "npos", "mb_class", "sse")
 
 
@@ -141,6 +153,10 @@ def peaks():
 # ncu capture summarised in profiles/me_kernel_cif30_halfpel.md (set to None
 # whenever the kernel changes until it is captured again).
 ME_KERNEL_TRAFFIC_BYTES = 3510016 + 13568
+# DRAM bytes of one sparse search launch of the headline's learned run, from
+# an ncu capture scaled as the profile summary states (None until captured
+# for the current kernel).
+SEARCH_KERNEL_TRAFFIC_BYTES = None
 
 
 def algorithmic_bytes(P, M, F):
@@ -170,29 +186,57 @@ def algorithmic_int_ops(res):
     return int(192 * npos[op].sum() + 1280 * iters[op].sum() + 64 * npos[bd].sum() + 192 * cls.size)
 
 
+def uhd_oracle_sample(seed=1005, n_seq=16, frames=60, keep=3):
+    """The first `keep` frames of every sequence of the headline workload
+    (the same scenes as synth_gpu.uhd_batch; only those frames are rendered,
+    on the GPU when there is one): the bounded sample the CPU oracle runs."""
+    import torch
+
+    from paper_1002_1168_gb300 import synth_gpu
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    out = []
+    rng = np.random.default_rng(seed)
+    for i in range(n_seq):
+        luma, alpha, _ = synth_gpu.make_sequence_gpu(
+            UHD_W, UHD_H, frames, seed * 1000 + i, n_objects=8, vmax=32.0, bg_step=tuple(rng.uniform(-4, 4, 2)),
+            noise_sigma=2.0, change_every=20, max_rot_deg=3.0, scale_range=(1.0, 1.0), obj_frac=0.35, device=dev,
+            render_frames=keep)
+        out.append((luma.cpu().numpy(), alpha.cpu().numpy()))
+    return out
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle (as it stands) on a bounded sample of
+    the headline workload -- the first two frame pairs of every VOP of the
+    16 x 3840x2160 x 60-frame batch, plain method -- one VOP per host thread."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle as O
 
-    seq = workload(0)
-    p = O.OracleParams(W, H, S, SUBPEL)
-    P = FRAMES - 1
+    sample = uhd_oracle_sample(n_seq=args.scale_seqs, frames=args.scale_frames)
+    p = O.OracleParams(UHD_W, UHD_H, UHD_S, 2)
+    units = [(p, l, a[j], None) for l, a in sample for j in range(a.shape[0])]
+    threads = os.cpu_count() or 1
+    M = (UHD_W // 16) * (UHD_H // 16)
+    mbs = len(units) * 2 * M
     for _ in range(args.warmup):
-        O.estimate_sequence(p, seq.luma, seq.alpha[0])
-    t0 = time.perf_counter()
+        oracle_units(units, threads)
+    dt = 0.0
     for _ in range(args.steps):
-        O.estimate_sequence(p, seq.luma, seq.alpha[0])
-    dt = time.perf_counter() - t0
-    mbs = P * p.mbs * args.steps
-    v = mbs / dt
+        dt += oracle_units(units, threads)[1]
+    v = mbs * args.steps / dt
+    smp = (f"first 2 pairs of every VOP of the headline workload ({len(units)} VOPs, {mbs} MBs per step), "
+           f"plain method, one VOP per thread on {threads} threads")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8+f32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "pairs": P, "mbs_per_step": P * p.mbs},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full passes over the workload, single-threaded C"},
+            "data": "synthetic",
+            "config": {"workload": uhd_workload(args.scale_seqs, args.scale_frames), "mbs_per_step": mbs,
+                       "sample": smp},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": smp,
+                             **host_cpu()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -628,34 +672,318 @@ def measure_paper_setup(sme, torch):
             "bit_exact_vs_oracle": bool(exact), "es_bit_exact_vs_oracle_sample": es_ok, "four_mv": four_mv}
 
 
-def measure_at_scale(sme, torch, args, params, dist):
-    """Learned proposal + batching at scale: 16 sequences of 3840x2160, 60
-    frames, 8 objects (8 VOPs) each, |v| <= 32, rotation <= 3 deg, S = 32,
-    half-pel, rendered on the device; the plain batch and the learned batch
-    (seed network with the trained weights), both autotuned and replayed
-    from CUDA graphs; the oracle on one sampled pair of each (given the GPU's
-    previous field and the seeds)."""
+def uhd_workload(n_seq, frames):
+    return (f"{n_seq} sequences of 3840x2160, {frames} frames, 8 VOPs each ({8 * n_seq} VOPs), |v| <= 32 px, "
+            "rotation <= 3 deg, S=32, half-pel, rendered on the device")
+
+
+def stage_times(torch, run_stage, seed_pass, stream, steps):
+    """Device time of each stage of a run (events on the run's stream):
+    stage 1 (classification: the sparse schedule's streaming pass, count,
+    scan, scatter), the seed pass (learned form), stage 2 (the search: one
+    me_sparse_kernel launch).  Returns the mean ms of each."""
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for e in ev:
+            e[0].record(stream)
+            run_stage(1)
+            e[1].record(stream)
+            if seed_pass:
+                seed_pass()
+            e[2].record(stream)
+            run_stage(2)
+            e[3].record(stream)
+    torch.cuda.synchronize()
+    return tuple(sum(e[i].elapsed_time(e[i + 1]) for e in ev) / steps for i in range(3))
+
+
+def _int_ops_device(torch, outputs):
+    """Algorithmic integer operations of a run from the method's own counters
+    (see algorithmic_int_ops), summed on the device."""
+    tot = 0
+    for o in outputs:
+        cls, npos, it = o["mb_class"], o["npos"].to(torch.int64), o["iters"].to(torch.int64)
+        op, bd = cls == 1, cls == 2
+        tot += int(192 * npos[op].sum() + 1280 * it[op].sum() + 64 * npos[bd].sum() + 192 * cls.numel())
+    return tot
+
+
+def uhd_alg_bytes(n_vops, n_luma, F, total_mbs, transparent_mbs=None):
+    """Algorithmic DRAM bytes of one run: every VOP's u8 alpha plane once,
+    every distinct luma plane once (the VOPs of a scene share it), 19 output
+    bytes per MB (vector 4, cost 4, update 8, steps, positions, class) and 8
+    per pair of each VOP.  With transparent_mbs: the streaming pass's share
+    (alpha, luma, the transparent MBs' outputs)."""
+    fs = UHD_W * UHD_H
+    inputs = n_vops * F * fs + n_luma * F * fs
+    mbs = total_mbs if transparent_mbs is None else transparent_mbs
+    return inputs + 19 * mbs + 8 * n_vops * (F - 1)
+
+
+def oracle_units(units, threads):
+    """The oracle on independent (params, luma, alpha, seed) units on `threads`
+    host threads (the C library releases the GIL), with the wall time."""
+    import oracle as O
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(u):
+        p, l, a, sd = u
+        return O.estimate_sequence(p, l, a, seed=sd)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(one, units))
+    return res, time.perf_counter() - t0
+
+
+def host_cpu():
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def sized_net(sme, net, max_cells):
+    """A network with net's trained parameters and room for max_cells cells."""
+    big = sme.SeedNet(max_cells=max_cells)
+    big.set_params(net.get_params())
+    return big
+
+
+def measure_headline(sme, torch, args, net, dist, rank):
+    """The headline: learned proposal + batching at scale, 16 sequences of
+    3840x2160, 60 frames, 8 VOPs each (|v| <= 32 px, rotation <= 3 deg),
+    S = 32, half-pel, rendered on the device (inputs 72 GB: far above L2).
+    The plain batch and the learned batch (the network trained in this run)
+    are both autotuned and replayed from CUDA graphs; `steps` timed runs of
+    each.  Also: device time per stage, end to end through the host-buffer
+    calls, the oracle on the first two pairs of every VOP on the host's
+    cores (with the plain field checked against it) and on sampled pairs of
+    the learned field given the same seeds."""
     import gc
 
     import oracle as O
     from paper_1002_1168_gb300 import seedtrain, synth_gpu
 
-    W4, H4, S4 = 3840, 2160, 32
+    ws = dist.get_world_size() if dist else 1
     t0 = time.perf_counter()
-    seqs = synth_gpu.uhd_batch(seed=1005, n_seq=args.scale_seqs, frames=args.scale_frames)
+    seqs = synth_gpu.uhd_batch(seed=1005 + 100 * rank, n_seq=args.scale_seqs, frames=args.scale_frames)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     F = seqs[0][0].shape[0]
+    P, M = F - 1, (UHD_W // 16) * (UHD_H // 16)
     groups = [(l, [a[j] for j in range(a.shape[0])]) for l, a, _ in seqs]
     lumas = [l for l, vops in groups for _ in vops]
     alphas = [a for _, vops in groups for a in vops]
-    total = len(alphas) * (F - 1) * (W4 // 16) * (H4 // 16)
-    n_seq, n_vops = len(seqs), len(alphas)
+    n_vops, n_seq = len(alphas), len(seqs)
+    total = n_vops * P * M
     want = ("cost", "disp", "iters", "npos", "mb_class", "sse")
-    steps = max(3, args.steps // 10)
+    steps = max(args.steps, 3)
+    warm = max(args.warmup, 3)
 
-    def timed(run, stream=None):
-        for _ in range(2):
+    def timed(run, stream, clocks=None):
+        for _ in range(warm):
+            run()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        w0 = time.perf_counter()
+        for e0, e1 in ev:
+            e0.record(stream)
+            run()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        clk = clocks.stop() if clocks else None
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+        return max_over_ranks(ms, dist), wall, clk
+
+    # ---- plain batch
+    b = sme.Batch(lumas, alphas, search_range=UHD_S, subpel=2, want=want)
+    b.tune(trials=2)
+    pstream = torch.cuda.current_stream()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    ms_plain, wall, clk = timed(lambda: b.run(sync=False), pstream, clocks if net is None else None)
+    b.synchronize()
+    plain_cfg = b.config()
+    b.set_config(plain_cfg["schedule"], plain_cfg["param"], plain_cfg["flag"])  # direct launches, same configuration
+    st_plain = stage_times(torch, b.run_stage, None, pstream, max(3, steps // 4))
+    b.synchronize()
+    plain_q = _device_quality(b.outputs, UHD_W, UHD_H)
+    plain_ops = _int_ops_device(torch, b.outputs)
+    transparent = sum(int((o["mb_class"] == 0).sum()) for o in b.outputs)
+    # the plain fields of pairs 0, 1 of every VOP, for the oracle leg below
+    plain01 = [{k: o[k][:2].cpu().numpy() for k in ("mv", "cost", "sse")} for o in b.outputs]
+    if net is not None:
+        b.close()
+        del b
+        gc.collect()
+        torch.cuda.empty_cache()
+
+    # ---- learned batch (the headline; the plain batch when no network is trained)
+    if net is not None:
+        net = sized_net(sme, net, P * (UHD_H // 4) * (UHD_W // 4))
+        lb = seedtrain.LearnedBatch(net, groups, search_range=UHD_S, subpel=2, want=want)
+        lb.tune(trials=2)
+        ms_learned, wall, clk = timed(lambda: lb.run(sync=False), lb.stream, clocks)
+        lb.synchronize()
+        learned_cfg = lb.config()
+        n_chunks = len(lb.chunks)
+        st_learned = stage_times(torch, lb.batch.run_stage, lb._seed_pass, lb.stream, max(3, steps // 4))
+        lb.synchronize()
+        lq = _device_quality(lb.outputs, UHD_W, UHD_H)
+        learned_ops = _int_ops_device(torch, lb.outputs)
+        head_batch, head_runner = lb.batch, lb
+    else:
+        lb = None
+        ms_learned, learned_cfg, n_chunks, st_learned = ms_plain, plain_cfg, 0, st_plain
+        lq, learned_ops = plain_q, plain_ops
+        head_batch, head_runner = b, b
+
+    # ---- oracle legs: the learned field on sampled pairs given the GPU's previous field and the same seeds
+    samples = [(min(7, n_seq - 1), 3, min(30, F - 2)), (0, 0, 1), (n_seq - 1, 7, F - 2)]
+    lexact = True
+    for s_, j_, k_ in (samples if lb is not None else []):
+        q = 8 * s_ + j_
+        out = lb.outputs[q]
+        luma, alpha, _ = seqs[s_]
+        tmp = None if k_ == 0 else out["mv"][k_ - 1].cpu().numpy()
+        o = O.estimate_sequence(O.OracleParams(UHD_W, UHD_H, UHD_S, 2), luma[k_:k_ + 2].cpu().numpy(),
+                                alpha[j_, k_:k_ + 2].cpu().numpy(), temporal_in=tmp,
+                                seed=lb.seeds[q][k_:k_ + 1].cpu().numpy())
+        lexact &= bool(np.array_equal(out["mv"][k_].cpu().numpy(), o["mv"][0]) and
+                       np.array_equal(out["cost"][k_].cpu().numpy().view(np.uint32), o["cost"][0]) and
+                       np.array_equal(out["iters"][k_].cpu().numpy(), o["iters"][0]) and
+                       int(out["sse"][k_].item()) == int(o["sse"][0]))
+
+    # ---- end to end through the host-buffer calls (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        host_in, host_out = [], []
+        luma_host = {}
+        for l, a in zip(lumas, alphas):
+            if l.data_ptr() not in luma_host:
+                luma_host[l.data_ptr()] = l.cpu().pin_memory()
+            host_in.append((luma_host[l.data_ptr()], a.cpu().pin_memory()))
+        for o in head_batch.outputs:
+            host_out.append({"mv": torch.empty(tuple(o["mv"].shape), dtype=torch.int16).pin_memory(),
+                             "sse": torch.empty(tuple(o["sse"].shape), dtype=torch.int64).pin_memory()})
+        io = head_batch.host_io(host_in, host_out)
+        head_runner.run_host(io)
+        e2e_steps = 3
+        if dist:
+            dist.barrier()
+        t1 = time.perf_counter()
+        for _ in range(e2e_steps):
+            head_runner.run_host(io)
+        e2e_s = max_over_ranks((time.perf_counter() - t1) / e2e_steps, dist)
+        h2d = sum(t.numel() for t in luma_host.values()) + sum(a.numel() for _, a in host_in)
+        d2h = sum(v.numel() * v.element_size() for h in host_out for v in h.values())
+        e2e_exact = all(torch.equal(h["mv"], o["mv"].cpu()) for h, o in zip(host_out[:8], head_batch.outputs[:8]))
+        e2e = {"value": job_rate(total, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s, "steps": e2e_steps,
+               "api": "sme_batch_upload -> run (one CUDA graph) -> sme_batch_download, pinned host buffers",
+               "mv_equals_device_run": bool(e2e_exact)}
+        del host_in, host_out, luma_host, io
+        gc.collect()
+
+    # ---- CPU oracle on the first two pairs of every VOP (plain method), all host cores
+    cpu = None
+    if rank == 0:
+        units, refs = [], []
+        for s_, (l, a, _) in enumerate(seqs):
+            l3 = l[:3].cpu().numpy()
+            for j in range(a.shape[0]):
+                units.append((O.OracleParams(UHD_W, UHD_H, UHD_S, 2), l3, a[j, :3].cpu().numpy(), None))
+                refs.append(plain01[8 * s_ + j])
+        threads = os.cpu_count() or 1
+        res, dt = oracle_units(units, threads)
+        mbs = len(units) * 2 * M
+        exact = all(np.array_equal(r["mv"], g["mv"]) and np.array_equal(r["cost"], g["cost"].view(np.uint32)) and
+                    np.array_equal(r["sse"], g["sse"].view(np.uint64)) for r, g in zip(res, refs))
+        _, dt1 = oracle_units(units[:4], 1)
+        cpu = {"value": mbs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first 2 pairs of every VOP sequence ({len(units)} VOPs, {mbs} MBs), {dt:.1f} s on "
+                         f"{threads} threads (C oracle, one VOP per thread)",
+               "single_thread_value": 4 * 2 * M / dt1, **host_cpu(),
+               "plain_field_bit_exact_vs_oracle": bool(exact)}
+    head_runner.close()
+    if net is not None:
+        net.close()
+    del lb, head_batch, head_runner, seqs, groups, lumas, alphas
+    gc.collect()
+    torch.cuda.empty_cache()
+    hbm, peak_kind = peaks()
+    alg_run = uhd_alg_bytes(n_vops, n_seq, F, total)
+    alg_stream = uhd_alg_bytes(n_vops, n_seq, F, total, transparent)
+    return {
+        "ms_learned": ms_learned, "ms_plain": ms_plain, "wall_s_timed": wall, "clocks": clk, "steps": steps,
+        "warmup": warm, "total_mbs": total, "generation_s": gen_s, "n_seq": n_seq, "frames": F,
+        "workload": uhd_workload(n_seq, F),
+        "plain": {"value": job_rate(total, ws, ms_plain / 1e3), "unit": UNIT, "ms_per_run": ms_plain,
+                  "config": plain_cfg, **plain_q,
+                  "stage_ms": {"classify_stream": st_plain[0], "search": st_plain[2]},
+                  "bit_exact_vs_oracle_sample": cpu["plain_field_bit_exact_vs_oracle"] if cpu else None},
+        "learned": {"value": job_rate(total, ws, ms_learned / 1e3), "ms_per_run": ms_learned, "config": learned_cfg,
+                    **lq, "psnr_delta_db": lq["psnr_db_mean"] - plain_q["psnr_db_mean"],
+                    "vs_plain_batched": ms_plain / ms_learned,
+                    "stage_ms": {"classify_stream": st_learned[0], "seed_network": st_learned[1],
+                                 "search": st_learned[2]},
+                    "bit_exact_vs_oracle_sample": lexact, "oracle_samples": samples},
+        "launches_per_run": {"sparse": 6 + 7 * n_chunks, "mb": 2 + 7 * n_chunks, "pair": 2 + 7 * n_chunks}.get(
+            learned_cfg["schedule"], 2 + 7 * n_chunks),
+        "roofline_search": {"bound": "alu", "kernel": {"sparse": "me_sparse_kernel", "mb": "me_kernel",
+                                                        "pair": "me_pair_kernel"}.get(learned_cfg["schedule"]),
+                            "achieved": learned_ops / (st_learned[2] / 1e3) / 1e12,
+                            "peak": ALU_PEAK_TOPS, "unit": "Tops/s", "frac": learned_ops / (st_learned[2] / 1e3) / 1e12 / ALU_PEAK_TOPS,
+                            "ops_per_launch": learned_ops, "avg_launch_ms": st_learned[2],
+                            "peak_kind": "derived upper bound: 152 SMs x 128 int32 lanes x 2.07 GHz, one packed op per lane per cycle"},
+        "roofline_stream": {"bound": "hbm", "kernel": "sparse_stream_kernel (+ count, scan, scatter)",
+                            "achieved": alg_stream / (st_learned[0] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                            "frac": alg_stream / (st_learned[0] / 1e3) / 1e9 / hbm, "alg_bytes_per_launch": alg_stream,
+                            "avg_launch_ms": st_learned[0], "peak_kind": f"{peak_kind} hbm_gbs"},
+        "run_hbm": {"alg_bytes_per_run": alg_run, "achieved_learned": alg_run / (ms_learned / 1e3) / 1e9,
+                    "achieved_plain": alg_run / (ms_plain / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac_plain": alg_run / (ms_plain / 1e3) / 1e9 / hbm,
+                    "frac_learned": alg_run / (ms_learned / 1e3) / 1e9 / hbm},
+        "e2e": e2e, "cpu_baseline": cpu,
+    }
+
+
+def measure_hd(sme, torch, args, net):
+    """The learned proposal's evaluation workload: 1920x1088, 300 frames, 4
+    objects (4 VOPs), |v| <= 8 px, rotation <= 5 deg, scale 0.95-1.05, S = 16,
+    half-pel; plain batch against the learned batch (trained network), both
+    autotuned and replayed from graphs; one sampled pair of each against the
+    oracle."""
+    import gc
+
+    import oracle as O
+    from paper_1002_1168_gb300 import seedtrain, synth_gpu
+
+    W4, H4, S4 = 1920, 1088, 16
+    t0 = time.perf_counter()
+    luma, alpha, _ = synth_gpu.hd_learned_eval(seed=1004, frames=args.hd_frames)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    F = luma.shape[0]
+    vops = [alpha[j] for j in range(alpha.shape[0])]
+    total = len(vops) * (F - 1) * (W4 // 16) * (H4 // 16)
+    want = ("cost", "disp", "iters", "npos", "mb_class", "sse")
+    steps = max(3, args.steps // 4)
+
+    def timed(run, stream):
+        for _ in range(3):
             run()
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -664,54 +992,160 @@ def measure_at_scale(sme, torch, args, params, dist):
             run()
             e1.record(stream)
         torch.cuda.synchronize()
-        return max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps, dist)
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
 
-    # the sampled (sequence, VOP, pair) of the oracle checks
-    s_smp, j_smp, k_smp = min(7, len(seqs) - 1), 3, min(30, F - 2)
+    k_smp, j_smp = min(150, F - 2), 1
 
-    def oracle_sample(out, s, j, k, seeds=None):
-        luma, alpha, _ = seqs[s]
-        tmp = None if k == 0 else out["mv"][k - 1].cpu().numpy()
-        sd = None if seeds is None else seeds[k:k + 1].cpu().numpy()
-        o = O.estimate_sequence(O.OracleParams(W4, H4, S4, 2), luma[k:k + 2].cpu().numpy(),
-                                alpha[j, k:k + 2].cpu().numpy(), temporal_in=tmp, seed=sd)
-        return bool(np.array_equal(out["mv"][k].cpu().numpy(), o["mv"][0]) and
-                    np.array_equal(out["cost"][k].cpu().numpy().view(np.uint32), o["cost"][0]) and
-                    int(out["sse"][k].item()) == int(o["sse"][0]))
+    def oracle_ok(out, seeds=None):
+        tmp = None if k_smp == 0 else out["mv"][k_smp - 1].cpu().numpy()
+        sd = None if seeds is None else seeds[k_smp:k_smp + 1].cpu().numpy()
+        o = O.estimate_sequence(O.OracleParams(W4, H4, S4, 2), luma[k_smp:k_smp + 2].cpu().numpy(),
+                                alpha[j_smp, k_smp:k_smp + 2].cpu().numpy(), temporal_in=tmp, seed=sd)
+        return bool(np.array_equal(out["mv"][k_smp].cpu().numpy(), o["mv"][0]) and
+                    np.array_equal(out["cost"][k_smp].cpu().numpy().view(np.uint32), o["cost"][0]) and
+                    int(out["sse"][k_smp].item()) == int(o["sse"][0]))
 
-    b = sme.Batch(lumas, alphas, search_range=S4, subpel=2, want=want)
+    b = sme.Batch([luma] * len(vops), vops, search_range=S4, subpel=2, want=want)
     b.tune(trials=2)
-    ms = timed(lambda: b.run(sync=False))
+    ms = timed(lambda: b.run(sync=False), torch.cuda.current_stream())
     b.synchronize()
-    plain = {"value": job_rate(total, dist.get_world_size() if dist else 1, ms / 1e3), "unit": UNIT, "ms_per_run": ms,
-             "config": b.config(), **_device_quality(b.outputs, W4, H4),
-             "bit_exact_vs_oracle_sample": oracle_sample(b.outputs[8 * s_smp + j_smp], s_smp, j_smp, k_smp)}
+    pq = _device_quality(b.outputs, W4, H4)
+    plain = {"value": total / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "config": b.config(), **pq,
+             "bit_exact_vs_oracle_sample": oracle_ok(b.outputs[j_smp])}
     b.close()
-    del b
-    gc.collect()
-    learned = None
-    if params is not None:
-        net = sme.SeedNet(max_cells=(F - 1) * (H4 // 4) * (W4 // 4))
-        net.set_params(params)
-        lb = seedtrain.LearnedBatch(net, groups, search_range=S4, subpel=2, want=want)
-        lb.tune(trials=2)
-        lms = timed(lambda: lb.run(sync=False), lb.stream)
-        lb.synchronize()
-        lq = _device_quality(lb.outputs, W4, H4)
-        learned = {"value": job_rate(total, dist.get_world_size() if dist else 1, lms / 1e3), "unit": UNIT,
-                   "ms_per_run": lms, "config": lb.config(), **lq, "vs_plain_at_scale": ms / lms,
-                   "psnr_delta_db": lq["psnr_db_mean"] - plain["psnr_db_mean"],
-                   "bit_exact_vs_oracle_sample": oracle_sample(lb.outputs[8 * s_smp + j_smp], s_smp, j_smp, k_smp,
-                                                               lb.seeds[8 * s_smp + j_smp])}
-        lb.close()
-        net.close()
-        del lb
-    del seqs, groups, lumas, alphas
+    net = sized_net(sme, net, (F - 1) * (H4 // 4) * (W4 // 4))
+    lb = seedtrain.LearnedBatch(net, [(luma, vops)], search_range=S4, subpel=2, want=want)
+    lb.tune(trials=2)
+    lms = timed(lambda: lb.run(sync=False), lb.stream)
+    lb.synchronize()
+    lq = _device_quality(lb.outputs, W4, H4)
+    learned = {"value": total / (lms / 1e3), "unit": UNIT, "ms_per_run": lms, "config": lb.config(), **lq,
+               "vs_plain_batched": ms / lms, "psnr_delta_db": lq["psnr_db_mean"] - pq["psnr_db_mean"],
+               "iters_delta_pct": 100.0 * (lq["iters_per_opaque_mb"] / pq["iters_per_opaque_mb"] - 1.0),
+               "bit_exact_vs_oracle_sample": oracle_ok(lb.outputs[j_smp], lb.seeds[j_smp])}
+    lb.close()
+    net.close()
+    del b, lb, luma, alpha, vops
     gc.collect()
     torch.cuda.empty_cache()
-    return {"workload": f"{n_seq} sequences of 3840x2160, {F} frames, 8 VOPs each ({n_vops} VOPs), |v| <= 32, "
-                        "rotation <= 3 deg, S=32, half-pel, rendered on the device",
+    return {"workload": f"1920x1088, {F} frames, 4 VOPs, |v| <= 8, rotation <= 5 deg, scale 0.95-1.05, S=16, half-pel",
             "mb_per_run": total, "generation_s": gen_s, "runs": steps, "plain": plain, "learned_seeded": learned}
+
+
+def measure_cif(sme, torch, args, rank, dist, net, train_info):
+    """The single-sequence workload: CIF 352x288, 30 frames (29 pairs), one
+    VOP, S = 16, half-pel (latency-bound: one dependency chain).  The plain
+    pass (autotuned, L2 flushed between steps), end to end through
+    sme_estimate_sequence_host, the oracle on the same sequence (parity and
+    its single-threaded time), the exhaustive search, four vectors per MB,
+    and the learned-seeded pass."""
+    import oracle as O
+
+    ws = dist.get_world_size() if dist else 1
+    seq = workload(rank)
+    P, M = FRAMES - 1, (W // 16) * (H // 16)
+    est = sme.Estimator(W, H, search_range=S, subpel=SUBPEL)
+    luma = torch.from_numpy(seq.luma).cuda()
+    alpha = torch.from_numpy(seq.alpha[0]).cuda()
+    out = est._alloc_outputs(P, OUT_FIELDS, luma.device)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=luma.device)
+    if args.schedule == "auto":
+        est.autotune(luma, alpha, out=out, trials=5)  # outside the timed region
+    else:
+        est.set_schedule(args.schedule)
+    est_cfg = est.config()
+    steps = max(args.steps, 3)
+    for _ in range(max(args.warmup, 3)):
+        est.estimate_sequence(luma, alpha, out=out, sync=False)
+    est.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    est.profile_begin(steps)
+    for i in range(steps):
+        flush.fill_(i & 0xff)  # L2 flush, outside the timed events
+        starts[i].record()
+        est.estimate_sequence(luma, alpha, out=out, sync=False)
+        ends[i].record()
+    torch.cuda.synchronize()
+    calls, cls_ms, me_ms = est.profile_end()
+    est.synchronize()  # raises on a device-side failure
+    dev_ms = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)), dist)
+
+    # end-to-end through the public API with host buffers (pinned)
+    hl = torch.from_numpy(seq.luma).pin_memory()
+    ha = torch.from_numpy(seq.alpha[0]).pin_memory()
+    hout = {k: v.pin_memory() for k, v in est._alloc_outputs(P, OUT_FIELDS, "cpu").items()}
+    for _ in range(3):
+        est.estimate_sequence_host(hl, ha, out=hout)
+    e2e_steps = max(steps, 5)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        est.estimate_sequence_host(hl, ha, out=hout)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    h2d = int(hl.numel() + ha.numel())
+    d2h = int(sum(v.numel() * v.element_size() for v in hout.values()))
+
+    es_rec, es_mv, es_sad = measure_es(sme, torch, est, luma, flush, max(steps // 4, 3))
+    four_mv_rec = measure_four_mv(sme, torch, seq, luma, alpha, flush, max(steps // 4, 3))
+    learned = None
+    if net is not None:
+        learned, lres, lseeds = measure_learned(sme, torch, args, net, est, luma, alpha, flush)
+
+    mbs_step = P * M
+    value = job_rate(mbs_step * steps, ws, dev_ms / 1e3)
+    cls = res["mb_class"]
+    hbm, peak_kind = peaks()
+    me_avg_s = me_ms / max(calls, 1) / 1e3
+    alg = algorithmic_bytes(P, M, FRAMES)
+    cb, orc = cpu_baseline(seq, budget_s=args.cpu_seconds)
+    exact = all(np.array_equal(res[a].view(np.uint8), orc[b].view(np.uint8)) for a, b in
+                [("mv", "mv"), ("cost", "cost"), ("iters", "iters"), ("npos", "npos"), ("disp", "disp"),
+                 ("mb_class", "mbclass"), ("sse", "sse")])
+    psnr = [O.psnr(int(x), W, H) for x in res["sse"].view(np.uint64)]
+    op = cls == 1
+    es_exact = True
+    es_mv_np = es_mv.cpu().numpy()
+    for k in (0, P // 2):
+        bm, bs, _ = O.full_search(seq.luma[k], seq.luma[k + 1], W, H, SUBPEL, S)
+        es_exact &= bool(np.array_equal(es_mv_np[k], bm) and np.array_equal(es_sad[k], bs))
+    es_vop = es_psnr_like_method(sme, est, luma, es_mv, cls, 1, W, H)
+    es_rec.update({"bit_exact_vs_oracle_sample": es_exact, "pairs_checked": [0, P // 2],
+                   "search_points_ratio_method_vs_es": float(res["npos"][cls > 0].mean()) / es_rec["positions_per_mb"],
+                   "psnr_db_mean_transparent_at_zero": es_vop,
+                   "psnr_method_minus_es_db": float(np.mean(psnr)) - es_vop})
+    if learned is not None:
+        lexact, judge = learned_oracle_leg(seq, res, lres, lseeds)
+        lq = stats(lres, W, H)
+        learned.update({"vs_plain": learned["value"] / value, **lq,
+                        "psnr_delta_db": lq["psnr_db_mean"] - float(np.mean(psnr)),
+                        "bit_exact_vs_oracle": lexact,
+                        "seed_changed_mbs": int((lres["mv"] != res["mv"]).any(axis=-1).sum()),
+                        "es_judge": judge, "training": train_info})
+    est.close()
+    return {"workload": WORKLOAD, "value": value, "unit": UNIT, "ms_per_step": dev_ms / steps, "steps": steps,
+            "execution": est_cfg, "l2": "flushed between steps (256 MiB write outside the timed events)",
+            "e2e": {"value": job_rate(mbs_step * e2e_steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "hbm", "achieved": alg / me_avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / me_avg_s / 1e9 / hbm, "traffic": ME_KERNEL_TRAFFIC_BYTES, "kernel": "me_kernel",
+                         "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg,
+                         "avg_launch_ms": me_avg_s * 1e3, "classify_avg_ms": cls_ms / max(calls, 1),
+                         "critical_path_steps": (W // 16 - 1) + 2 * (H // 16 - 1) + P,
+                         "alu": {"achieved_tops": algorithmic_int_ops(res) / me_avg_s / 1e12,
+                                 "peak_tops": ALU_PEAK_TOPS,
+                                 "frac": algorithmic_int_ops(res) / me_avg_s / 1e12 / ALU_PEAK_TOPS,
+                                 "ops_per_launch": algorithmic_int_ops(res),
+                                 "peak_kind": "derived upper bound: 152 SMs x 128 int32 lanes x 2.07 GHz"}},
+            "cpu_baseline": cb,
+            "quality": {"bit_exact_vs_oracle": exact, "mb_per_s_non_transparent": value * float((cls > 0).mean()),
+                        "iters_per_opaque_mb": float(res["iters"][op].mean()),
+                        "positions_per_mb": float(res["npos"][cls > 0].mean()),
+                        "psnr_db_mean": float(np.mean(psnr)), "learned_seeded": learned,
+                        "exhaustive_search": es_rec, "four_mv": four_mv_rec}}
 
 
 def run_ours(args):
@@ -728,160 +1162,48 @@ def run_ours(args):
     from paper_1002_1168_gb300 import sme
 
     cuda_build.build()
-    seq = workload(rank)
-    P, M = FRAMES - 1, (W // 16) * (H // 16)
-    est = sme.Estimator(W, H, search_range=S, subpel=SUBPEL)
-    luma = torch.from_numpy(seq.luma).cuda()
-    alpha = torch.from_numpy(seq.alpha[0]).cuda()
-    out = est._alloc_outputs(P, OUT_FIELDS, luma.device)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=luma.device)
-    if args.schedule == "auto":
-        est.autotune(luma, alpha, out=out, trials=5)  # outside the timed region
-    else:
-        est.set_schedule(args.schedule)
-    est_cfg = est.config()
-
-    for _ in range(max(args.warmup, 3)):
-        est.estimate_sequence(luma, alpha, out=out, sync=False)
-    est.synchronize()
-    res = {k: v.cpu().numpy() for k, v in out.items()}
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    est.profile_begin(args.steps)
-    w0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(i & 0xff)  # L2 flush, outside the timed events
-        starts[i].record()
-        est.estimate_sequence(luma, alpha, out=out, sync=False)
-        ends[i].record()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - w0
-    calls, cls_ms, me_ms = est.profile_end()
-    est.synchronize()  # raises on a device-side failure
-    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    dev_ms = max_over_ranks(dev_ms, dist)
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-
-    # end-to-end through the public API with host buffers (pinned)
-    hl = torch.from_numpy(seq.luma).pin_memory()
-    ha = torch.from_numpy(seq.alpha[0]).pin_memory()
-    hout = est._alloc_outputs(P, OUT_FIELDS, "cpu")
-    hout = {k: v.pin_memory() for k, v in hout.items()}
-    for _ in range(3):
-        est.estimate_sequence_host(hl, ha, out=hout)
-    e2e_steps = max(args.steps, 5)
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        est.estimate_sequence_host(hl, ha, out=hout)
-    e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(e2e_s, dist)
-    h2d = int(hl.numel() + ha.numel())
-    d2h = int(sum(v.numel() * v.element_size() for v in hout.values()))
-
-    es_rec, es_mv, es_sad = measure_es(sme, torch, est, luma, flush, max(args.steps // 4, 3))
-    four_mv_rec = measure_four_mv(sme, torch, seq, luma, alpha, flush, max(args.steps // 4, 3))
-    net, learned, train_info = None, None, None
+    net, train_info = None, None
     if not args.no_learned:
         net, train_info = train_seednet(sme, torch, args)
-        learned, lres, lseeds = measure_learned(sme, torch, args, net, est, luma, alpha, flush)
-
-    batched = None
-    if not args.no_batch:
-        batched = measure_batch(sme, torch, args, rank, dist, net)
-    paper_setup = measure_paper_setup(sme, torch) if rank == 0 else None
-    at_scale = None
-    if not args.no_scale:
-        at_scale = measure_at_scale(sme, torch, args, net.get_params() if net is not None else None, dist)
+    head = measure_headline(sme, torch, args, net, dist, rank)
+    cif = None if args.no_cif else measure_cif(sme, torch, args, rank, dist, net, train_info)
+    batched = None if args.no_batch else measure_batch(sme, torch, args, rank, dist, net)
+    hd = None if (args.no_hd or net is None) else measure_hd(sme, torch, args, net)
+    paper_setup = measure_paper_setup(sme, torch) if (rank == 0 and not args.no_paper) else None
     if net is not None:
         net.close()
-
     if rank != 0:
-        est.close()
         if dist:
             dist.destroy_process_group()
         return
 
-    mbs_step = P * M
-    value = job_rate(mbs_step * args.steps, ws, dev_ms / 1e3)
-    cls = res["mb_class"]
-    hbm, peak_kind = peaks()
-    me_avg_s = me_ms / max(calls, 1) / 1e3
-    alg = algorithmic_bytes(P, M, FRAMES)
-    achieved = alg / me_avg_s / 1e9
-    cb, orc = cpu_baseline(seq, budget_s=args.cpu_seconds)
-    match = float((res["mv"] == orc["mv"]).all(axis=-1).mean())
-    exact = all(np.array_equal(res[a].view(np.uint8), orc[b].view(np.uint8)) for a, b in
-                [("mv", "mv"), ("cost", "cost"), ("iters", "iters"), ("npos", "npos"), ("disp", "disp"),
-                 ("mb_class", "mbclass"), ("sse", "sse")])
-    import oracle as O
-
-    psnr = [O.psnr(int(s), W, H) for s in res["sse"].view(np.uint64)]
-    op = cls == 1
-    # exhaustive search: the oracle's on two pairs, and the Table 1 / Table 2 comparison
-    es_exact = True
-    es_mv_np = es_mv.cpu().numpy()
-    for k in (0, P // 2):
-        bm, bs, _ = O.full_search(seq.luma[k], seq.luma[k + 1], W, H, SUBPEL, S)
-        es_exact &= bool(np.array_equal(es_mv_np[k], bm) and np.array_equal(es_sad[k], bs))
-    es_vop = es_psnr_like_method(sme, est, luma, es_mv, cls, 1, W, H)
-    es_rec.update({"bit_exact_vs_oracle_sample": es_exact, "pairs_checked": [0, P // 2],
-                   "search_points_ratio_method_vs_es": float(res["npos"][cls > 0].mean()) / es_rec["positions_per_mb"],
-                   "psnr_db_mean_transparent_at_zero": es_vop,
-                   "psnr_method_minus_es_db": float(np.mean(psnr)) - es_vop})
-    if learned is not None:
-        lexact, judge = learned_oracle_leg(seq, res, lres, lseeds)
-        lq = stats(lres, W, H)
-        learned.update({"vs_plain": learned["value"] / value, **lq,
-                        "psnr_delta_db": lq["psnr_db_mean"] - float(np.mean(psnr)),
-                        "mv_match_oracle": lexact, "bit_exact_vs_oracle": lexact,
-                        "seed_changed_mbs": int((lres["mv"] != res["mv"]).any(axis=-1).sum()),
-                        "es_judge": judge, "training": train_info})
+    learned = head["learned"] if net is not None else None
+    value = learned["value"] if learned else head["plain"]["value"]
+    ms = head["ms_learned"] if learned else head["ms_plain"]
+    rs = head["roofline_search"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": head["steps"],
+        "warmup": head["warmup"], "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8+f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pairs": P, "mbs_per_step": mbs_step, "seed": 1002,
-                   "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "schedule": args.schedule,
-                   "execution": est_cfg},
-        "clocks": clk,
-        "e2e": {"value": job_rate(mbs_step * e2e_steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": ME_KERNEL_TRAFFIC_BYTES, "kernel": "me_kernel",
-                     "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg,
-                     "avg_launch_ms": me_avg_s * 1e3, "classify_avg_ms": cls_ms / max(calls, 1),
-                     "critical_path_steps": (W // 16 - 1) + 2 * (H // 16 - 1) + P,
-                     "alu": {"achieved_tops": algorithmic_int_ops(res) / me_avg_s / 1e12, "peak_tops": ALU_PEAK_TOPS,
-                             "frac": algorithmic_int_ops(res) / me_avg_s / 1e12 / ALU_PEAK_TOPS,
-                             "ops_per_launch": algorithmic_int_ops(res),
-                             "peak_kind": "derived: 152 SMs x 128 int32 lanes x 2.07 GHz"}},
-        "cpu_baseline": cb,
-        "quality": {"mv_match_oracle": match, "bit_exact_vs_oracle": exact,
-                    "mb_per_s_non_transparent": value * float((cls > 0).mean()),
-                    "iters_per_opaque_mb": float(res["iters"][op].mean()),
-                    "positions_per_mb": float(res["npos"][cls > 0].mean()),
-                    "psnr_db_mean": float(np.mean(psnr)), "learned_seeded": learned,
-                    "exhaustive_search": es_rec, "four_mv": four_mv_rec},
-        "wall_s_timed": wall,
-        "batched": batched,
-        "at_scale": at_scale,
-        "paper_setup": paper_setup,
+        "config": {"workload": head["workload"], "form": "learned-seeded" if learned else "plain",
+                   "mbs_per_step": head["total_mbs"], "seed": 1005, "search_range": UHD_S, "subpel": 2,
+                   "l2": "inputs (72 GB) far above L2; no flush needed",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "execution": learned["config"] if learned else head["plain"]["config"]},
+        "plain": head["plain"], "learned_seeded": learned,
+        "clocks": head["clocks"],
+        "e2e": head["e2e"] or {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": head["launches_per_run"] * head["steps"],
+        "roofline": {"bound": rs["bound"], "achieved": rs["achieved"], "peak": rs["peak"], "unit": rs["unit"],
+                     "frac": rs["frac"], "traffic": SEARCH_KERNEL_TRAFFIC_BYTES, "kernel": rs["kernel"],
+                     "peak_kind": rs["peak_kind"], "ops_per_launch": rs["ops_per_launch"],
+                     "avg_launch_ms": rs["avg_launch_ms"],
+                     "stream_pass": head["roofline_stream"], "run_hbm": head["run_hbm"]},
+        "cpu_baseline": head["cpu_baseline"],
+        "wall_s_timed": head["wall_s_timed"], "generation_s": head["generation_s"],
+        "cif30": cif, "batched": batched, "hd_learned_eval": hd, "paper_setup": paper_setup,
     }
     print(json.dumps(line))
-    est.close()
     if dist:
         dist.destroy_process_group()
 
@@ -925,7 +1247,11 @@ def main():
     ap.add_argument("--schedule", default="auto", choices=["auto", "pair", "mb", "cluster"])
     ap.add_argument("--no-batch", action="store_true", help="skip the secondary batched measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip training and the learned-seeded measurements")
-    ap.add_argument("--no-scale", action="store_true", help="skip the 16 x 3840x2160 measurement")
+    ap.add_argument("--no-cif", action="store_true", help="skip the CIF x 30 single-sequence measurements")
+    ap.add_argument("--no-hd", action="store_true", help="skip the 1920x1088 x 300-frame learned evaluation")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper-setting QCIF measurement")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the headline's host-buffer (end-to-end) runs")
+    ap.add_argument("--hd-frames", type=int, default=300, help="frames of the 1920x1088 learned evaluation")
     ap.add_argument("--learn-pairs", type=int, default=2000, help="CIF VOP pairs the seed network is trained on")
     ap.add_argument("--learn-steps", type=int, default=800, help="Adam steps (32 pairs each)")
     ap.add_argument("--batch-only", action="store_true", help="only the batched measurement (profiling)")
@@ -954,7 +1280,8 @@ def main():
         from paper_1002_1168_gb300 import sme
 
         cuda_build.build()
-        print(json.dumps({"at_scale": measure_at_scale(sme, torch, args, None, None)}))
+        args.no_e2e = True
+        print(json.dumps({"headline_plain": measure_headline(sme, torch, args, None, None, 0)}))
     else:
         run_ours(args)
 

@@ -360,6 +360,24 @@ int sme_batch_set_config(sme_batch* b, int schedule, int param, int flag);
  * or sequence index. */
 int sme_batch_run_stage(sme_batch* b, int stage);
 int sme_batch_class_map(sme_batch* b, int seq, const uint8_t** mb_class);
+/* Host-memory inputs and outputs of a batch.  sme_batch_upload copies io[i]
+ * (HOST luma and alpha, [n_frames][H][W] of sequence i; n = the batch's
+ * sequence count) into the device buffers the batch was created with, on the
+ * batch's stream; a luma plane that sequence i shares with sequence i - 1
+ * (the same device address: the VOPs of one scene) is copied once.
+ * sme_batch_download copies every non-NULL HOST pointer of io[i].out from
+ * the matching device output of sequence i (SME_ERR_ARG if that output was
+ * not requested at creation).  Both are asynchronous on the batch's stream
+ * (page-locked host buffers let the copies run at link speed) and finish
+ * by sme_batch_synchronize; upload -> run -> download -> synchronize is the
+ * whole host-to-host pass. */
+typedef struct {
+    const uint8_t* luma;
+    const uint8_t* alpha;
+    sme_outputs out;
+} sme_host_io;
+int sme_batch_upload(sme_batch* b, const sme_host_io* io, int n);
+int sme_batch_download(sme_batch* b, const sme_host_io* io, int n);
 int sme_batch_destroy(sme_batch* b);
 
 /* Learned seed proposal (no counterpart in the paper, whose seeds are the

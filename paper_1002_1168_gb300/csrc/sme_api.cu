@@ -1197,6 +1197,7 @@ struct sme_batch {
     DevBuf descs, packed, cls, ready, sched, sched_seq, unit_seq, unit_pair, fseq, ffrm, maps;
     SparseScratch sp;
     std::vector<size_t> cls_off;  // byte offset of each sequence's class map [F][M] in cls
+    std::vector<SeqDesc> host_desc;  // the descriptors (device addresses, sizes) of every sequence
     ExecCfg cfg = {kSchedMB, 0, 0, 1, 0, 1};
     float tuned_ms = 0.0f;
     cudaGraph_t graph = nullptr;
@@ -1441,6 +1442,7 @@ int sme_batch_create(sme_batch** out, const sme_params* p, const sme_sequence* s
         }
     if (k != (size_t)gid) return fail(SME_ERR_STATE);
     if ((rc = setup_sparse(b->sp, d, nullptr))) return fail(rc);
+    b->host_desc = d;
     // Per-pair schedule: pair k of every sequence before pair k+1 of any.
     std::vector<int> useq, upair;
     int max_p = 0;
@@ -1506,6 +1508,51 @@ int sme_batch_run_stage(sme_batch* b, int stage)
 {
     if (!b || (stage != 1 && stage != 2)) return SME_ERR_ARG;
     return batch_enqueue(b, b->stream, stage);
+}
+
+int sme_batch_upload(sme_batch* b, const sme_host_io* io, int n)
+{
+    if (!b || !io || n != b->n) return SME_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!io[i].luma || !io[i].alpha) return SME_ERR_ARG;
+    const void* last_luma = nullptr;
+    for (int i = 0; i < n; ++i) {
+        const SeqDesc& d = b->host_desc[i];
+        const size_t bytes = (size_t)d.F * d.W * d.H;
+        // a luma plane shared with the previous sequence (the same device
+        // address: the VOPs of one scene) is copied once
+        if (d.luma != last_luma &&
+            cudaMemcpyAsync((void*)d.luma, io[i].luma, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+            return SME_ERR_CUDA;
+        last_luma = d.luma;
+        if (cudaMemcpyAsync((void*)d.alpha, io[i].alpha, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+            return SME_ERR_CUDA;
+    }
+    return SME_OK;
+}
+
+int sme_batch_download(sme_batch* b, const sme_host_io* io, int n)
+{
+    if (!b || !io || n != b->n) return SME_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        const SeqDesc& d = b->host_desc[i];
+        const sme_outputs& h = io[i].out;
+        const size_t PM = (size_t)d.P * d.M;
+        const struct {
+            void* host;
+            const void* dev;
+            size_t bytes;
+        } f[] = {{h.mv, d.mv, PM * sizeof(sme_mv)}, {h.cost, d.cost, PM * 4},         {h.disp, d.disp, PM * 8},
+                 {h.iters, d.iters, PM},            {h.npos, d.npos, PM},             {h.mb_class, d.out_cls, PM},
+                 {h.sse_mb, d.sse_mb, PM * 4},      {h.sse, d.sse, (size_t)d.P * 8}, {h.pred, d.pred, (size_t)d.P * d.W * d.H}};
+        for (const auto& x : f) {
+            if (!x.host) continue;
+            if (!x.dev) return SME_ERR_ARG;  // not requested at creation
+            if (cudaMemcpyAsync(x.host, x.dev, x.bytes, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+                return SME_ERR_CUDA;
+        }
+    }
+    return SME_OK;
 }
 
 int sme_batch_class_map(sme_batch* b, int seq, const uint8_t** mb_class)

@@ -328,6 +328,17 @@ class LearnedBatch:
             self.batch.synchronize()
         return self.outputs
 
+    def run_host(self, io):
+        """The whole host-to-host pass: inputs uploaded from host memory, the
+        run, the outputs named in io downloaded, on the run's stream
+        (io: Batch.host_io); synchronises."""
+        with self.torch.cuda.stream(self.stream):
+            self.batch.upload(io)
+            self.run(sync=False)
+            self.batch.download(io)
+        self.batch.synchronize()
+        return io
+
     def synchronize(self):
         self.batch.synchronize()
 

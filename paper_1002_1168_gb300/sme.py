@@ -36,6 +36,7 @@ EXPORTS = [
     "sme_full_search",
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_set_config", "sme_batch_run_stage", "sme_batch_class_map", "sme_seednet_forward_active_table",
+    "sme_batch_upload", "sme_batch_download",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_features_table",
     "sme_seednet_forward",
@@ -62,6 +63,10 @@ class Outputs(C.Structure):
     _fields_ = [("mv", C.c_void_p), ("cost", C.c_void_p), ("disp", C.c_void_p),
                 ("iters", C.c_void_p), ("npos", C.c_void_p), ("mb_class", C.c_void_p),
                 ("sse_mb", C.c_void_p), ("sse", C.c_void_p), ("pred", C.c_void_p)]
+
+
+class HostIO(C.Structure):
+    _fields_ = [("luma", C.c_void_p), ("alpha", C.c_void_p), ("out", Outputs)]
 
 
 class Sequence(C.Structure):
@@ -120,6 +125,8 @@ def _lib():
                                      C.POINTER(C.c_float)]),
             "sme_batch_set_config": (i, [vp, i, i, i]),
             "sme_batch_run_stage": (i, [vp, i]),
+            "sme_batch_upload": (i, [vp, C.POINTER(HostIO), i]),
+            "sme_batch_download": (i, [vp, C.POINTER(HostIO), i]),
             "sme_batch_class_map": (i, [vp, i, C.POINTER(C.c_void_p)]),
             "sme_seednet_forward_active_table": (i, [vp, vp, i, i, i, vp, i, vp]),
             "sme_batch_destroy": (i, [vp]),
@@ -456,6 +463,33 @@ class Batch:
                "sme_batch_config")
         name = {v: k for k, v in SCHEDULES.items()}[s_.value]
         return {"schedule": name, "param": p_.value, "flag": sp_.value, "tuned_ms": ms.value}
+
+    def host_io(self, host_inputs, host_outputs):
+        """The sme_host_io array for host_inputs [(luma, alpha) CPU tensors]
+        and host_outputs [{field: CPU tensor}] (pinned for link-speed copies)."""
+        n = len(self.inputs)
+        io = (HostIO * n)()
+        for i in range(n):
+            l, a = host_inputs[i]
+            o = host_outputs[i] if host_outputs is not None else {}
+            io[i] = HostIO(l.data_ptr(), a.data_ptr(), Outputs(*[_ptr(o.get(k)) for k in OUTPUT_FIELDS]))
+        return io
+
+    def upload(self, io):
+        """Copy every sequence's inputs from host memory (sme_batch_upload)."""
+        _check(_lib().sme_batch_upload(self._h, io, len(self.inputs)), "sme_batch_upload")
+
+    def download(self, io):
+        """Copy the requested outputs to host memory (sme_batch_download)."""
+        _check(_lib().sme_batch_download(self._h, io, len(self.inputs)), "sme_batch_download")
+
+    def run_host(self, io):
+        """The whole host-to-host pass: upload, run, download, synchronise."""
+        self.upload(io)
+        self.run(sync=False)
+        self.download(io)
+        self.synchronize()
+        return io
 
     def run_stage(self, stage):
         """Enqueue stage 1 (classification) or 2 (search) of one run."""

@@ -75,11 +75,16 @@ def render_gpu(W, H, F, background, bg_offsets, objects, noise_sigma, seed, devi
 
 
 def make_sequence_gpu(W, H, F, seed, n_objects=1, vmax=8.0, bg_step=(1.0, 0.5), noise_sigma=3.0, blobby=True,
-                      change_every=10, max_rot_deg=0.0, scale_range=(1.0, 1.0), obj_frac=0.30, device="cuda"):
-    """synth.make_sequence's scene, rendered on the device: (luma, alpha, meta)."""
+                      change_every=10, max_rot_deg=0.0, scale_range=(1.0, 1.0), obj_frac=0.30, device="cuda",
+                      render_frames=None):
+    """synth.make_sequence's scene, rendered on the device: (luma, alpha, meta).
+    render_frames: only the first frames of the F-frame scene (identical to
+    those of the whole rendering: the scene is drawn for F frames and the
+    noise is drawn frame after frame)."""
     background, bg_offsets, objects, _ = synth.draw_scene(W, H, F, seed, n_objects, vmax, bg_step, blobby,
                                                           change_every, max_rot_deg, scale_range, obj_frac)
-    luma, alpha = render_gpu(W, H, F, background, bg_offsets, objects, noise_sigma, seed, device)
+    Fr = F if render_frames is None else min(F, render_frames)
+    luma, alpha = render_gpu(W, H, Fr, background, bg_offsets, objects, noise_sigma, seed, device)
     meta = dict(width=W, height=H, frames=F, n_objects=n_objects, vmax=vmax, noise_sigma=noise_sigma,
                 seed=seed, generator="numpy PCG64 scene, torch CUDA noise, FP32 device rendering")
     return luma, alpha, meta

@@ -155,3 +155,46 @@ def test_batch_two_stage_run_and_class_maps(sme, schedule, param, flag):
     b.synchronize()
     _check_all(b.outputs, seqs)
     b.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_batch_host_upload_run_download(sme, pinned):
+    """Host-to-host pass: the batch is created over empty device buffers,
+    the inputs come from host memory (sme_batch_upload, a luma plane shared
+    by the VOPs of one scene copied once), the results go back to host memory
+    (sme_batch_download); they equal the oracle's."""
+    seqs = _batch_inputs()
+    dev_luma, lumas, alphas = {}, [], []
+    for l, a in seqs:
+        key = l.ctypes.data  # the VOPs of one scene share one luma array
+        if key not in dev_luma:
+            dev_luma[key] = torch.zeros(l.shape, dtype=torch.uint8, device="cuda")
+        lumas.append(dev_luma[key])
+        alphas.append(torch.zeros(a.shape, dtype=torch.uint8, device="cuda"))
+    b = sme.Batch(lumas, alphas, search_range=16, subpel=2)
+    b.set_config("sparse", 2, 0)
+    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+    host_in = [(pin(torch.from_numpy(l)), pin(torch.from_numpy(a))) for l, a in seqs]
+    host_out = [{"mv": pin(torch.zeros(tuple(o["mv"].shape), dtype=torch.int16)),
+                 "sse": pin(torch.zeros(tuple(o["sse"].shape), dtype=torch.int64)),
+                 "cost": pin(torch.zeros(tuple(o["cost"].shape), dtype=torch.int32))} for o in b.outputs]
+    io = b.host_io(host_in, host_out)
+    for _ in range(2):
+        b.upload(io)
+        b.run(sync=False)
+        b.download(io)
+        b.synchronize()
+        for (luma, alpha), h in zip(seqs, host_out):
+            F, H, W = luma.shape
+            o = O.estimate_sequence(O.OracleParams(W, H, 16, 2), luma, alpha)
+            assert np.array_equal(h["mv"].numpy(), o["mv"])
+            assert np.array_equal(h["sse"].numpy().view(np.uint64), o["sse"])
+            assert np.array_equal(h["cost"].numpy().view(np.uint32), o["cost"])
+        for h in host_out:
+            for v in h.values():
+                v.zero_()
+    # an output that was not requested at creation cannot be downloaded
+    bad = b.host_io(host_in, [{"pred": torch.zeros(1, dtype=torch.uint8)} for _ in host_out])
+    with pytest.raises(sme.SmeError):
+        b.download(bad)
+    b.close()

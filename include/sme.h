@@ -220,8 +220,8 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     by several VOPs), then the per-MB search runs over a list of the
  *     other MBs in wavefront order, taking a transparent neighbour's (0,0)
  *     from the class map without waiting (never speculatively);
- *     SME_OPT_MB_CTAS_PER_SM 2 selects the search kernel built for two
- *     resident CTAs per SM, else one;
+ *     SME_OPT_MB_CTAS_PER_SM 2 or 3 selects the search kernel built for
+ *     that many resident CTAs per SM, else one;
  *     SME_SCHED_AUTO (default) -- chosen per workload.
  *   SME_OPT_PAIR_WARPS: warps (MB rows in flight) per CTA of the pair
  *     schedule, 1..16 (at most 8 used with SME_OPT_PAIR_DIRECT); 0
@@ -319,8 +319,8 @@ int sme_autotune(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha, int n_
  *                      SME_SCHED_MB (param = CTAs per SM, 0..32, 0 = all that
  *                      fit; flag = speculation), SME_SCHED_PAIR (param =
  *                      warps per CTA, 0..16, 0 = automatic; flag = direct
- *                      transparent runs) or SME_SCHED_SPARSE (param 0..2: 2 =
- *                      the search kernel built for two CTAs per SM; flag
+ *                      transparent runs) or SME_SCHED_SPARSE (param 0..3: 2, 3
+ *                      = the search kernel built for that many CTAs per SM; flag
  *                      0 or 1, unused); drops a captured graph (later runs
  *                      launch directly until sme_batch_tune).  SME_ERR_ARG on
  *                      other values.
@@ -365,6 +365,8 @@ int sme_batch_class_map(sme_batch* b, int seq, const uint8_t** mb_class);
  * sequence count) into the device buffers the batch was created with, on the
  * batch's stream; a luma plane that sequence i shares with sequence i - 1
  * (the same device address: the VOPs of one scene) is copied once.
+ * The copies run on four internal streams forked from and joined back to
+ * the batch's stream, so that several copy engines share them.
  * sme_batch_download copies every non-NULL HOST pointer of io[i].out from
  * the matching device output of sequence i (SME_ERR_ARG if that output was
  * not requested at creation).  Both are asynchronous on the batch's stream

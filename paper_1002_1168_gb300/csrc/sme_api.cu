@@ -598,6 +598,7 @@ const ExecCfg kTuneCandidates[] = {
     {kSchedPair, 4, 0, 0, 0, 0},     {kSchedPair, 8, 0, 0, 0, 0},
     {kSchedPair, 16, 0, 0, 0, 0},    {kSchedCluster, 0, 0, 1, 16, 1}, {kSchedCluster, 0, 0, 0, 16, 1},
     {kSchedCluster, 0, 0, 1, 8, 1},  {kSchedSparse, 0, 1, 0, 0, 1},   {kSchedSparse, 0, 2, 0, 0, 1},
+    {kSchedSparse, 0, 3, 0, 0, 1},
 };
 
 // Device time of `trials` back-to-back runs of `enqueue` (the minimum), ms;
@@ -1198,6 +1199,11 @@ struct sme_batch {
     SparseScratch sp;
     std::vector<size_t> cls_off;  // byte offset of each sequence's class map [F][M] in cls
     std::vector<SeqDesc> host_desc;  // the descriptors (device addresses, sizes) of every sequence
+    // host-buffer uploads: copies spread over several streams (copy engines),
+    // forked from and joined back to the batch's stream
+    static constexpr int kCopyStreams = 4;
+    cudaStream_t copy[kCopyStreams] = {};
+    cudaEvent_t fork = nullptr, join[kCopyStreams] = {};
     ExecCfg cfg = {kSchedMB, 0, 0, 1, 0, 1};
     float tuned_ms = 0.0f;
     cudaGraph_t graph = nullptr;
@@ -1515,19 +1521,38 @@ int sme_batch_upload(sme_batch* b, const sme_host_io* io, int n)
     if (!b || !io || n != b->n) return SME_ERR_ARG;
     for (int i = 0; i < n; ++i)
         if (!io[i].luma || !io[i].alpha) return SME_ERR_ARG;
+    const int K = sme_batch::kCopyStreams;
+    if (!b->fork) {
+        if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return SME_ERR_CUDA;
+        for (int c = 0; c < K; ++c)
+            if (cudaStreamCreateWithFlags(&b->copy[c], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming) != cudaSuccess)
+                return SME_ERR_CUDA;
+    }
+    // the copies start after the work already queued on the batch's stream
+    // (which may still read the buffers) and the stream waits for all of them
+    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return SME_ERR_CUDA;
+    for (int c = 0; c < K; ++c)
+        if (cudaStreamWaitEvent(b->copy[c], b->fork, 0) != cudaSuccess) return SME_ERR_CUDA;
     const void* last_luma = nullptr;
+    int next = 0;
     for (int i = 0; i < n; ++i) {
         const SeqDesc& d = b->host_desc[i];
         const size_t bytes = (size_t)d.F * d.W * d.H;
         // a luma plane shared with the previous sequence (the same device
         // address: the VOPs of one scene) is copied once
-        if (d.luma != last_luma &&
-            cudaMemcpyAsync((void*)d.luma, io[i].luma, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        if (d.luma != last_luma && cudaMemcpyAsync((void*)d.luma, io[i].luma, bytes, cudaMemcpyHostToDevice,
+                                                   b->copy[next++ % K]) != cudaSuccess)
             return SME_ERR_CUDA;
         last_luma = d.luma;
-        if (cudaMemcpyAsync((void*)d.alpha, io[i].alpha, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        if (cudaMemcpyAsync((void*)d.alpha, io[i].alpha, bytes, cudaMemcpyHostToDevice, b->copy[next++ % K]) !=
+            cudaSuccess)
             return SME_ERR_CUDA;
     }
+    for (int c = 0; c < K; ++c)
+        if (cudaEventRecord(b->join[c], b->copy[c]) != cudaSuccess ||
+            cudaStreamWaitEvent(b->stream, b->join[c], 0) != cudaSuccess)
+            return SME_ERR_CUDA;
     return SME_OK;
 }
 
@@ -1591,7 +1616,7 @@ int sme_batch_set_config(sme_batch* b, int schedule, int param, int flag)
         e.speculate = flag;
         break;
     case kSchedSparse:
-        if (param < 0 || param > 2) return SME_ERR_ARG;
+        if (param < 0 || param > 3) return SME_ERR_ARG;
         e.mb_ctas_per_sm = param;
         e.speculate = flag;
         break;
@@ -1619,6 +1644,14 @@ int sme_batch_destroy(sme_batch* b)
                       &b->unit_pair, &b->fseq, &b->ffrm, &b->maps};
     for (DevBuf* x : bufs) release(*x);
     release_sparse(b->sp);
+    for (int c = 0; c < sme_batch::kCopyStreams; ++c) {
+        if (b->copy[c]) {
+            cudaStreamSynchronize(b->copy[c]);
+            cudaStreamDestroy(b->copy[c]);
+        }
+        if (b->join[c]) cudaEventDestroy(b->join[c]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->status) cudaFree(b->status);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;

@@ -218,7 +218,7 @@ cudaError_t launch_compensate(const Geom& g, const Method& m, const CompArgs& a,
 // Sparse schedule: preparation (desc: single-sequence descriptor stored by the
 // reset launch, or NULL when a.seqs already holds the descriptors) and the search.
 cudaError_t launch_sparse_prep(const SparseArgs& a, const SeqDesc* desc, cudaStream_t s);
-// min_blocks selects the register budget of the search kernel (1 or 2 CTAs per SM).
+// min_blocks selects the register budget of the search kernel (1, 2 or 3 CTAs per SM).
 cudaError_t me_sparse_occupancy(int S, int min_blocks, int* blocks_per_sm, bool variants);
 cudaError_t launch_me_sparse(const Method& m, const MeArgs& a, int grid, int min_blocks, cudaStream_t s);
 

@@ -1447,22 +1447,18 @@ __global__ void __launch_bounds__(256) sparse_stream_kernel(const SparseArgs a)
     }
     __syncthreads();
     const size_t FS = (size_t)W * H;
-    const int hw = 2 * Wp;  // u16 slots per packed row
-    for (int u = tid; u < hw; u += blockDim.x) {
-        if (u >= MBW) {  // the zero words that end every packed row
-            for (int j = 0; j < nm; ++j) {
-                const SeqDesc* sd = a.seqs + __ldg(a.grp_members + m0 + j);
-                uint16_t* pk = reinterpret_cast<uint16_t*>(sd->packed_w + ((size_t)f * H + 16 * v) * Wp);
-#pragma unroll
-                for (int r = 0; r < 16; ++r) pk[(size_t)r * hw + u] = 0;
-            }
-            continue;
-        }
-        const size_t px = (size_t)(16 * v) * W + 16 * u;
+    const int hw = 2 * Wp;  // u16 slots per packed row (the slots from MBW on stay zero)
+    const int lane = tid & 31;
+    // Warp-uniform passes over the MB columns u (lane = column), so the
+    // per-VOP counts and sums are warp reductions, not shared atomics.
+    for (int u0 = tid & ~31; u0 < hw; u0 += blockDim.x) {
+        const int u = u0 + lane;
+        const bool col = u < MBW;
+        const size_t px = (size_t)(16 * v) * W + 16 * (col ? u : 0);
         // Sec. 4: the co-located prediction error of the MB, shared by every
         // VOP of the group (a transparent MB predicts from (0,0)).
         unsigned sse0 = 0;
-        if (k >= 0) {
+        if (k >= 0 && col) {
             const uint8_t* cur = s0->luma + (size_t)f * FS + px;
             const uint8_t* ref = s0->luma + (size_t)k * FS + px;
 #pragma unroll 4
@@ -1472,26 +1468,37 @@ __global__ void __launch_bounds__(256) sparse_stream_kernel(const SparseArgs a)
         }
         for (int j = 0; j < nm; ++j) {
             const SeqDesc* sd = a.seqs + __ldg(a.grp_members + m0 + j);
-            const uint8_t* al = sd->alpha + (size_t)f * FS + px;
             uint16_t* pk = reinterpret_cast<uint16_t*>(sd->packed_w + ((size_t)f * H + 16 * v) * Wp);
-            unsigned n = 0;
+            int cls = SME_TRANSPARENT;
+            if (col) {
+                const uint8_t* al = sd->alpha + (size_t)f * FS + px;
+                unsigned n = 0;
 #pragma unroll 8
-            for (int r = 0; r < 16; ++r) {
-                const unsigned bits = bab_bits16(al + (size_t)r * W);
-                n += __popc(bits);
-                pk[(size_t)r * hw + u] = (uint16_t)bits;
+                for (int r = 0; r < 16; ++r) {
+                    const unsigned bits = bab_bits16(al + (size_t)r * W);
+                    n += __popc(bits);
+                    pk[(size_t)r * hw + u] = (uint16_t)bits;
+                }
+                cls = n == 0 ? SME_TRANSPARENT : (n == 256 ? SME_OPAQUE : SME_BOUNDARY);
+                sd->cls_w[(size_t)f * M + v * MBW + u] = (uint8_t)cls;
+            } else if (u < hw) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) pk[(size_t)r * hw + u] = 0;
             }
-            const int cls = n == 0 ? SME_TRANSPARENT : (n == 256 ? SME_OPAQUE : SME_BOUNDARY);
-            const int mb = v * MBW + u;
-            sd->cls_w[(size_t)f * M + mb] = (uint8_t)cls;
-            if (k < 0) continue;
-            if (cls != SME_TRANSPARENT) {
-                atomicAdd(&s_cnt[j], 1u);
-                atomicMin(&s_umin[j], u);
-                continue;
+            if (k < 0) continue;  // uniform: frames before the first pair's current frame
+            const unsigned listed = __ballot_sync(kFull, col && cls != SME_TRANSPARENT);
+            if (lane == 0 && listed) {
+                atomicAdd(&s_cnt[j], (unsigned)__popc(listed));
+                atomicMin(&s_umin[j], u0 + __ffs(listed) - 1);
             }
+            const bool tr = col && cls == SME_TRANSPARENT;
+            if (sd->sse) {  // below 32 x 2^24: one 32-bit reduction
+                const unsigned ws = __reduce_add_sync(kFull, tr ? sse0 : 0u);
+                if (lane == 0 && ws) atomicAdd(&s_sse[j], (unsigned long long)ws);
+            }
+            if (!tr) continue;
             // Fig. 1: no vector is computed for a transparent MB.
-            const size_t idx = (size_t)k * M + mb;
+            const size_t idx = (size_t)k * M + v * MBW + u;
             sd->mv[idx] = sme_mv{0, 0};
             if (sd->cost) sd->cost[idx] = 0;
             if (sd->disp) {
@@ -1502,7 +1509,6 @@ __global__ void __launch_bounds__(256) sparse_stream_kernel(const SparseArgs a)
             if (sd->npos) sd->npos[idx] = 0;
             if (sd->out_cls) sd->out_cls[idx] = (uint8_t)SME_TRANSPARENT;
             if (sd->sse_mb) sd->sse_mb[idx] = sse0;
-            if (sd->sse) atomicAdd(&s_sse[j], (unsigned long long)sse0);
             if (sd->pred) {
                 const uint8_t* ref = sd->luma + (size_t)k * FS + px;
                 uint8_t* pr = sd->pred + (size_t)k * FS + px;
@@ -1633,7 +1639,7 @@ __device__ __forceinline__ int seq_of_gid(const int* seq_base, int n, int gid)
 // of an MB has a smaller key, hence an earlier ticket, so the warps (all
 // resident) can always make progress, as in me_kernel.
 // kMinBlocks: CTAs per SM the register budget is cut for (1: no spills, one
-// 8-warp CTA per SM; 2: twice the warps with a few spills), chosen by tuning.
+// 8-warp CTA per SM; 2 and 3: more warps, with some spills), chosen by tuning.
 template <bool kVariants, int kMinBlocks>
 __global__ void __launch_bounds__(32 * kMeWarps, kMinBlocks) me_sparse_kernel(const MeArgs a)
 {
@@ -3129,8 +3135,13 @@ cudaError_t sparse_attr(const void** fn, size_t smem)
 
 cudaError_t sparse_kernel(bool variants, int min_blocks, size_t smem, const void** fn)
 {
-    if (variants) return min_blocks >= 2 ? sparse_attr<true, 2>(fn, smem) : sparse_attr<true, 1>(fn, smem);
-    return min_blocks >= 2 ? sparse_attr<false, 2>(fn, smem) : sparse_attr<false, 1>(fn, smem);
+    if (variants)
+        return min_blocks >= 3   ? sparse_attr<true, 3>(fn, smem)
+               : min_blocks == 2 ? sparse_attr<true, 2>(fn, smem)
+                                 : sparse_attr<true, 1>(fn, smem);
+    return min_blocks >= 3   ? sparse_attr<false, 3>(fn, smem)
+           : min_blocks == 2 ? sparse_attr<false, 2>(fn, smem)
+                             : sparse_attr<false, 1>(fn, smem);
 }
 
 cudaError_t me_sparse_occupancy(int S, int min_blocks, int* blocks_per_sm, bool variants)

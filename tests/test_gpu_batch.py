@@ -75,7 +75,7 @@ def test_autotune_context_keeps_results(sme):
     est.close()
 
 
-@pytest.mark.parametrize("schedule,param,flag", [("sparse", 1, 1), ("sparse", 2, 0), ("sparse", 2, 1), ("mb", 0, 1),
+@pytest.mark.parametrize("schedule,param,flag", [("sparse", 1, 1), ("sparse", 2, 0), ("sparse", 3, 0), ("mb", 0, 1),
                                                  ("pair", 8, 1), ("pair", 4, 0)])
 def test_batch_each_configuration_matches_oracle(sme, schedule, param, flag):
     """Every execution configuration of a batch, set explicitly, gives the
@@ -109,7 +109,7 @@ def test_batch_set_config_rejects_bad_values(sme):
     with pytest.raises(sme.SmeError):
         b.set_config("cluster")
     with pytest.raises(sme.SmeError):
-        b.set_config("sparse", 3)
+        b.set_config("sparse", 4)
     with pytest.raises(sme.SmeError):
         b.set_config("pair", 17)
     b.close()

@@ -267,7 +267,9 @@ def train_seednet(sme, torch, args):
     from paper_1002_1168_gb300 import seedtrain, synth
 
     t0 = time.perf_counter()
-    pairs = seedtrain.training_pairs(args.learn_pairs, seed=11, workers=min(os.cpu_count() or 1, 16))
+    # three-frame sequences: each VOP gives a first pair (no previous field)
+    # and a second one with the plain method's first field as network input
+    pairs = seedtrain.training_pairs(args.learn_pairs, seed=11, workers=min(os.cpu_count() or 1, 16), frames=3)
     gen_s = time.perf_counter() - t0
     net = sme.SeedNet(max_cells=len(pairs) * (H // 4) * (W // 4))
     net.set_params(sme.pack_params(synth.seednet_init(3)))
@@ -830,6 +832,48 @@ def measure_headline(sme, torch, args, net, dist, rank):
         gc.collect()
         torch.cuda.empty_cache()
 
+    # ---- the oracle on sampled pairs of a learned field, given the GPU's
+    # previous field and the same seeds
+    samples = [(min(7, n_seq - 1), 3, min(30, F - 2)), (0, 0, 1), (n_seq - 1, 7, F - 2)]
+
+    def oracle_pairs(outputs, seeds):
+        ok = True
+        for s_, j_, k_ in samples:
+            q = 8 * s_ + j_
+            out = outputs[q]
+            luma, alpha, _ = seqs[s_]
+            tmp = None if k_ == 0 else out["mv"][k_ - 1].cpu().numpy()
+            o = O.estimate_sequence(O.OracleParams(UHD_W, UHD_H, UHD_S, 2), luma[k_:k_ + 2].cpu().numpy(),
+                                    alpha[j_, k_:k_ + 2].cpu().numpy(), temporal_in=tmp,
+                                    seed=seeds[q][k_:k_ + 1].cpu().numpy())
+            ok &= bool(np.array_equal(out["mv"][k_].cpu().numpy(), o["mv"][0]) and
+                       np.array_equal(out["cost"][k_].cpu().numpy().view(np.uint32), o["cost"][0]) and
+                       np.array_equal(out["iters"][k_].cpu().numpy(), o["iters"][0]) and
+                       int(out["sse"][k_].item()) == int(o["sse"][0]))
+        return ok
+
+    # ---- learned, pair rounds: the previous pair's field as network input
+    rounds = None
+    if net is not None and not args.no_rounds:
+        rnet = sized_net(sme, net, n_seq * (UHD_H // 4) * (UHD_W // 4))
+        lr = seedtrain.LearnedRounds(rnet, groups, search_range=UHD_S, subpel=2, want=want)
+        lr.tune(trials=1)
+        ms_r, _, _ = timed(lambda: lr.run(sync=False), lr.stream)
+        lr.synchronize()
+        rq = _device_quality(lr.outputs, UHD_W, UHD_H)
+        rounds = {"value": job_rate(total, ws, ms_r / 1e3), "unit": UNIT, "ms_per_run": ms_r,
+                  "config": lr.config(), **rq, "psnr_delta_db": rq["psnr_db_mean"] - plain_q["psnr_db_mean"],
+                  "iters_delta_pct": 100.0 * (rq["iters_per_opaque_mb"] / plain_q["iters_per_opaque_mb"] - 1.0),
+                  "vs_plain_batched": ms_plain / ms_r,
+                  "bit_exact_vs_oracle_sample": oracle_pairs(lr.outputs, lr.seeds),
+                  "form": "pair rounds: the network of pair k sees the final field of pair k-1",
+                  "launches_per_run": 5 + lr.rounds * (1 + 7 + 1) - 1}
+        lr.close()
+        rnet.close()
+        del lr
+        gc.collect()
+        torch.cuda.empty_cache()
+
     # ---- learned batch (the headline; the plain batch when no network is trained)
     if net is not None:
         net = sized_net(sme, net, P * (UHD_H // 4) * (UHD_W // 4))
@@ -850,21 +894,7 @@ def measure_headline(sme, torch, args, net, dist, rank):
         lq, learned_ops = plain_q, plain_ops
         head_batch, head_runner = b, b
 
-    # ---- oracle legs: the learned field on sampled pairs given the GPU's previous field and the same seeds
-    samples = [(min(7, n_seq - 1), 3, min(30, F - 2)), (0, 0, 1), (n_seq - 1, 7, F - 2)]
-    lexact = True
-    for s_, j_, k_ in (samples if lb is not None else []):
-        q = 8 * s_ + j_
-        out = lb.outputs[q]
-        luma, alpha, _ = seqs[s_]
-        tmp = None if k_ == 0 else out["mv"][k_ - 1].cpu().numpy()
-        o = O.estimate_sequence(O.OracleParams(UHD_W, UHD_H, UHD_S, 2), luma[k_:k_ + 2].cpu().numpy(),
-                                alpha[j_, k_:k_ + 2].cpu().numpy(), temporal_in=tmp,
-                                seed=lb.seeds[q][k_:k_ + 1].cpu().numpy())
-        lexact &= bool(np.array_equal(out["mv"][k_].cpu().numpy(), o["mv"][0]) and
-                       np.array_equal(out["cost"][k_].cpu().numpy().view(np.uint32), o["cost"][0]) and
-                       np.array_equal(out["iters"][k_].cpu().numpy(), o["iters"][0]) and
-                       int(out["sse"][k_].item()) == int(o["sse"][0]))
+    lexact = oracle_pairs(lb.outputs, lb.seeds) if lb is not None else True
 
     # ---- end to end through the host-buffer calls (pinned host memory)
     e2e = None
@@ -934,6 +964,7 @@ def measure_headline(sme, torch, args, net, dist, rank):
                   "config": plain_cfg, **plain_q,
                   "stage_ms": {"classify_stream": st_plain[0], "search": st_plain[2]},
                   "bit_exact_vs_oracle_sample": cpu["plain_field_bit_exact_vs_oracle"] if cpu else None},
+        "learned_rounds": rounds,
         "learned": {"value": job_rate(total, ws, ms_learned / 1e3), "ms_per_run": ms_learned, "config": learned_cfg,
                     **lq, "psnr_delta_db": lq["psnr_db_mean"] - plain_q["psnr_db_mean"],
                     "vs_plain_batched": ms_plain / ms_learned,
@@ -1190,7 +1221,7 @@ def run_ours(args):
                    "l2": "inputs (72 GB) far above L2; no flush needed",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "execution": learned["config"] if learned else head["plain"]["config"]},
-        "plain": head["plain"], "learned_seeded": learned,
+        "plain": head["plain"], "learned_seeded": learned, "learned_seeded_pair_rounds": head["learned_rounds"],
         "clocks": head["clocks"],
         "e2e": head["e2e"] or {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": head["launches_per_run"] * head["steps"],
@@ -1251,6 +1282,7 @@ def main():
     ap.add_argument("--no-hd", action="store_true", help="skip the 1920x1088 x 300-frame learned evaluation")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper-setting QCIF measurement")
     ap.add_argument("--no-e2e", action="store_true", help="skip the headline's host-buffer (end-to-end) runs")
+    ap.add_argument("--no-rounds", action="store_true", help="skip the pair-round learned form at the headline")
     ap.add_argument("--hd-frames", type=int, default=300, help="frames of the 1920x1088 learned evaluation")
     ap.add_argument("--learn-pairs", type=int, default=2000, help="CIF VOP pairs the seed network is trained on")
     ap.add_argument("--learn-steps", type=int, default=800, help="Adam steps (32 pairs each)")

@@ -172,6 +172,14 @@ int sme_advance(sme_ctx* ctx);
 int sme_score(sme_ctx* ctx, double* psnr_db);
 int sme_get_temporal_field(sme_ctx* ctx, sme_mv* field /* [M] device out */);
 int sme_set_temporal_field(sme_ctx* ctx, const sme_mv* field /* [M] device, NULL = zeros */);
+/* Seeds of the pair interface (the learned proposal; the paper's own seeds
+ * are the neighbour and temporal vectors of Sec. 3.1): seed [M][2] device
+ * FP32 pixels, copied into a context-owned buffer and used by every following
+ * sme_estimate as the fifth candidate of each MB exactly as the `seed`
+ * argument of sme_estimate_sequence (rounded to the MV grid, clamped to V,
+ * plain search as fallback), until replaced, or cleared with NULL.
+ * SME_ERR_ARG with max_iters > 8 or in the four-vector mode. */
+int sme_set_seed_field(sme_ctx* ctx, const float* seed);
 
 /* Motion compensation of one frame pair with a caller-supplied field (Sec. 4):
  * pred(p) = ref(p + mv(mb(p))) with half-sample interpolation, and the SSE
@@ -360,6 +368,19 @@ int sme_batch_set_config(sme_batch* b, int schedule, int param, int flag);
  * or sequence index. */
 int sme_batch_run_stage(sme_batch* b, int stage);
 int sme_batch_class_map(sme_batch* b, int seq, const uint8_t** mb_class);
+/* Pair rounds (sparse schedule only), for callers whose seeds for pair k
+ * depend on the field of pair k - 1 (the learned proposal with the previous
+ * field as input): sme_batch_set_pair_rounds(b, 1) lists the non-transparent
+ * MBs pair by pair (and selects the sparse schedule; synchronises), so that
+ * after stage 1, sme_batch_run_pair(b, k) for k = 0, 1, ... (in this order,
+ * each after the previous one on the batch's stream) searches pair k of every
+ * sequence, its temporal candidates being the results of round k - 1; stage
+ * 2 runs every round in order.  Results are those of sme_batch_run.
+ * sme_batch_set_pair_rounds(b, 0) returns to the whole-list order.
+ * SME_ERR_ARG for k outside [0, largest pair count) or without pair rounds;
+ * other schedules are then rejected by sme_batch_set_config. */
+int sme_batch_set_pair_rounds(sme_batch* b, int on);
+int sme_batch_run_pair(sme_batch* b, int k);
 /* Host-memory inputs and outputs of a batch.  sme_batch_upload copies io[i]
  * (HOST luma and alpha, [n_frames][H][W] of sequence i; n = the batch's
  * sequence count) into the device buffers the batch was created with, on the
@@ -423,7 +444,10 @@ int sme_batch_destroy(sme_batch* b);
  *                         as a DEVICE table rows [n_maps][n] of pointers to
  *                         [M] class rows (a NULL entry: every MB transparent),
  *                         so maps written elsewhere (sme_batch_class_map) are
- *                         read in place.
+ *                         read in place; the seeds go to `seeds` [n][M][2]
+ *                         (the other MBs get (0, 0)) or, with seeds NULL, to
+ *                         the DEVICE table seed_rows [n] of pointers to
+ *                         [M][2] rows (the other MBs' entries untouched).
  *   sme_seednet_set_stream  stream of the network's later calls.
  *   sme_seednet_synchronize waits for the network's stream; SME_ERR_TIMEOUT
  *                         if a device-side wait of an earlier call gave up
@@ -443,16 +467,25 @@ int sme_seednet_features(sme_seednet* net, const uint8_t* luma, int width, int h
                          int subpel, uint16_t* feat);
 /* The same features for n_pairs pairs gathered from anywhere, in one launch:
  * frames is a DEVICE array [n_pairs][2] of pointers to [height][width] luma
- * frames (reference, current; each 4-byte aligned); feat as above (no
- * temporal input). */
-int sme_seednet_features_table(sme_seednet* net, const uint8_t* const* frames, int n_pairs, int width,
-                               int height, int subpel, uint16_t* feat);
+ * frames (reference, current; each 4-byte aligned); temporal is NULL or a
+ * DEVICE array [n_pairs] of pointers to [M] temporal fields (a NULL entry:
+ * zeros); feat as above. */
+int sme_seednet_features_table(sme_seednet* net, const uint8_t* const* frames, const sme_mv* const* temporal,
+                               int n_pairs, int width, int height, int subpel, uint16_t* feat);
+/* One temporal field per scene for the network input, for n scenes of
+ * n_vops VOPs each, from the VOPs' fields (DEVICE arrays [n][n_vops] of
+ * pointers: fields[q][j] [M] vectors, classes[q][j] [M] MB classes, either
+ * NULL for an absent VOP): MB m of scene q takes fields[q][j][m] of the
+ * first VOP j whose class is not transparent there, else (0, 0); out [n][M]
+ * device.  No counterpart in the paper. */
+int sme_seednet_temporal_composite(sme_seednet* net, const sme_mv* const* fields, const uint8_t* const* classes,
+                                   int n, int n_vops, int width, int height, sme_mv* out);
 int sme_seednet_forward(sme_seednet* net, const uint16_t* feat, int n, int width, int height, float* seeds,
                         float* out_cells);
 int sme_seednet_forward_active(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
                                const uint8_t* mb_class, int n_maps, long long map_stride, float* seeds);
 int sme_seednet_forward_active_table(sme_seednet* net, const uint16_t* feat, int n, int width, int height,
-                                     const uint8_t* const* rows, int n_maps, float* seeds);
+                                     const uint8_t* const* rows, int n_maps, float* seeds, float* const* seed_rows);
 int sme_seednet_set_stream(sme_seednet* net, void* cuda_stream);
 int sme_seednet_synchronize(sme_seednet* net);
 int sme_seednet_gradients(sme_seednet* net, const uint16_t* feat, int n, int width, int height,

@@ -47,8 +47,10 @@ struct DevBuf {
 // streaming pass, the per-row counts, the per-step offsets and cursors, the
 // list of non-transparent MBs and its counters.
 struct SparseScratch {
-    DevBuf grp_first, grp_members, gf_group, gf_frame, row_base, rowcnt, hist, cursor, list, ctr, seq_base, first;
+    DevBuf grp_first, grp_members, gf_group, gf_frame, row_base, rowcnt, hist, cursor, list, ctr, seq_base, first,
+        round_ticket;
     int n_gf = 0, max_mbh = 0, steps = 0, nseq = 0;
+    int pair_keys = 0, rounds = 0;  // pair rounds: keys per pair (0: off), pairs of the longest sequence
     long long total_rows = 0;
     const void* key = nullptr;  // single-sequence path: the set-up is reused while (luma, F) stay the same
     int key_f = -1;
@@ -74,8 +76,8 @@ struct sme_ctx {
     int fault_ticket = -1;
     long long timeout_ns = kDefaultTimeoutNs;
     // pair interface
-    DevBuf pair_luma, pair_alpha, temporal, last_mv, last_sse;
-    bool have_ref = false, have_cur = false, have_temporal = false, have_result = false;
+    DevBuf pair_luma, pair_alpha, temporal, last_mv, last_sse, seed_field;
+    bool have_ref = false, have_cur = false, have_temporal = false, have_result = false, have_seed = false;
     // stage timing: three events per recorded call
     std::vector<cudaEvent_t> prof_ev;
     int prof_max = 0, prof_n = 0;
@@ -122,7 +124,8 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 void release_sparse(SparseScratch& sp)
 {
     DevBuf* bufs[] = {&sp.grp_first, &sp.grp_members, &sp.gf_group, &sp.gf_frame, &sp.row_base, &sp.rowcnt,
-                      &sp.hist,      &sp.cursor,      &sp.list,     &sp.ctr,      &sp.seq_base, &sp.first};
+                      &sp.hist,      &sp.cursor,      &sp.list,     &sp.ctr,      &sp.seq_base, &sp.first,
+                      &sp.round_ticket};
     for (DevBuf* b : bufs) release(*b);
     sp = SparseScratch{};
 }
@@ -141,20 +144,26 @@ int upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s)
 // descriptors, in launch order): sequences sharing one luma plane, size and
 // frame count form a group (at most kGroupMax VOPs) whose co-located errors
 // the streaming pass computes once; one block row per (group, frame).
-int setup_sparse(SparseScratch& sp, const std::vector<SeqDesc>& d, cudaStream_t s)
+int setup_sparse(SparseScratch& sp, const std::vector<SeqDesc>& d, cudaStream_t s, bool rounds = false)
 {
     const int n = (int)d.size();
     std::vector<int> first, members, gfg, gff, base(n);
     std::vector<long long> rb(n);
     std::vector<int> gid_of(n, -1);
     long long rows = 0;
-    int steps = 0, max_mbh = 0;
+    int steps = 0, max_mbh = 0, pair_keys = 0, max_p = 0;
     for (int i = 0; i < n; ++i) {
         rb[i] = rows;
         rows += (long long)d[i].F * d[i].MBH;
         base[i] = d[i].gid_base;
         steps = std::max(steps, (d[i].MBW - 1) + 2 * (d[i].MBH - 1) + d[i].P);
+        pair_keys = std::max(pair_keys, (d[i].MBW - 1) + 2 * (d[i].MBH - 1) + 1);
+        max_p = std::max(max_p, d[i].P);
         max_mbh = std::max(max_mbh, d[i].MBH);
+    }
+    if (rounds) {
+        if ((long long)pair_keys * max_p > (1LL << 26)) return SME_ERR_SIZE;
+        steps = pair_keys * max_p;
     }
     for (int i = 0; i < n; ++i) {
         if (gid_of[i] >= 0) continue;
@@ -179,12 +188,14 @@ int setup_sparse(SparseScratch& sp, const std::vector<SeqDesc>& d, cudaStream_t 
         (rc = upload(sp.gf_group, gfg, s)) || (rc = upload(sp.gf_frame, gff, s)) || (rc = upload(sp.row_base, rb, s)) ||
         (rc = upload(sp.seq_base, base, s)) || (rc = ensure(sp.rowcnt, (size_t)rows * 4)) ||
         (rc = ensure(sp.hist, ((size_t)steps + 1) * 32)) || (rc = ensure(sp.cursor, (size_t)steps * 32)) ||
-        (rc = ensure(sp.first, (size_t)n * 4)) ||
+        (rc = ensure(sp.first, (size_t)n * 4)) || (rc = ensure(sp.round_ticket, (size_t)max_p * 4)) ||
         (rc = ensure(sp.list, total * 4)) || (rc = ensure(sp.ctr, sizeof(SparseCounters))))
         return rc;
     sp.n_gf = (int)gfg.size();
     sp.max_mbh = max_mbh;
     sp.steps = steps;
+    sp.pair_keys = rounds ? pair_keys : 0;
+    sp.rounds = max_p;
     sp.nseq = n;
     sp.total_rows = rows;
     return SME_OK;
@@ -209,6 +220,9 @@ SparseArgs sparse_args(const SparseScratch& sp, SeqDesc* seqs, DevStatus* status
     a.first_step = (int*)sp.first.p;
     a.cursor = (unsigned*)sp.cursor.p;
     a.steps = sp.steps;
+    a.pair_keys = sp.pair_keys;
+    a.round_ticket = (unsigned*)sp.round_ticket.p;
+    a.rounds = sp.rounds;
     a.list = (int*)sp.list.p;
     a.ctr = (SparseCounters*)sp.ctr.p;
     a.status = status;
@@ -218,7 +232,7 @@ SparseArgs sparse_args(const SparseScratch& sp, SeqDesc* seqs, DevStatus* status
 // The search launch of the sparse schedule: every CTA resident (the warps
 // wait on each other), min_blocks selects the register budget.
 int launch_sparse_search(const Method& m, MeArgs a, const SparseScratch& sp, int num_sms, int min_blocks,
-                         cudaStream_t s)
+                         cudaStream_t s, int round = -1)
 {
     int per_sm = 0;
     if (me_sparse_occupancy(m.S, min_blocks, &per_sm, m.tt != 0) != cudaSuccess || per_sm < 1) return SME_ERR_CUDA;
@@ -226,6 +240,11 @@ int launch_sparse_search(const Method& m, MeArgs a, const SparseScratch& sp, int
     a.seq_base = (const int*)sp.seq_base.p;
     a.nseq = sp.nseq;
     a.ctr = (SparseCounters*)sp.ctr.p;
+    a.round = round;
+    a.pair_keys = sp.pair_keys;
+    a.rounds = sp.rounds;
+    a.offs = (const unsigned*)sp.hist.p;
+    a.round_ticket = (unsigned*)sp.round_ticket.p;
     return cuda_status(launch_me_sparse(m, a, num_sms * per_sm, min_blocks, s));
 }
 
@@ -698,7 +717,7 @@ int sme_destroy(sme_ctx* c)
     if (!c) return SME_ERR_ARG;
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->packed, &c->cls, &c->ready, &c->sched, &c->desc, &c->qpacked, &c->qcls,
-                      &c->pair_luma, &c->pair_alpha, &c->temporal, &c->last_mv, &c->last_sse,
+                      &c->pair_luma, &c->pair_alpha, &c->temporal, &c->last_mv, &c->last_sse, &c->seed_field,
                       &c->h_luma, &c->h_alpha, &c->h_tmp, &c->h_seed, &c->h_mv, &c->h_cost,
                       &c->h_disp, &c->h_iters, &c->h_npos, &c->h_cls, &c->h_ssemb, &c->h_sse,
                       &c->h_pred, &c->cl_items, &c->cl_count, &c->cl_cons};
@@ -897,7 +916,8 @@ int sme_estimate(sme_ctx* c, const sme_outputs* out)
     const int rd = c->prm.ref_distance;
     c->prm.ref_distance = 1;
     rc = run_sequence(c, (const uint8_t*)c->pair_luma.p, (const uint8_t*)c->pair_alpha.p, 2,
-                      c->have_temporal ? (const sme_mv*)c->temporal.p : nullptr, nullptr, &o);
+                      c->have_temporal ? (const sme_mv*)c->temporal.p : nullptr,
+                      c->have_seed ? (const float*)c->seed_field.p : nullptr, &o);
     c->prm.ref_distance = rd;
     if (rc) return rc;
     if (user_mv && cudaMemcpyAsync(c->last_mv.p, o.mv, g.M * sizeof(sme_mv), cudaMemcpyDeviceToDevice, c->stream))
@@ -959,6 +979,23 @@ int sme_set_temporal_field(sme_ctx* c, const sme_mv* field)
     if (cudaMemcpyAsync(c->temporal.p, field, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
         return SME_ERR_CUDA;
     c->have_temporal = true;
+    return SME_OK;
+}
+
+int sme_set_seed_field(sme_ctx* c, const float* seed)
+{
+    if (!c) return SME_ERR_ARG;
+    if (!seed) {
+        c->have_seed = false;
+        return SME_OK;
+    }
+    if (c->four_mv || c->m.K > kMaxSeededIters) return SME_ERR_ARG;
+    const size_t bytes = (size_t)c->g.M * 2 * sizeof(float);
+    int rc = ensure(c->seed_field, bytes);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(c->seed_field.p, seed, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return SME_ERR_CUDA;
+    c->have_seed = true;
     return SME_OK;
 }
 
@@ -1213,12 +1250,13 @@ struct sme_batch {
 namespace {
 
 // stage 1: the classification launch(es); stage 2: the motion search;
-// 0: both.
+// 0: both; 3 + k: the search of pair round k (sparse schedule, pair rounds).
 int batch_enqueue(sme_batch* b, cudaStream_t s, int stage = 0)
 {
     if (b->cfg.schedule == kSchedCluster) return SME_ERR_ARG;  // single sequences only
+    if (stage >= 3 && b->cfg.schedule != kSchedSparse) return SME_ERR_ARG;
     if (b->cfg.schedule == kSchedSparse) {
-        if (stage != 2 &&
+        if (stage <= 1 &&
             launch_sparse_prep(sparse_args(b->sp, (SeqDesc*)b->descs.p, b->status), nullptr, s) != cudaSuccess)
             return SME_ERR_CUDA;
         if (stage == 1) return SME_OK;
@@ -1231,7 +1269,12 @@ int batch_enqueue(sme_batch* b, cudaStream_t s, int stage = 0)
         a.fault_ticket = -1;
         a.speculate = b->cfg.speculate;
         a.timeout_ns = kDefaultTimeoutNs;
-        return launch_sparse_search(b->m, a, b->sp, b->num_sms, b->cfg.mb_ctas_per_sm, s);
+        if (stage >= 3)  // one pair round
+            return launch_sparse_search(b->m, a, b->sp, b->num_sms, b->cfg.mb_ctas_per_sm, s, stage - 3);
+        if (!b->sp.pair_keys) return launch_sparse_search(b->m, a, b->sp, b->num_sms, b->cfg.mb_ctas_per_sm, s);
+        for (int k = 0; k < b->sp.rounds; ++k)
+            if (int rc = launch_sparse_search(b->m, a, b->sp, b->num_sms, b->cfg.mb_ctas_per_sm, s, k)) return rc;
+        return SME_OK;
     }
     ClassifyBatchArgs ca{(const SeqDesc*)b->descs.p, (const int*)b->fseq.p, (const int*)b->ffrm.p, b->status};
     if (stage != 2 && launch_classify_batch(ca, b->max_mbh, b->total_frames, s) != cudaSuccess) return SME_ERR_CUDA;
@@ -1485,6 +1528,7 @@ int sme_batch_tune(sme_batch* b, int trials)
     float best = -1.0f;
     ExecCfg pick = b->cfg;
     for (const ExecCfg& e : kTuneCandidates) {
+        if (b->sp.pair_keys && e.schedule != kSchedSparse) continue;  // pair rounds: the sparse schedule only
         b->cfg = e;
         if (batch_enqueue(b, b->stream) != SME_OK || cudaStreamSynchronize(b->stream) != cudaSuccess) {
             cudaGetLastError();
@@ -1514,6 +1558,24 @@ int sme_batch_run_stage(sme_batch* b, int stage)
 {
     if (!b || (stage != 1 && stage != 2)) return SME_ERR_ARG;
     return batch_enqueue(b, b->stream, stage);
+}
+
+int sme_batch_set_pair_rounds(sme_batch* b, int on)
+{
+    if (!b || (on != 0 && on != 1)) return SME_ERR_ARG;
+    if (on == (b->sp.pair_keys > 0)) return SME_OK;
+    int rc = setup_sparse(b->sp, b->host_desc, b->stream, on != 0);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SME_ERR_CUDA;
+    batch_drop_graph(b);
+    if (on) b->cfg = ExecCfg{kSchedSparse, 0, b->cfg.schedule == kSchedSparse ? b->cfg.mb_ctas_per_sm : 2, 0, 0, 1};
+    return SME_OK;
+}
+
+int sme_batch_run_pair(sme_batch* b, int k)
+{
+    if (!b || !b->sp.pair_keys || k < 0 || k >= b->sp.rounds) return SME_ERR_ARG;
+    return batch_enqueue(b, b->stream, 3 + k);
 }
 
 int sme_batch_upload(sme_batch* b, const sme_host_io* io, int n)
@@ -1629,6 +1691,7 @@ int sme_batch_set_config(sme_batch* b, int schedule, int param, int flag)
     default:
         return SME_ERR_ARG;  // the cluster schedule runs single sequences only
     }
+    if (b->sp.pair_keys && schedule != kSchedSparse) return SME_ERR_ARG;  // pair rounds: sparse only
     batch_drop_graph(b);
     b->cfg = e;
     b->tuned_ms = 0.0f;

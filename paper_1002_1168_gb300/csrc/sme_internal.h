@@ -132,7 +132,10 @@ struct SparseArgs {
     int* first_step;           // [nseq]: first wavefront step with a non-transparent MB of each sequence
     unsigned* hist;            // [8 * (steps + 1)]: MBs per list key (one 32-byte sector each)
     unsigned* cursor;          // [8 * steps]: scatter cursor of each key
-    int steps;
+    int steps;                 // list keys (steps, or pair_keys * the largest pair count)
+    int pair_keys;             // > 0: pair rounds -- key = k * pair_keys + u + 2v (pair k's MBs contiguous)
+    unsigned* round_ticket;    // [rounds]: next entry of each pair round's search launch
+    int rounds;
     int* list;                 // global MB ids of the non-transparent MBs, by step
     SparseCounters* ctr;
     DevStatus* status;
@@ -168,6 +171,12 @@ struct MeArgs {
     const int* seq_base;      // [nseq] first global MB id of each sequence (ascending)
     int nseq;
     SparseCounters* ctr;
+    // pair rounds: the launch searches pair `round` of every sequence only:
+    // list entries [offs[8 * round * pair_keys], offs[8 * (round + 1) * pair_keys])
+    int round;                // -1: the whole list
+    int pair_keys, rounds;
+    const unsigned* offs;     // exclusive list offset of each key (one 32-byte sector each)
+    unsigned* round_ticket;   // [rounds]
 };
 
 struct CompArgs {

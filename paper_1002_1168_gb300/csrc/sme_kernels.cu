@@ -1395,6 +1395,7 @@ __global__ void __launch_bounds__(256) sparse_reset_kernel(const SparseArgs a, c
             a.ctr->ticket = 0;
         }
         for (int i = tid; i <= a.steps; i += blockDim.x) a.hist[8 * (size_t)i] = 0;
+        for (int i = tid; i < a.rounds; i += blockDim.x) a.round_ticket[i] = 0;
     }
     for (int q = blockIdx.x; q < a.nseq; q += gridDim.x) {
         if (tid == 0) a.first_step[q] = 0x7fffffff;
@@ -1540,6 +1541,7 @@ __global__ void __launch_bounds__(256) sparse_stream_kernel(const SparseArgs a)
 // instead of waiting for the work of other VOPs at smaller absolute steps.
 __device__ __forceinline__ int list_key(const SparseArgs& a, int q, int u, int v, int k)
 {
+    if (a.pair_keys) return k * a.pair_keys + u + 2 * v;  // pair rounds: A, B, C before, T a round earlier
     return u + 2 * v + k - __ldg(a.first_step + q);
 }
 
@@ -1609,12 +1611,18 @@ __global__ void __launch_bounds__(1024) sparse_scan_kernel(const SparseArgs a)
         }
         __syncthreads();
         const unsigned excl = carry + wsum[wid] + inc - x;
-        if (i < a.steps) a.cursor[8 * (size_t)i] = excl;
+        if (i < a.steps) {
+            a.hist[8 * (size_t)i] = excl;  // kept: the pair rounds' list segments
+            a.cursor[8 * (size_t)i] = excl;
+        }
         __syncthreads();
         if (tid == 1023) carry = excl + x;
         __syncthreads();
     }
-    if (tid == 0) a.ctr->total = carry;
+    if (tid == 0) {
+        a.ctr->total = carry;
+        a.hist[8 * (size_t)a.steps] = carry;
+    }
 }
 
 // Every non-transparent MB goes to the next slot of its key.
@@ -1653,16 +1661,24 @@ __global__ void __launch_bounds__(32 * kMeWarps, kMinBlocks) me_sparse_kernel(co
     __shared__ float s_rcp[512];
     fill_rcp(s_rcp);
     __syncthreads();
-    const unsigned total = ld_relaxed(&a.ctr->total);
+    // The whole list, or (pair rounds) the segment of pair `round`, whose
+    // T candidates were published by the previous round's launch.
+    unsigned begin = 0, total = ld_relaxed(&a.ctr->total);
+    unsigned* ticket = &a.ctr->ticket;
+    if (a.round >= 0) {
+        begin = __ldg(a.offs + 8 * (size_t)a.round * a.pair_keys);
+        total = __ldg(a.offs + 8 * (size_t)(a.round + 1) * a.pair_keys);
+        ticket = a.round_ticket + a.round;
+    }
     // The next ticket is taken while the current MB is searched (a warp holds
     // at most one ticket it has not started, later than its current one,
     // which keeps the progress argument above).
     unsigned t = 0;
-    if (lane == 0) t = atomicAdd(&a.ctr->ticket, 1u);
+    if (lane == 0) t = begin + atomicAdd(ticket, 1u);
     t = __shfl_sync(kFull, t, 0);
     while (t < total) {
         unsigned next = 0;
-        if (lane == 0) next = ld_relaxed(&a.status->abort) ? total : atomicAdd(&a.ctr->ticket, 1u);
+        if (lane == 0) next = ld_relaxed(&a.status->abort) ? total : begin + atomicAdd(ticket, 1u);
         const int gid = __ldg(a.list + t);
         const SeqDesc* sd = a.seqs + seq_of_gid(a.seq_base, a.nseq, gid);
         if (!me_one_mb<GlobalLinks, kVariants, true>(a, m, gid, sd, win, slog, s_rcp, L, lane, pitch)) return;

@@ -59,9 +59,11 @@ __device__ __forceinline__ unsigned pack_bf2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 // difference, the temporal candidate of the cell's MB (pixels / 16).
 // Pair q of the launch (blockIdx.y) uses frames ref_f + q and cur_f + q.
 // frames: when non-null, pair q reads frames[2q] (reference) and frames[2q + 1]
-// (current) instead of frames ref_f0 + q and cur_f0 + q of luma.
+// (current) instead of frames ref_f0 + q and cur_f0 + q of luma.  tmp_tab:
+// when non-null, pair q's temporal field is tmp_tab[q] (NULL: zeros).
 __global__ void features_kernel(const uint8_t* luma, const uint8_t* const* frames, int W, int H, int ref_f0,
-                                int cur_f0, const sme_mv* temporal, int subpel, __nv_bfloat16* out_all)
+                                int cur_f0, const sme_mv* temporal, const sme_mv* const* tmp_tab, int subpel,
+                                __nv_bfloat16* out_all)
 {
     const int Wc = W / 4, Hc = H / 4;
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,6 +88,7 @@ __global__ void features_kernel(const uint8_t* luma, const uint8_t* const* frame
     f[0] = mc / 255.0f - 0.5f;
     f[1] = mr / 255.0f - 0.5f;
     f[2] = (mc - mr) / 255.0f;
+    if (tmp_tab) temporal = tmp_tab[q];
     if (temporal) {
         const sme_mv t = temporal[(ci / 4) * (W / 16) + cj / 4];
         f[3] = (float)t.dx / (16.0f * subpel);
@@ -105,12 +108,15 @@ __global__ void features_kernel(const uint8_t* luma, const uint8_t* const* frame
 // each [N][M] (pair-major); or `rows`: a device table [n_maps][N] of pointers
 // to [M] class rows (a NULL entry is an empty plane), so the maps can stay
 // wherever another launch wrote them (e.g. a batch's own classification).
+// seed_rows: when non-null, the seeds of grid n go to seed_rows[n] ([M][2])
+// instead of the contiguous seed output.
 struct ClsMaps {
     const uint8_t* cls;
     const uint8_t* const* rows;
     int n_maps;
     long long stride;
     int N, M;
+    float* const* seed_rows;
 };
 __device__ __forceinline__ bool any_visible(const ClsMaps& c, size_t i)
 {
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(
                 v[c] = __uint_as_float(r[c]) + s_bias[c];
                 if (relu) v[c] = fmaxf(v[c], 0.0f);
             }
-            if (seeds) {
+            if (seeds || cm.seed_rows) {
                 // MB = 4 x 4 cells: this warp's 4 tile rows are one MB row of
                 // the tile; lanes (row = lane >> 3, col = lane & 7) -> MB
                 // column col >> 2.  Sum over lane bits 0, 1 (columns) and
@@ -453,8 +459,9 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(
                     const int mbw = Wc >> 2, mb = (i_cell >> 2) * mbw + (j_cell >> 2);
                     const size_t id = (size_t)n * mbw * (Hc >> 2) + mb;
                     if ((!cm.cls && !cm.rows) || any_visible(cm, id)) {
-                        seeds[2 * id] = kSeedScale * s0 / 16.0f;
-                        seeds[2 * id + 1] = kSeedScale * s1 / 16.0f;
+                        float* dst = cm.seed_rows ? cm.seed_rows[n] + 2 * mb : seeds + 2 * id;
+                        dst[0] = kSeedScale * s0 / 16.0f;
+                        dst[1] = kSeedScale * s1 / 16.0f;
                     }
                 }
                 continue;
@@ -814,7 +821,8 @@ int forward(sme_seednet* s, const __nv_bfloat16* feat, int N, int Hc, int Wc, co
         conv<32, 32>(s->act[1], w[1], b[1], nullptr, 1, N, Hc, Wc, units, s->act[2], nullptr, nullptr, none, e, st) ||
         conv<32, 32>(s->act[2], w[2], b[2], nullptr, 1, N, Hc, Wc, units, s->act[3], nullptr, nullptr, none, e, st) ||
         conv<32, 32>(s->act[3], w[3], b[3], nullptr, 1, N, Hc, Wc, units, s->act[4], nullptr, nullptr, none, e, st) ||
-        conv<32, 16>(s->act[4], w[4], b[4], nullptr, 0, N, Hc, Wc, units, nullptr, seeds ? nullptr : s->out32, seeds,
+        conv<32, 16>(s->act[4], w[4], b[4], nullptr, 0, N, Hc, Wc, units, nullptr,
+                     (seeds || cm.seed_rows) ? nullptr : s->out32, seeds,
                      cm, e, st))
         return SME_ERR_CUDA;
     return SME_OK;
@@ -960,19 +968,20 @@ int sme_seednet_features(sme_seednet* s, const uint8_t* luma, int width, int hei
         return SME_ERR_ARG;
     const int cells = (width / 4) * (height / 4);
     features_kernel<<<dim3((cells + 127) / 128, n_pairs), 128, 0, s->stream>>>(
-        luma, nullptr, width, height, ref_frame, cur_frame, temporal, subpel, reinterpret_cast<__nv_bfloat16*>(feat));
+        luma, nullptr, width, height, ref_frame, cur_frame, temporal, nullptr, subpel,
+        reinterpret_cast<__nv_bfloat16*>(feat));
     return cudaGetLastError() == cudaSuccess ? SME_OK : SME_ERR_CUDA;
 }
 
-int sme_seednet_features_table(sme_seednet* s, const uint8_t* const* frames, int n_pairs, int width, int height,
-                               int subpel, uint16_t* feat)
+int sme_seednet_features_table(sme_seednet* s, const uint8_t* const* frames, const sme_mv* const* temporal,
+                               int n_pairs, int width, int height, int subpel, uint16_t* feat)
 {
     if (!s || !frames || !feat || ((uintptr_t)feat & 15) || width % 16 || height % 16 || width <= 0 || height <= 0 ||
         n_pairs < 1 || n_pairs > 65535 || (subpel != 1 && subpel != 2))
         return SME_ERR_ARG;
     const int cells = (width / 4) * (height / 4);
     features_kernel<<<dim3((cells + 127) / 128, n_pairs), 128, 0, s->stream>>>(
-        nullptr, frames, width, height, 0, 0, nullptr, subpel, reinterpret_cast<__nv_bfloat16*>(feat));
+        nullptr, frames, width, height, 0, 0, nullptr, temporal, subpel, reinterpret_cast<__nv_bfloat16*>(feat));
     return cudaGetLastError() == cudaSuccess ? SME_OK : SME_ERR_CUDA;
 }
 
@@ -998,7 +1007,9 @@ int sme_seednet_forward(sme_seednet* s, const uint16_t* feat, int n, int width, 
     return SME_OK;
 }
 
-// The sparse forward for class maps given either way (see ClsMaps).
+// The sparse forward for class maps given either way (see ClsMaps).  With
+// contiguous seeds the MBs not evaluated get (0, 0); with seed rows they are
+// left as they are.
 static int forward_active(sme_seednet* s, const uint16_t* feat, int n, int width, int height, const ClsMaps& cm,
                           float* seeds)
 {
@@ -1007,7 +1018,7 @@ static int forward_active(sme_seednet* s, const uint16_t* feat, int n, int width
     if (cudaMemsetAsync(s->units, 0, sizeof(int), s->stream) != cudaSuccess) return SME_ERR_CUDA;
     active_tiles_kernel<<<(T + 127) / 128, 128, 0, s->stream>>>(cm, n, Wc / 4, Hc / 4, TR, TC, s->units);
     if (cudaGetLastError() != cudaSuccess ||
-        cudaMemsetAsync(seeds, 0, sizeof(float) * 2 * (size_t)M, s->stream) != cudaSuccess)
+        (!cm.seed_rows && cudaMemsetAsync(seeds, 0, sizeof(float) * 2 * (size_t)M, s->stream) != cudaSuccess))
         return SME_ERR_CUDA;
     return forward(s, reinterpret_cast<const __nv_bfloat16*>(feat), n, Hc, Wc, s->units, seeds, cm);
 }
@@ -1029,17 +1040,50 @@ int sme_seednet_forward_active(sme_seednet* s, const uint16_t* feat, int n, int 
 }
 
 int sme_seednet_forward_active_table(sme_seednet* s, const uint16_t* feat, int n, int width, int height,
-                                     const uint8_t* const* rows, int n_maps, float* seeds)
+                                     const uint8_t* const* rows, int n_maps, float* seeds, float* const* seed_rows)
 {
     int rc = check_geom(s, feat, n, width, height);
     if (rc) return rc;
-    if (!rows || !seeds || n_maps < 1) return SME_ERR_ARG;
+    if (!rows || (!seeds == !seed_rows) || n_maps < 1) return SME_ERR_ARG;
     ClsMaps cm{};
     cm.rows = rows;
+    cm.seed_rows = seed_rows;
     cm.n_maps = n_maps;
     cm.N = n;
     cm.M = (height / 16) * (width / 16);
     return forward_active(s, feat, n, width, height, cm, seeds);
+}
+
+// One temporal field per scene from its VOPs' fields (the network input is
+// shared by the VOPs of a scene): in scene q (blockIdx.y), MB m takes the
+// vector of the first VOP j whose class row marks it non-transparent
+// (fields[q][j][m]), else (0, 0).
+__global__ void temporal_composite_kernel(const sme_mv* const* fields, const uint8_t* const* classes, int n_vops,
+                                          int M, sme_mv* out)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+    if (m >= M) return;
+    sme_mv t{0, 0};
+    for (int j = 0; j < n_vops; ++j) {
+        const uint8_t* c = classes[(size_t)q * n_vops + j];
+        const sme_mv* f = fields[(size_t)q * n_vops + j];
+        if (c && f && c[m] != 0) {
+            t = f[m];
+            break;
+        }
+    }
+    out[(size_t)q * M + m] = t;
+}
+
+int sme_seednet_temporal_composite(sme_seednet* s, const sme_mv* const* fields, const uint8_t* const* classes,
+                                   int n, int n_vops, int width, int height, sme_mv* out)
+{
+    if (!s || !fields || !classes || !out || n < 1 || n > 65535 || n_vops < 1 || width <= 0 || height <= 0 ||
+        width % 16 || height % 16)
+        return SME_ERR_ARG;
+    const int M = (width / 16) * (height / 16);
+    temporal_composite_kernel<<<dim3((M + 255) / 256, n), 256, 0, s->stream>>>(fields, classes, n_vops, M, out);
+    return cudaGetLastError() == cudaSuccess ? SME_OK : SME_ERR_CUDA;
 }
 
 int sme_seednet_synchronize(sme_seednet* s)

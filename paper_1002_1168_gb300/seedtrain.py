@@ -7,10 +7,15 @@ pairs in one batched launch, and each non-transparent MB's final vector (in
 pixels) is its label.  The network is trained with the library's own forward
 and backward kernels (sme_seednet_train_step).
 
-The temporal channel of the network input is left at zero: in the one-launch
-sequence path every pair's seeds are computed before the launch, when the
-previous pair's field is not yet known (the block search still offers the
-temporal vector as its own candidate).
+The temporal channels of the network input carry the previous pair's final
+field where it is known: LearnedRounds estimates a batch pair by pair (the
+network for pair k runs after the search of pair k - 1), and the training
+samples come in both forms -- the first pair of a sequence (no previous
+field: zeros) and the second pair with the plain method's field of the first
+as input.  In the one-launch forms (LearnedBatch, sequence_seeds) every
+pair's seeds are computed before any field exists, so the channels stay zero
+there (the block search still offers the temporal vector as its own
+candidate).
 
 Evaluation compares the plain path with the learned-seeded path (seeds as a
 fifth candidate, plain search as fallback) on the same sequence: macroblocks
@@ -29,24 +34,25 @@ from . import sme, synth
 
 
 def _pair_job(job):
-    W, H, sseed, n_objects, bg = job
-    s = synth.make_sequence(W, H, 2, sseed, n_objects=n_objects, vmax=8.0, bg_step=bg, noise_sigma=2.0,
+    W, H, sseed, n_objects, bg, frames = job
+    s = synth.make_sequence(W, H, frames, sseed, n_objects=n_objects, vmax=8.0, bg_step=bg, noise_sigma=2.0,
                             blobby=True, max_rot_deg=5.0, scale_range=(0.95, 1.05), obj_frac=0.33)
     return [(s.luma, s.alpha[j]) for j in range(s.alpha.shape[0])]
 
 
-def training_pairs(n_pairs, seed, W=352, H=288, workers=1):
-    """At least n_pairs VOP frame pairs (luma [2, H, W], alpha [2, H, W]) from
-    two-frame sequences with 1-2 objects (rotation <= 5 deg, scale
-    0.95-1.05); sequence i uses seed * 100003 + i.  workers > 1 renders in a
-    spawned process pool (same result)."""
+def training_pairs(n_pairs, seed, W=352, H=288, workers=1, frames=2):
+    """At least n_pairs VOP frame pairs (luma [frames, H, W], alpha [frames,
+    H, W]) from short sequences with 1-2 objects (rotation <= 5 deg, scale
+    0.95-1.05); sequence i uses seed * 100003 + i.  frames = 3 gives each VOP
+    a second pair whose previous field is known (build_dataset).  workers > 1
+    renders in a spawned process pool (same result)."""
     rng = np.random.default_rng(seed)
     jobs, count = [], 0
     while count < n_pairs:
         n_objects = int(rng.integers(1, 3))
         bg = tuple(rng.uniform(-2, 2, 2))
-        jobs.append((W, H, seed * 100003 + len(jobs), n_objects, bg))
-        count += n_objects
+        jobs.append((W, H, seed * 100003 + len(jobs), n_objects, bg, frames))
+        count += n_objects * (frames - 1)
     if workers > 1:
         import multiprocessing as mp
         from concurrent.futures import ProcessPoolExecutor
@@ -70,22 +76,30 @@ def training_pairs(n_pairs, seed, W=352, H=288, workers=1):
 
 
 def build_dataset(pairs, net, search_range=16, subpel=2):
-    """Features, labels (pixels) and masks (non-transparent MBs) of every pair,
-    labelled by the plain method in one batched launch."""
+    """Features, labels (pixels) and masks (non-transparent MBs), labelled by
+    the plain method in one batched launch: for every VOP sequence of F
+    frames, its F - 1 pairs, pair k > 0 with the plain field of pair k - 1 as
+    the temporal input (pair 0: none)."""
     import torch
 
     lumas = [torch.from_numpy(l).cuda() for l, _ in pairs]
     alphas = [torch.from_numpy(a).cuda() for _, a in pairs]
     b = sme.Batch(lumas, alphas, search_range=search_range, subpel=subpel, want=("mb_class",))
     outs = b.run()
-    H, W = pairs[0][0].shape[1:]
-    feats = torch.empty((len(pairs), H // 4, W // 4, 16), dtype=torch.int16, device="cuda")
-    for i, l in enumerate(lumas):
-        net.features(l, 0, 1, temporal=None, subpel=subpel, out=feats[i])
-    labels = torch.stack([o["mv"][0].float() / subpel for o in outs])
-    mask = torch.stack([(o["mb_class"][0] > 0).to(torch.uint8) for o in outs])
+    F, H, W = pairs[0][0].shape
+    n = len(pairs) * (F - 1)
+    feats = torch.empty((n, H // 4, W // 4, 16), dtype=torch.int16, device="cuda")
+    labels, mask = [], []
+    i = 0
+    for l, o in zip(lumas, outs):
+        for k in range(F - 1):
+            tmp = None if k == 0 else o["mv"][k - 1].contiguous()
+            net.features(l, k, k + 1, temporal=tmp, subpel=subpel, out=feats[i])
+            labels.append(o["mv"][k].float() / subpel)
+            mask.append((o["mb_class"][k] > 0).to(torch.uint8))
+            i += 1
     b.close()
-    return feats, labels, mask
+    return feats, torch.stack(labels), torch.stack(mask)
 
 
 def train(net, feats, labels, mask, steps=600, batch=32, lr=1e-3, seed=0, log_every=0):
@@ -332,6 +346,150 @@ class LearnedBatch:
         """The whole host-to-host pass: inputs uploaded from host memory, the
         run, the outputs named in io downloaded, on the run's stream
         (io: Batch.host_io); synchronises."""
+        with self.torch.cuda.stream(self.stream):
+            self.batch.upload(io)
+            self.run(sync=False)
+            self.batch.download(io)
+        self.batch.synchronize()
+        return io
+
+    def synchronize(self):
+        self.batch.synchronize()
+
+    def config(self):
+        return self.batch.config()
+
+    def close(self):
+        self.batch.close()
+
+
+class LearnedRounds:
+    """The learned-seeded batch with the previous field as network input:
+    pair rounds of the sparse schedule.  A run is the batch's classification
+    stage, then for every pair k (in order) and every frame size: one
+    temporal-composite launch (for each scene, the final vectors of its VOPs
+    at pair k - 1, the VOP that covers an MB giving its vector), one features
+    launch over pair k of every sequence with those fields as the temporal
+    channels, one sparse forward writing the seeds of pair k straight into
+    each sequence's seed rows, and the search of pair k of every VOP.  Once
+    tuned, the whole run is one CUDA graph.  groups as for LearnedBatch."""
+
+    def __init__(self, net, groups, search_range=16, subpel=2, ref_distance=1,
+                 want=("cost", "iters", "npos", "mb_class", "sse")):
+        import torch
+
+        self.torch, self.net, self.subpel, self.rd = torch, net, subpel, ref_distance
+        rd = ref_distance
+        self.stream = torch.cuda.Stream()
+        self.graph = None
+        with torch.cuda.stream(self.stream):
+            lumas, alphas, seeds_list, owner = [], [], [], []
+            seq_seeds = []
+            for i, (luma, alist) in enumerate(groups):  # VOP order = the caller's order
+                F, H, W = luma.shape
+                sd = torch.zeros((F - rd, (W // 16) * (H // 16), 2), dtype=torch.float32, device=luma.device)
+                seq_seeds.append(sd)
+                for j, a in enumerate(alist):
+                    lumas.append(luma)
+                    alphas.append(a)
+                    seeds_list.append(sd)
+                    owner.append((i, j))
+            self.batch = sme.Batch(lumas, alphas, search_range=search_range, subpel=subpel,
+                                   ref_distance=ref_distance, want=want, seed_list=seeds_list)
+            self.batch.set_pair_rounds(True)
+            vop_of = {o: q for q, o in enumerate(owner)}
+            # size groups: every sequence of one frame size goes through one
+            # composite, features and forward launch per round
+            sizes = {}
+            for i, (luma, _) in enumerate(groups):
+                sizes.setdefault(tuple(luma.shape[1:]), []).append(i)
+            self.rounds = max(l.shape[0] for l, _ in groups) - rd
+            self.per_size = []
+            for (H, W), members in sizes.items():
+                M = (W // 16) * (H // 16)
+                n = len(members)
+                V = max(len(groups[i][1]) for i in members)
+                dev = groups[members[0]][0].device
+                if n * (H // 4) * (W // 4) > net.max_cells:
+                    raise ValueError("the network's capacity is below one pair of every sequence of this size")
+                feat = torch.empty((n, H // 4, W // 4, 16), dtype=torch.int16, device=dev)
+                comp = torch.zeros((n, M, 2), dtype=torch.int16, device=dev)
+                tabs = []
+                for k in range(self.rounds):
+                    frames, fields, classes, rows, srows, tmp = [], [], [], [[0] * n for _ in range(V)], [], []
+                    live = []
+                    for q, i in enumerate(members):
+                        luma, alist = groups[i]
+                        P = luma.shape[0] - rd
+                        FS = H * W
+                        kk = min(k, P - 1)  # a sequence with fewer pairs repeats its last (unused)
+                        live.append(k < P)
+                        frames.append((luma.data_ptr() + kk * FS, luma.data_ptr() + (kk + rd) * FS))
+                        srows.append(seq_seeds[i].data_ptr() + kk * M * 8)
+                        tmp.append(comp.data_ptr() + q * M * 4 if k > 0 else 0)
+                        fq, cq = [], []
+                        for j in range(V):
+                            if j < len(alist) and k > 0:
+                                vq = vop_of[(i, j)]
+                                fq.append(self.batch.outputs[vq]["mv"][kk - 1].data_ptr())
+                                cq.append(self.batch.class_map_ptr(vq) + (kk - 1 + rd) * M)
+                            else:
+                                fq.append(0)
+                                cq.append(0)
+                            if j < len(alist) and k < P:
+                                rows[j][q] = self.batch.class_map_ptr(vop_of[(i, j)]) + (kk + rd) * M
+                        fields.append(fq)
+                        classes.append(cq)
+                    t64 = lambda x: torch.tensor(x, dtype=torch.int64, device=dev)  # noqa: E731
+                    tabs.append({"frames": t64(frames), "fields": t64(fields), "classes": t64(classes),
+                                 "rows": t64(rows).reshape(-1), "seed_rows": t64(srows),
+                                 "tmp": t64(tmp) if k > 0 else None, "any": any(live)})
+                self.per_size.append((H, W, n, V, feat, comp, tabs))
+        self.outputs = self.batch.outputs
+        self.seeds = seeds_list
+
+    def _round(self, k):
+        for H, W, n, V, feat, comp, tabs in self.per_size:
+            t = tabs[k]
+            if not t["any"]:
+                continue
+            if k > 0:
+                self.net.temporal_composite(t["fields"], t["classes"], n, V, W, H, comp)
+            self.net.features_table(t["frames"], W, H, subpel=self.subpel, out=feat, temporal=t["tmp"])
+            self.net.forward_active_table(feat, t["rows"], V, seed_rows=t["seed_rows"])
+        self.batch.run_pair(k)
+
+    def _run_direct(self):
+        self.batch.run_stage(1)
+        for k in range(self.rounds):
+            self._round(k)
+
+    def tune(self, trials=3):
+        """Seeds once, the batch's autotuner (sparse configurations), then the
+        capture of a whole run in one graph."""
+        t = self.torch
+        with t.cuda.stream(self.stream):
+            self._run_direct()
+            self.batch.tune(trials)
+            self._run_direct()  # the seeds of the tuned configuration's fields
+            self.stream.synchronize()
+            g = t.cuda.CUDAGraph()
+            with t.cuda.graph(g, stream=self.stream):
+                self._run_direct()
+            self.graph = g
+
+    def run(self, sync=True):
+        with self.torch.cuda.stream(self.stream):
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._run_direct()
+        if sync:
+            self.batch.synchronize()
+        return self.outputs
+
+    def run_host(self, io):
+        """Upload, run, download, synchronise (io: Batch.host_io)."""
         with self.torch.cuda.stream(self.stream):
             self.batch.upload(io)
             self.run(sync=False)

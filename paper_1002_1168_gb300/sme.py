@@ -30,13 +30,14 @@ EXPORTS = [
     "sme_default_params", "sme_strerror", "sme_create", "sme_destroy", "sme_set_stream",
     "sme_synchronize", "sme_classify", "sme_classify_table", "sme_packed_words", "sme_estimate_sequence",
     "sme_estimate_sequence_host", "sme_set_reference", "sme_set_current", "sme_estimate",
-    "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field",
+    "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field", "sme_set_seed_field",
     "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
     "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_get_option", "sme_autotune",
     "sme_full_search",
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_set_config", "sme_batch_run_stage", "sme_batch_class_map", "sme_seednet_forward_active_table",
-    "sme_batch_upload", "sme_batch_download",
+    "sme_batch_upload", "sme_batch_download", "sme_batch_set_pair_rounds", "sme_batch_run_pair",
+    "sme_seednet_temporal_composite",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_features_table",
     "sme_seednet_forward",
@@ -106,6 +107,7 @@ def _lib():
             "sme_score": (i, [vp, C.POINTER(C.c_double)]),
             "sme_get_temporal_field": (i, [vp, vp]),
             "sme_set_temporal_field": (i, [vp, vp]),
+            "sme_set_seed_field": (i, [vp, vp]),
             "sme_compensate": (i, [vp, vp, vp, vp, vp, vp]),
             "sme_psnr": (C.c_double, [C.c_ulonglong, i, i]),
             "sme_eval_costs": (i, [vp, vp, vp, vp, vp, vp, i, vp, vp]),
@@ -125,10 +127,12 @@ def _lib():
                                      C.POINTER(C.c_float)]),
             "sme_batch_set_config": (i, [vp, i, i, i]),
             "sme_batch_run_stage": (i, [vp, i]),
+            "sme_batch_set_pair_rounds": (i, [vp, i]),
+            "sme_batch_run_pair": (i, [vp, i]),
             "sme_batch_upload": (i, [vp, C.POINTER(HostIO), i]),
             "sme_batch_download": (i, [vp, C.POINTER(HostIO), i]),
             "sme_batch_class_map": (i, [vp, i, C.POINTER(C.c_void_p)]),
-            "sme_seednet_forward_active_table": (i, [vp, vp, i, i, i, vp, i, vp]),
+            "sme_seednet_forward_active_table": (i, [vp, vp, i, i, i, vp, i, vp, vp]),
             "sme_batch_destroy": (i, [vp]),
             "sme_seednet_param_count": (i, []),
             "sme_seednet_create": (i, [ip, i, vp]),
@@ -136,6 +140,8 @@ def _lib():
             "sme_seednet_set_params": (i, [vp, vp]),
             "sme_seednet_get_params": (i, [vp, vp]),
             "sme_seednet_features": (i, [vp, vp, i, i, i, i, i, vp, i, vp]),
+            "sme_seednet_features_table": (i, [vp, vp, vp, i, i, i, i, vp]),
+            "sme_seednet_temporal_composite": (i, [vp, vp, vp, i, i, i, i, vp]),
             "sme_seednet_forward": (i, [vp, vp, i, i, i, vp, vp]),
             "sme_seednet_forward_active": (i, [vp, vp, i, i, i, vp, i, C.c_longlong, vp]),
             "sme_seednet_set_stream": (i, [vp, vp]),
@@ -352,6 +358,10 @@ class Estimator:
     def set_temporal_field(self, field):
         _check(_lib().sme_set_temporal_field(self._bind(), _ptr(field)), "sme_set_temporal_field")
 
+    def set_seed_field(self, seed):
+        """Seeds [M, 2] FP32 pixels (CUDA) for the following estimates; None clears."""
+        _check(_lib().sme_set_seed_field(self._bind(), _ptr(seed)), "sme_set_seed_field")
+
     def set_option(self, option, value):
         _check(_lib().sme_set_option(self._h, int(option), int(value)), "sme_set_option")
 
@@ -491,6 +501,14 @@ class Batch:
         self.synchronize()
         return io
 
+    def set_pair_rounds(self, on=True):
+        """Pair rounds of the sparse schedule (sme_batch_set_pair_rounds)."""
+        _check(_lib().sme_batch_set_pair_rounds(self._h, int(bool(on))), "sme_batch_set_pair_rounds")
+
+    def run_pair(self, k):
+        """Enqueue the search of pair k of every sequence (pair rounds)."""
+        _check(_lib().sme_batch_run_pair(self._h, int(k)), "sme_batch_run_pair")
+
     def run_stage(self, stage):
         """Enqueue stage 1 (classification) or 2 (search) of one run."""
         _check(_lib().sme_batch_run_stage(self._h, int(stage)), "sme_batch_run_stage")
@@ -565,17 +583,26 @@ class SeedNet:
                                            _ptr(temporal), int(subpel), _ptr(out)), "sme_seednet_features")
         return out
 
-    def features_table(self, frames, width, height, subpel=2, out=None):
+    def features_table(self, frames, width, height, subpel=2, out=None, temporal=None):
         """Input grids of the pairs whose (reference, current) luma frame
         addresses are in frames (int64 CUDA tensor [n, 2]), in one launch:
-        [n, H/4, W/4, 16]."""
+        [n, H/4, W/4, 16].  temporal: None or an int64 CUDA tensor [n] of
+        temporal-field addresses (0: zeros)."""
         t = self.torch
         n = frames.shape[0]
         assert frames.is_cuda and frames.dtype == t.int64 and frames.is_contiguous() and frames.shape[1] == 2
         if out is None:
             out = t.empty((n, height // 4, width // 4, 16), dtype=t.int16, device=frames.device)
-        _check(_lib().sme_seednet_features_table(self._bind(), _ptr(frames), n, width, height, int(subpel),
-                                                 _ptr(out)), "sme_seednet_features_table")
+        _check(_lib().sme_seednet_features_table(self._bind(), _ptr(frames), _ptr(temporal), n, width, height,
+                                                 int(subpel), _ptr(out)), "sme_seednet_features_table")
+        return out
+
+    def temporal_composite(self, fields, classes, n, n_vops, width, height, out):
+        """One temporal field per scene for n scenes (sme_seednet_temporal_composite):
+        fields, classes int64 CUDA tensors [n, n_vops] of addresses; out [n, M, 2]."""
+        _check(_lib().sme_seednet_temporal_composite(self._bind(), _ptr(fields), _ptr(classes), int(n),
+                                                     int(n_vops), int(width), int(height), _ptr(out)),
+               "sme_seednet_temporal_composite")
         return out
 
     def forward(self, feat, want_cells=False):
@@ -588,15 +615,19 @@ class SeedNet:
                "sme_seednet_forward")
         return (seeds, cells) if want_cells else seeds
 
-    def forward_active_table(self, feat, rows, n_maps, out=None):
+    def forward_active_table(self, feat, rows, n_maps, out=None, seed_rows=None):
         """forward_active with the class maps as a device table [n_maps, n]
-        (int64 CUDA tensor) of row addresses; 0 = an empty plane."""
+        (int64 CUDA tensor) of row addresses; 0 = an empty plane.  With
+        seed_rows (int64 CUDA tensor [n] of [M, 2] row addresses) the seeds
+        go there instead of `out`."""
         n, Hc, Wc, _ = feat.shape
         t = self.torch
         M = (Hc // 4) * (Wc // 4)
-        out = out if out is not None else t.empty((n, M, 2), dtype=t.float32, device=feat.device)
+        if seed_rows is None and out is None:
+            out = t.empty((n, M, 2), dtype=t.float32, device=feat.device)
         _check(_lib().sme_seednet_forward_active_table(self._bind(), _ptr(feat), n, 4 * Wc, 4 * Hc, _ptr(rows),
-                                                        int(n_maps), _ptr(out)), "sme_seednet_forward_active_table")
+                                                        int(n_maps), _ptr(out), _ptr(seed_rows)),
+               "sme_seednet_forward_active_table")
         return out
 
     def forward_active(self, feat, mb_class, out=None):

@@ -198,3 +198,35 @@ def test_batch_host_upload_run_download(sme, pinned):
     with pytest.raises(sme.SmeError):
         b.download(bad)
     b.close()
+
+
+def test_batch_pair_rounds_match_oracle(sme):
+    """Pair rounds: the whole run, and stage 1 followed by the rounds one by
+    one, give the oracle's results; switching back gives them too; other
+    schedules are refused while rounds are on."""
+    seqs = _batch_inputs()
+    lumas = [torch.from_numpy(l).cuda() for l, _ in seqs]
+    alphas = [torch.from_numpy(a).cuda() for _, a in seqs]
+    b = sme.Batch(lumas, alphas, search_range=16, subpel=2)
+    b.set_pair_rounds(True)
+    assert b.config()["schedule"] == "sparse"
+    _check_all(b.run(), seqs)
+    for o in b.outputs:
+        for v in o.values():
+            v.zero_()
+    b.run_stage(1)
+    rounds = max(l.shape[0] for l, _ in seqs) - 1
+    for k in range(rounds):
+        b.run_pair(k)
+    b.synchronize()
+    _check_all(b.outputs, seqs)
+    with pytest.raises(sme.SmeError):
+        b.run_pair(rounds)
+    with pytest.raises(sme.SmeError):
+        b.set_config("mb")
+    b.tune(trials=1)
+    assert b.config()["schedule"] == "sparse"
+    _check_all(b.run(), seqs)
+    b.set_pair_rounds(False)
+    _check_all(b.run(), seqs)
+    b.close()

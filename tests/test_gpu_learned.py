@@ -91,3 +91,86 @@ def test_trained_network_gain(lib):
             assert np.all(r["cost"][k].view(np.uint32)[op] >= es[op])  # ES is the optimum over V
             gaps[name].append(float((r["cost"][k].view(np.uint32)[op].astype(np.int64) - es[op]).mean()))
     print("mean SAD above ES", gaps)
+
+
+def test_learned_rounds_match_oracle(lib):
+    """Pair rounds with the previous field as network input (LearnedRounds):
+    every VOP's field equals the oracle's given the same seeds; the seeds of
+    the first pair equal those of the one-launch form (no previous field
+    there), later pairs' seeds differ (the temporal channels are in use)."""
+    sme, seedtrain = lib
+    seqs = [synth.make_sequence(176, 144, 4, 41, n_objects=2, vmax=6.0),
+            synth.make_sequence(352, 288, 4, 42, n_objects=1, vmax=8.0),
+            synth.make_sequence(176, 144, 3, 43, n_objects=1, vmax=4.0)]
+    params = SN.init_params(4)
+    params = [(w * (30.0 if li == 4 else 1.0), b) for li, (w, b) in enumerate(params)]
+    net = sme.SeedNet(max_cells=3 * 3 * 88 * 72)
+    net.set_params(sme.pack_params(params))
+    groups = []
+    for sq in seqs:
+        lt = torch.from_numpy(sq.luma).cuda()
+        groups.append((lt, [torch.from_numpy(sq.alpha[j]).cuda() for j in range(sq.alpha.shape[0])]))
+    lr = seedtrain.LearnedRounds(net, groups, search_range=16, subpel=2)
+    lr.tune(trials=1)
+    for _ in range(2):
+        outs = lr.run()
+    lb = seedtrain.LearnedBatch(net, groups, search_range=16, subpel=2)
+    lb.run()
+    k = 0
+    later_differ = False
+    for (lt, vops), sq in zip(groups, seqs):
+        seeds = lr.seeds[k].cpu().numpy()
+        one = lb.seeds[k].cpu().numpy()
+        vis = np.zeros(seeds.shape[:2], bool)
+        for j in range(len(vops)):
+            vis |= outs[k + j]["mb_class"].cpu().numpy() > 0
+        assert np.array_equal(seeds[0][vis[0]], one[0][vis[0]])
+        later_differ |= bool(np.any(seeds[1:][vis[1:]] != one[1:][vis[1:]]))
+        for j in range(len(vops)):
+            o = O.estimate_sequence(O.OracleParams(sq.width, sq.height, 16, 2), sq.luma, sq.alpha[j], seed=seeds)
+            g = outs[k + j]
+            assert np.array_equal(g["mv"].cpu().numpy(), o["mv"])
+            assert np.array_equal(g["cost"].cpu().numpy().view(np.uint32), o["cost"])
+            assert np.array_equal(g["iters"].cpu().numpy(), o["iters"])
+            assert np.array_equal(g["sse"].cpu().numpy().view(np.uint64), o["sse"])
+        k += len(vops)
+    assert later_differ
+    lr.close()
+    lb.close()
+    net.close()
+
+
+def test_temporal_composite_and_features_table(lib):
+    """The composite temporal field of a scene takes, per MB, the first VOP
+    that covers it; the features of a pair table with temporal fields equal
+    the single-pair features with that field."""
+    sme, _ = lib
+    W, H = 176, 144
+    M = (W // 16) * (H // 16)
+    rng = np.random.default_rng(3)
+    f = [torch.from_numpy(rng.integers(-30, 31, (M, 2)).astype(np.int16)).cuda() for _ in range(3)]
+    c = [torch.from_numpy((rng.random(M) < 0.3).astype(np.uint8)).cuda() for _ in range(3)]
+    want = np.zeros((M, 2), np.int16)
+    done = np.zeros(M, bool)
+    for j in range(3):
+        take = (c[j].cpu().numpy() != 0) & ~done
+        want[take] = f[j].cpu().numpy()[take]
+        done |= take
+    net = sme.SeedNet(max_cells=2 * (W // 4) * (H // 4))
+    fields = torch.tensor([[x.data_ptr() for x in f], [f[0].data_ptr(), 0, 0]], dtype=torch.int64).cuda()
+    classes = torch.tensor([[x.data_ptr() for x in c], [c[0].data_ptr(), 0, 0]], dtype=torch.int64).cuda()
+    out = torch.empty((2, M, 2), dtype=torch.int16, device="cuda")
+    net.temporal_composite(fields, classes, 2, 3, W, H, out)
+    assert np.array_equal(out[0].cpu().numpy(), want)
+    w1 = np.where((c[0].cpu().numpy() != 0)[:, None], f[0].cpu().numpy(), 0)
+    assert np.array_equal(out[1].cpu().numpy(), w1)
+    seq = synth.make_sequence(W, H, 3, 44)
+    luma = torch.from_numpy(seq.luma).cuda()
+    FS = W * H
+    frames = torch.tensor([[luma.data_ptr(), luma.data_ptr() + FS], [luma.data_ptr() + FS, luma.data_ptr() + 2 * FS]],
+                          dtype=torch.int64).cuda()
+    tmp = torch.tensor([0, out[0].data_ptr()], dtype=torch.int64).cuda()
+    got = net.features_table(frames, W, H, subpel=2, temporal=tmp).cpu()
+    assert torch.equal(got[0], net.features(luma, 0, 1, subpel=2).cpu())
+    assert torch.equal(got[1], net.features(luma, 1, 2, temporal=out[0].contiguous(), subpel=2).cpu())
+    net.close()

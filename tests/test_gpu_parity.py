@@ -296,6 +296,46 @@ def test_pair_interface_matches_sequence(sme):
     est.close()
 
 
+@pytest.mark.parametrize("schedule", ["mb", "sparse"])
+def test_pair_interface_with_seed_field(sme, schedule):
+    """Seeds through the pair interface (sme_set_seed_field): each pair
+    equals the oracle's pair estimate with the previous field as T and the
+    same seeds; clearing the seeds gives the unseeded result back."""
+    seq = synth.make_sequence(176, 144, 4, seed=22, vmax=5.0, obj_frac=0.4)
+    luma, alpha = cuda(seq.luma), cuda(seq.alpha[0])
+    p = O.OracleParams(176, 144, 16, 2)
+    est = sme.Estimator(176, 144, search_range=16, subpel=2)
+    set_schedule(sme, est, schedule)
+    rng = np.random.default_rng(5)
+    est.set_reference(luma[0], alpha[0])
+    prev = None
+    for k in range(3):
+        seed = rng.normal(0, 4, (p.mbs, 2)).astype(np.float32)
+        est.set_seed_field(cuda(seed))
+        est.set_current(luma[k + 1], alpha[k + 1])
+        r = est.estimate(want=("cost", "iters", "npos", "sse"))
+        o = O.estimate_pair(p, seq.luma[k], seq.luma[k + 1], seq.alpha[0][k], seq.alpha[0][k + 1],
+                            temporal=prev, seed=seed)
+        assert np.array_equal(r["mv"][0].cpu().numpy(), o["mv"])
+        assert np.array_equal(r["cost"][0].cpu().numpy().view(np.uint32), o["cost"])
+        assert np.array_equal(r["iters"][0].cpu().numpy(), o["iters"])
+        assert np.array_equal(r["npos"][0].cpu().numpy(), o["npos"])
+        prev = o["mv"]
+        est.advance()
+    est.set_seed_field(None)
+    est.set_current(luma[1], alpha[1])
+    est.set_temporal_field(None)
+    est.set_reference(luma[0], alpha[0])
+    r = est.estimate(want=("cost",))
+    o = O.estimate_pair(p, seq.luma[0], seq.luma[1], seq.alpha[0][0], seq.alpha[0][1])
+    assert np.array_equal(r["mv"][0].cpu().numpy(), o["mv"])
+    est.close()
+    est = sme.Estimator(176, 144, search_range=16, subpel=2, max_iters=9)
+    with pytest.raises(sme.SmeError):
+        est.set_seed_field(cuda(np.zeros((p.mbs, 2), np.float32)))
+    est.close()
+
+
 @pytest.mark.parametrize("h", [1, 2])
 def test_compensate_given_field(sme, h):
     W, H = 128, 96

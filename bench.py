@@ -1197,6 +1197,8 @@ def run_ours(args):
     if not args.no_learned:
         net, train_info = train_seednet(sme, torch, args)
     head = measure_headline(sme, torch, args, net, dist, rank)
+    if args.headline_only:
+        args.no_cif = args.no_batch = args.no_hd = args.no_paper = True
     cif = None if args.no_cif else measure_cif(sme, torch, args, rank, dist, net, train_info)
     batched = None if args.no_batch else measure_batch(sme, torch, args, rank, dist, net)
     hd = None if (args.no_hd or net is None) else measure_hd(sme, torch, args, net)
@@ -1283,6 +1285,7 @@ def main():
     ap.add_argument("--no-paper", action="store_true", help="skip the paper-setting QCIF measurement")
     ap.add_argument("--no-e2e", action="store_true", help="skip the headline's host-buffer (end-to-end) runs")
     ap.add_argument("--no-rounds", action="store_true", help="skip the pair-round learned form at the headline")
+    ap.add_argument("--headline-only", action="store_true", help="only the headline measurement (profiling)")
     ap.add_argument("--hd-frames", type=int, default=300, help="frames of the 1920x1088 learned evaluation")
     ap.add_argument("--learn-pairs", type=int, default=2000, help="CIF VOP pairs the seed network is trained on")
     ap.add_argument("--learn-steps", type=int, default=800, help="Adam steps (32 pairs each)")

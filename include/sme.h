@@ -257,10 +257,11 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     the layout of the estimate outputs: mv, cost, iters, npos become
  *     [P][M][4] and disp [P][M][4][2] (block-major inside each MB);
  *     temporal_in becomes [M][4]; mb_class, sse_mb, sse, pred keep theirs.
- *     Runs on the pair schedule with every MB staged (whatever
- *     SME_OPT_SCHEDULE / SME_OPT_PAIR_DIRECT say); seeds and
+ *     Runs on the per-MB schedule or the pair schedule with every MB staged
+ *     (whatever SME_OPT_PAIR_DIRECT says); seeds and
  *     SME_OPT_BOUNDARY_T_TEXTURE are rejected (SME_ERR_ARG);
- *     sme_estimate_sequence* only.  0 (default) = one vector per MB.
+ *     sme_estimate_sequence* (batches: sme_batch_set_option).  0 (default)
+ *     = one vector per MB.
  *   SME_OPT_BOUNDARY_T_TEXTURE: 1 = Sec. 3.1's prose for boundary MBs: the
  *     spatial candidates (and a seed) are judged by shape, the temporal one
  *     by texture -- the first strict minimum of the others by alpha
@@ -381,6 +382,12 @@ int sme_batch_class_map(sme_batch* b, int seq, const uint8_t** mb_class);
  * other schedules are then rejected by sme_batch_set_config. */
 int sme_batch_set_pair_rounds(sme_batch* b, int on);
 int sme_batch_run_pair(sme_batch* b, int k);
+/* Options of a batch: SME_OPT_FOUR_MV 1 = four vectors per MB for every
+ * sequence (Sec. 3.2, as for a context: the outputs given at creation must
+ * have the four-vector layout [P][M][4], temporal_in [M][4]); the batch then
+ * runs the per-MB schedule or the staged per-pair one (tuned between them);
+ * SME_ERR_ARG with seeds, pair rounds, another option or value. */
+int sme_batch_set_option(sme_batch* b, int option, int value);
 /* Host-memory inputs and outputs of a batch.  sme_batch_upload copies io[i]
  * (HOST luma and alpha, [n_frames][H][W] of sequence i; n = the batch's
  * sequence count) into the device buffers the batch was created with, on the

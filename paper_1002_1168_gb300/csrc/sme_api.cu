@@ -1234,6 +1234,7 @@ struct sme_batch {
     DevStatus* status = nullptr;
     DevBuf descs, packed, cls, ready, sched, sched_seq, unit_seq, unit_pair, fseq, ffrm, maps;
     SparseScratch sp;
+    int four_mv = 0;              // four vectors per MB (Sec. 3.2): per-MB or staged per-pair schedule
     std::vector<size_t> cls_off;  // byte offset of each sequence's class map [F][M] in cls
     std::vector<SeqDesc> host_desc;  // the descriptors (device addresses, sizes) of every sequence
     // host-buffer uploads: copies spread over several streams (copy engines),
@@ -1294,25 +1295,32 @@ int batch_enqueue(sme_batch* b, cudaStream_t s, int stage = 0)
     a.total = (int)b->total_mbs;
     a.fault_ticket = -1;
     a.speculate = b->cfg.speculate;
-    a.pair_direct = b->cfg.pair_direct;
+    a.pair_direct = b->four_mv ? 0 : b->cfg.pair_direct;
+    a.four_mv = b->four_mv;
     a.timeout_ns = kDefaultTimeoutNs;
+    if (b->four_mv) {  // three ready words per MB (blocks 0, 1, 2)
+        a.ready_a = a.ready + b->total_mbs;
+        a.ready_bc = a.ready + 2 * b->total_mbs;
+    }
     if (b->cfg.schedule == kSchedPair) {
         int nw = b->cfg.pair_warps > 0 ? b->cfg.pair_warps : kPairWarpsMax;
         if (a.pair_direct) nw = std::min(nw, 8);  // the direct instantiation's bound
-        while (nw > 1 && me_pair_smem_bytes(b->m.S, nw, b->mbw_max) > (size_t)b->smem_optin) --nw;
+        while (nw > 1 && me_pair_smem_bytes(b->m.S, nw, b->mbw_max, b->four_mv != 0) > (size_t)b->smem_optin) --nw;
         int per_sm = 0;
-        if (me_pair_occupancy(b->m.S, nw, b->mbw_max, a.pair_direct != 0, false, &per_sm) != cudaSuccess || per_sm < 1)
+        if (me_pair_occupancy(b->m.S, nw, b->mbw_max, a.pair_direct != 0, b->four_mv != 0, &per_sm) != cudaSuccess ||
+            per_sm < 1)
             return SME_ERR_CUDA;
         const int grid = std::max(1, std::min(b->num_sms * per_sm, b->total_units));
         MapSet unused;
         memset(&unused, 0, sizeof(unused));
         return cuda_status(launch_me_pair(b->m, a, &unused, nw, grid, s));
     }
-    const int per_sm =
-        b->cfg.mb_ctas_per_sm > 0 ? std::min(b->cfg.mb_ctas_per_sm, b->me_blocks_per_sm) : b->me_blocks_per_sm;
+    int resident = b->me_blocks_per_sm;
+    if (b->four_mv && (me4_occupancy(b->m.S, &resident) != cudaSuccess || resident < 1)) return SME_ERR_CUDA;
+    const int per_sm = b->cfg.mb_ctas_per_sm > 0 ? std::min(b->cfg.mb_ctas_per_sm, resident) : resident;
     const long long want = (b->total_mbs + kMeWarps - 1) / kMeWarps;
     const int grid = (int)std::max(1LL, std::min<long long>((long long)b->num_sms * per_sm, want));
-    return cuda_status(launch_me(b->m, a, grid, s));
+    return cuda_status(b->four_mv ? launch_me4(b->m, a, grid, s) : launch_me(b->m, a, grid, s));
 }
 
 void batch_drop_graph(sme_batch* b)
@@ -1529,6 +1537,8 @@ int sme_batch_tune(sme_batch* b, int trials)
     ExecCfg pick = b->cfg;
     for (const ExecCfg& e : kTuneCandidates) {
         if (b->sp.pair_keys && e.schedule != kSchedSparse) continue;  // pair rounds: the sparse schedule only
+        // four vectors per MB: the per-MB schedule and the staged per-pair one
+        if (b->four_mv && (e.schedule == kSchedSparse || (e.schedule == kSchedPair && e.pair_direct))) continue;
         b->cfg = e;
         if (batch_enqueue(b, b->stream) != SME_OK || cudaStreamSynchronize(b->stream) != cudaSuccess) {
             cudaGetLastError();
@@ -1560,9 +1570,34 @@ int sme_batch_run_stage(sme_batch* b, int stage)
     return batch_enqueue(b, b->stream, stage);
 }
 
+int sme_batch_set_option(sme_batch* b, int option, int value)
+{
+    if (!b || option != SME_OPT_FOUR_MV || (value != 0 && value != 1)) return SME_ERR_ARG;
+    if (value == b->four_mv) return SME_OK;
+    if (value) {
+        if (b->sp.pair_keys) return SME_ERR_ARG;
+        for (const SeqDesc& d : b->host_desc)
+            if (d.seed) return SME_ERR_ARG;  // as in sme_estimate_sequence: no seeds with four vectors
+        // the per-MB schedule publishes three words per MB in this mode
+        DevBuf bigger;
+        if (int rc = ensure(bigger, 3 * (size_t)b->total_mbs * sizeof(unsigned long long), true, b->stream)) return rc;
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SME_ERR_CUDA;
+        release(b->ready);
+        b->ready = bigger;
+        b->cfg = ExecCfg{kSchedMB, 0, 0, 1, 0, 1};
+    } else if (b->cfg.schedule == kSchedPair) {
+        b->cfg.pair_direct = 1;
+    }
+    batch_drop_graph(b);
+    b->tuned_ms = 0.0f;
+    b->four_mv = value;
+    return SME_OK;
+}
+
 int sme_batch_set_pair_rounds(sme_batch* b, int on)
 {
     if (!b || (on != 0 && on != 1)) return SME_ERR_ARG;
+    if (on && b->four_mv) return SME_ERR_ARG;
     if (on == (b->sp.pair_keys > 0)) return SME_OK;
     int rc = setup_sparse(b->sp, b->host_desc, b->stream, on != 0);
     if (rc) return rc;
@@ -1692,6 +1727,7 @@ int sme_batch_set_config(sme_batch* b, int schedule, int param, int flag)
         return SME_ERR_ARG;  // the cluster schedule runs single sequences only
     }
     if (b->sp.pair_keys && schedule != kSchedSparse) return SME_ERR_ARG;  // pair rounds: sparse only
+    if (b->four_mv && schedule == kSchedSparse) return SME_ERR_ARG;
     batch_drop_graph(b);
     b->cfg = e;
     b->tuned_ms = 0.0f;

@@ -8,10 +8,12 @@
 // One CTA per MB.  The reference window every vector of V can reach is
 // staged in shared memory, at half-pel as the four MPEG-4 planes (integer,
 // horizontal, vertical and diagonal half samples, rounding control 0), each
-// row padded to whole 32-bit words; the current block sits in shared memory
-// too.  Each thread takes whole positions: per block row it reads 5 aligned
-// words of the plane, shifts them into the 4 words under the block and adds
-// __vsadu4 against the current row -- 16 x 4 packed operations per position.
+// row padded to whole 32-bit words, the planes 16 banks apart modulo 32 (the
+// lanes of a warp read two planes at once: odd and even dx); each thread
+// keeps the current block in registers.  Each thread takes whole positions:
+// per block row it reads 5 aligned words of the plane once, shifts them into
+// the 4 words under the block and adds __vsadu4 against the current row --
+// 16 x 4 packed operations per position.
 // The CTA's minimum is taken over (SAD << 32 | raster index), so ties go to
 // the first position in raster order exactly as in the definition.
 #include <cuda_runtime.h>
@@ -28,12 +30,11 @@ struct EsGeom {
     int W, H, S, h, rd, M, MBW;
 };
 
-__device__ __forceinline__ unsigned es_row_word(const uint32_t* row, int byte_off, int k)
+// Words per plane: wh rows of pw words, rounded up to 16 modulo 32 words.
+__host__ __device__ __forceinline__ int es_plane_words(int wh, int pw)
 {
-    // 4 bytes starting at byte byte_off + 4k of a word-aligned row
-    const int b = byte_off + 4 * k, w = b >> 2, sh = (b & 3) * 8;
-    const unsigned lo = row[w], hi = row[w + 1];
-    return sh ? __funnelshift_r(lo, hi, sh) : lo;
+    const int n = wh * pw;
+    return n + ((16 - n % 32) + 32) % 32;
 }
 
 __global__ void __launch_bounds__(kEsThreads) es_kernel(const uint8_t* __restrict__ luma, EsGeom g, sme_mv* mv,
@@ -57,9 +58,9 @@ __global__ void __launch_bounds__(kEsThreads) es_kernel(const uint8_t* __restric
     const int wx0 = X0 + qlx, wy0 = Y0 + qly;
     const int ww = 16 + (hix + h - 1) / h - qlx, wh = 16 + (hiy + h - 1) / h - qly;
     const int pw = (ww + 3) / 4 + 2;  // words per plane row (+1 for unaligned reads, +1 slack)
-    const int planes = h * h;
+    const int planes = h * h, pstride = es_plane_words(wh, pw);
     uint32_t* cur_s = es_smem;                 // 16 rows x 4 words
-    uint32_t* win = es_smem + 64;              // planes x wh x pw words
+    uint32_t* win = es_smem + 64;              // planes x pstride words (rows of pw words)
     const int tid = threadIdx.x;
     // current block
     if (tid < 64) {
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(kEsThreads) es_kernel(const uint8_t* __restric
     uint8_t* winb = reinterpret_cast<uint8_t*>(win);
     for (int i = tid; i < planes * wh * pw * 4; i += blockDim.x) {
         const int p = i / (wh * pw * 4), rem = i - p * wh * pw * 4, r = rem / (pw * 4), c = rem - r * (pw * 4);
+        uint8_t* dst = winb + (size_t)p * pstride * 4 + rem;
         const int fy = p >> 1, fx = p & 1;
         int val = 0;
         const int x = wx0 + c, y = wy0 + r;
@@ -81,9 +83,12 @@ __global__ void __launch_bounds__(kEsThreads) es_kernel(const uint8_t* __restric
             else if (!fx && fy) val = (a + q[g.W] + 1) >> 1;
             else val = (a + q[1] + q[g.W] + q[g.W + 1] + 2) >> 2;
         }
-        winb[i] = (uint8_t)val;
+        *dst = (uint8_t)val;
     }
     __syncthreads();
+    uint32_t cw[64];  // the current block, row-major words
+#pragma unroll
+    for (int i = 0; i < 64; ++i) cw[i] = cur_s[i];
 
     const int nx = hix - lox + 1, n = nx * (hiy - loy + 1);
     unsigned long long best = ~0ull;
@@ -93,13 +98,17 @@ __global__ void __launch_bounds__(kEsThreads) es_kernel(const uint8_t* __restric
         const int fx = h == 2 ? (dx & 1) : 0, fy = h == 2 ? (dy & 1) : 0;
         const int qx = (dx - fx) / h, qy = (dy - fy) / h;
         const int c0 = X0 + qx - wx0, r0 = Y0 + qy - wy0;
-        const uint32_t* plane = win + (size_t)(fy * 2 + fx) * wh * pw;
+        const uint32_t* plane = win + (size_t)(fy * 2 + fx) * pstride;
+        const int w0 = c0 >> 2, sh = (c0 & 3) * 8;
         unsigned s = 0;
-#pragma unroll 4
-        for (int r = 0; r < 16; ++r) {
-            const uint32_t* row = plane + (size_t)(r0 + r) * pw;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) s = __vsadu4(es_row_word(row, c0, k), cur_s[4 * r + k]) + s;
+        for (int r = 0; r < 16; ++r) {
+            const uint32_t* row = plane + (size_t)(r0 + r) * pw + w0;
+            const unsigned a0 = row[0], a1 = row[1], a2 = row[2], a3 = row[3], a4 = row[4];
+            s = __vsadu4(__funnelshift_r(a0, a1, sh), cw[4 * r]) + s;
+            s = __vsadu4(__funnelshift_r(a1, a2, sh), cw[4 * r + 1]) + s;
+            s = __vsadu4(__funnelshift_r(a2, a3, sh), cw[4 * r + 2]) + s;
+            s = __vsadu4(__funnelshift_r(a3, a4, sh), cw[4 * r + 3]) + s;
         }
         const unsigned long long key = ((unsigned long long)s << 32) | (unsigned)idx;
         best = key < best ? key : best;
@@ -127,7 +136,7 @@ __global__ void __launch_bounds__(kEsThreads) es_kernel(const uint8_t* __restric
 size_t es_smem_bytes(int S, int h)
 {
     const int ww = 16 + 2 * S, pw = (ww + 3) / 4 + 2;  // the widest window: |d| <= S px both ways
-    return (size_t)(64 + h * h * ww * pw) * 4;
+    return (size_t)(64 + h * h * es_plane_words(ww, pw)) * 4;
 }
 
 cudaError_t launch_es(const uint8_t* luma, int W, int H, int S, int h, int rd, int pairs, sme_mv* mv, uint32_t* sad,

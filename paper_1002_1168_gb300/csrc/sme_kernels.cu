@@ -322,6 +322,27 @@ __device__ __forceinline__ P8 avg4p(const P8& a, const P8& b, const P8& c, const
     return r;
 }
 
+// ref8 without branches on the half-sample parity: every combination is
+// computed and the right one selected, so that several evaluations can
+// interleave.  The second row is the next one only when it is used (dy odd),
+// so every read stays inside the window as in ref8.
+__device__ __forceinline__ P8 ref8_nb(const uint8_t* win, int pitch, int lx, int ly, int dx, int dy, int h)
+{
+    if (h == 1) return ref8(win, pitch, lx, ly, dx, dy, 1);
+    const int fx = dx & 1, fy = dy & 1;
+    const int pos = (ly + (dy >> 1)) * pitch + lx + (dx >> 1);
+    unsigned w[4], v[4];
+    int off, o2;
+    row16(win, pos, w, off);
+    row16(win, fy ? pos + pitch : pos, v, o2);
+    const P8 a = extract8(w, off), b = extract8(w, off + 1), c = extract8(v, off), d = extract8(v, off + 1);
+    const P8 hz = avg2p(a, b), vt = avg2p(a, c), dg = avg4p(a, b, c, d);
+    P8 r;
+    r.lo = fx ? (fy ? dg.lo : hz.lo) : (fy ? vt.lo : a.lo);
+    r.hi = fx ? (fy ? dg.hi : hz.hi) : (fy ? vt.hi : a.hi);
+    return r;
+}
+
 // Half-sample positions d-1, d, d+1 along one axis, for the parity P of d:
 // position i reads integer sample (base) and, when frac, averages it with
 // the next one.  Even d: (-1,frac) (0) (0,frac); odd d: (0) (0,frac) (1).
@@ -1210,7 +1231,50 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
     const int lx = x0 - wx0, ly = y - wy0;
     bool failed = false;
     unsigned long long t_start = 0;
-    for (unsigned it = 0;; ++it) {
+    if constexpr (kSparse) {
+        // Throughput form: the producers are mostly done already, so wait for
+        // all of them, then cost every candidate in one branch-free block
+        // (equal positions give equal costs, so nothing needs deduplicating).
+        for (unsigned it = 0; have != all; ++it) {
+            const unsigned long long w = (lane < 4 && !res_l) ? L.poll(dep, lane) : 0ull;
+            if (lane < 4 && !res_l && L.arrived(w)) {
+                const int kk = (int)(unsigned)w;
+                key = pack_mv(clampi(mv_x(kk), V.lox, V.hix), clampi(mv_y(kk), V.loy, V.hiy));
+                res_l = true;
+            }
+            have = __ballot_sync(kFull, lane < nc && res_l) & all;
+            if ((it & 15u) == 15u && have != all) {
+                int give_up = 0;
+                if (lane == 0) {
+                    const unsigned long long now = globaltimer();
+                    if (t_start == 0) t_start = now;
+                    give_up = ld_relaxed(&a.status->abort) || (long long)(now - t_start) > a.timeout_ns ||
+                              it > (1u << 24);
+                }
+                if (__shfl_sync(kFull, give_up, 0)) {
+                    if (lane == 0 && !ld_relaxed(&a.status->abort)) raise_error(a.status, SME_ERR_TIMEOUT, true);
+                    return false;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) ckey[c] = __shfl_sync(kFull, key, c);
+        if (cls == SME_BOUNDARY) {
+            shape_costs(pcur, pref, sd->Wp, X0, Y0, ckey, nc, h, lane, ccost);
+        } else {
+            unsigned part[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                cs8[c] = c < nc ? ref8_nb(win, pitch, lx, ly, mv_x(ckey[c]), mv_y(ckey[c]), h) : c8;
+                part[c] = sad8(cs8[c], c8);
+            }
+            warp_sum2(part[0], part[1], ccost[0], ccost[1]);
+            warp_sum2(part[2], part[3], ccost[2], ccost[3]);
+            ccost[4] = __reduce_add_sync(kFull, part[4]);
+        }
+        costed = all;
+    }
+    for (unsigned it = 0; !kSparse; ++it) {
         // The next poll is issued first, so its latency overlaps the
         // costing below; its result is consumed at the end of the pass.
         unsigned long long w = 0;
@@ -2772,13 +2836,14 @@ __global__ void __launch_bounds__(32 * (kDirect ? 8 : kPairWarpsMax)) me_pair_ke
                 bool ok = true;
                 if (lane == 0) ok = mbar_wait(&bars[cur], (parity >> cur) & 1u, a.timeout_ns);
                 ok = __shfl_sync(kFull, ok, 0);
-                parity ^= 1u << cur;
-                pending &= ~(1u << cur);
                 if (!ok) {
+                    // the copies of `cur` stay pending: the drain below waits for them too
                     if (lane == 0) raise_error(a.status, SME_ERR_TIMEOUT, true);
                     failed = true;
                     break;
                 }
+                parity ^= 1u << cur;
+                pending &= ~(1u << cur);
                 const uint8_t* buf = wbase + cur * L.buf_bytes;
                 const uint8_t* win = buf + L.o_ref;
                 const uint32_t* acur = reinterpret_cast<const uint32_t*>(buf + L.o_acur);
@@ -2932,7 +2997,11 @@ __global__ void __launch_bounds__(32 * (kDirect ? 8 : kPairWarpsMax)) me_pair_ke
                 nt = nn;
                 ++u;
             }
-            // A failing warp drains its own copies in flight before the CTA moves on.
+            // A failing warp drains its own copies in flight -- including the
+            // one whose wait gave up -- before the CTA moves on.  Each drain is
+            // bounded too: a copy still outstanding after a second full wait
+            // limit (a TMA stall of seconds) is the one case this path cannot
+            // cover; the launch has then already reported SME_ERR_TIMEOUT.
             if (failed) {
                 for (int b = 0; b < 2; ++b)
                     if (pending & (1u << b)) {

@@ -37,7 +37,7 @@ EXPORTS = [
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_set_config", "sme_batch_run_stage", "sme_batch_class_map", "sme_seednet_forward_active_table",
     "sme_batch_upload", "sme_batch_download", "sme_batch_set_pair_rounds", "sme_batch_run_pair",
-    "sme_seednet_temporal_composite",
+    "sme_seednet_temporal_composite", "sme_batch_set_option",
     "sme_batch_destroy", "sme_seednet_param_count", "sme_seednet_create", "sme_seednet_destroy",
     "sme_seednet_set_params", "sme_seednet_get_params", "sme_seednet_features", "sme_seednet_features_table",
     "sme_seednet_forward",
@@ -128,6 +128,7 @@ def _lib():
             "sme_batch_set_config": (i, [vp, i, i, i]),
             "sme_batch_run_stage": (i, [vp, i]),
             "sme_batch_set_pair_rounds": (i, [vp, i]),
+            "sme_batch_set_option": (i, [vp, i, i]),
             "sme_batch_run_pair": (i, [vp, i]),
             "sme_batch_upload": (i, [vp, C.POINTER(HostIO), i]),
             "sme_batch_download": (i, [vp, C.POINTER(HostIO), i]),
@@ -427,7 +428,7 @@ class Batch:
 
     def __init__(self, luma_list, alpha_list, search_range=16, subpel=2, theta=2.0, epsilon=1.0,
                  max_iters=8, ref_distance=1, want=("cost", "disp", "iters", "npos", "mb_class", "sse"),
-                 temporal_list=None, seed_list=None):
+                 temporal_list=None, seed_list=None, four_mv=False):
         import torch
 
         self.torch = torch
@@ -443,6 +444,7 @@ class Batch:
             F, H, W = l.shape
             est_like = Estimator.__new__(Estimator)
             est_like.torch, est_like.M, est_like.height, est_like.width = torch, (W // 16) * (H // 16), H, W
+            est_like.four_mv = bool(four_mv)
             out = Estimator._alloc_outputs(est_like, F - ref_distance, want, l.device)
             self.outputs.append(out)
             tmp = None if temporal_list is None else temporal_list[i]
@@ -454,6 +456,8 @@ class Batch:
         stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
         _check(lib.sme_batch_create(C.byref(h), C.byref(self.params), seqs, n, stream), "sme_batch_create")
         self._h = h
+        if four_mv:  # Sec. 3.2: four vectors per MB, outputs [P, M, 4, ...]
+            _check(lib.sme_batch_set_option(h, SME_OPT_FOUR_MV, 1), "sme_batch_set_option")
 
     def tune(self, trials=3):
         _check(_lib().sme_batch_tune(self._h, int(trials)), "sme_batch_tune")

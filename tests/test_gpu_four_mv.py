@@ -159,3 +159,42 @@ def test_bounded_wait_reports_timeout_and_context_recovers(sme, schedule):
     o = O.estimate_sequence4(O.OracleParams(64, 64, 8, 1), luma, alpha)
     assert np.array_equal(g["mv"].cpu().numpy(), o["mv"])
     est.close()
+
+
+@pytest.mark.parametrize("schedule,param,flag", [("mb", 0, 1), ("pair", 8, 0), ("pair", 4, 0)])
+def test_four_mv_batch_matches_oracle(sme, schedule, param, flag):
+    """Four vectors per MB in a batch of uneven sequences (sme_batch_set_option):
+    every VOP's block fields equal the oracle's, in both schedules of the
+    mode, twice in a row; tuning keeps them; the sparse schedule, seeds and
+    pair rounds are refused in this mode."""
+    sizes = [(176, 144, 4), (352, 288, 3), (96, 64, 3)]
+    seqs = []
+    for i, (W, H, F) in enumerate(sizes):
+        s = synth.make_sequence(W, H, F, seed=600 + i, n_objects=1 + i % 2, vmax=6.0, obj_frac=0.35)
+        seqs += [(s.luma, s.alpha[j]) for j in range(s.alpha.shape[0])]
+    b = sme.Batch([cuda(l) for l, _ in seqs], [cuda(a) for _, a in seqs], search_range=16, subpel=2,
+                  want=WANT, four_mv=True)
+    b.set_config(schedule, param, flag)
+    for _ in range(2):
+        outs = b.run()
+        for (luma, alpha), g in zip(seqs, outs):
+            F, H, W = luma.shape
+            o = O.estimate_sequence4(O.OracleParams(W, H, 16, 2), luma, alpha, want_pred=True)
+            g = {k: v.cpu().numpy() for k, v in g.items()}
+            assert_parity(g, o, luma)
+    with pytest.raises(sme.SmeError):
+        b.set_config("sparse", 2, 0)
+    with pytest.raises(sme.SmeError):
+        b.set_pair_rounds(True)
+    b.tune(trials=1)
+    assert b.config()["schedule"] in ("mb", "pair")
+    outs = b.run()
+    for (luma, alpha), g in zip(seqs, outs):
+        F, H, W = luma.shape
+        o = O.estimate_sequence4(O.OracleParams(W, H, 16, 2), luma, alpha)
+        assert np.array_equal(g["mv"].cpu().numpy(), o["mv"])
+    b.close()
+    seeds = [torch.zeros((l.shape[0] - 1, (l.shape[2] // 16) * (l.shape[1] // 16), 2), device="cuda") for l, _ in seqs]
+    with pytest.raises(sme.SmeError):
+        sme.Batch([cuda(l) for l, _ in seqs], [cuda(a) for _, a in seqs], search_range=16, subpel=2,
+                  seed_list=seeds, four_mv=True)

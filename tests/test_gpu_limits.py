@@ -119,3 +119,32 @@ def test_one_step_beyond_each_limit(sme, field, value, status):
     h = C.c_void_p()
     assert _lib().sme_create(C.byref(h), C.byref(p), None) == status
     assert not h.value
+
+
+@pytest.mark.parametrize("schedule", ["mb", "pair", "sparse"])
+def test_seeded_search_at_the_position_log_bound(sme, schedule):
+    """Seeds with max_iters = 8 on unstructured frames with far seeds: the
+    seed often wins and both searches run (reading c21), filling the position
+    record towards its 149-entry bound; every output equals the oracle's.
+    One step more is refused before any GPU work."""
+    W = H = 96
+    rng = np.random.default_rng(17)
+    luma = rng.integers(0, 256, (3, H, W), dtype=np.uint8)
+    alpha = np.full((3, H, W), 255, np.uint8)
+    M = (W // 16) * (H // 16)
+    seed = rng.normal(0, 10, (2, M, 2)).astype(np.float32)
+    est = sme.Estimator(W, H, search_range=16, subpel=2, max_iters=8)
+    est.set_schedule(schedule)
+    g = est.estimate_sequence(torch.from_numpy(luma).cuda(), torch.from_numpy(alpha).cuda(),
+                              seed=torch.from_numpy(seed).cuda(), want=("cost", "iters", "npos", "mb_class", "sse"))
+    o = O.estimate_sequence(O.OracleParams(W, H, 16, 2, max_iters=8), luma, alpha, seed=seed)
+    assert np.array_equal(g["mv"].cpu().numpy(), o["mv"])
+    assert np.array_equal(g["iters"].cpu().numpy(), o["iters"])
+    assert np.array_equal(g["npos"].cpu().numpy(), o["npos"])
+    assert int(o["npos"].max()) <= 149
+    est.close()
+    est = sme.Estimator(W, H, search_range=16, subpel=2, max_iters=9)
+    with pytest.raises(sme.SmeError):
+        est.estimate_sequence(torch.from_numpy(luma).cuda(), torch.from_numpy(alpha).cuda(),
+                              seed=torch.from_numpy(seed).cuda())
+    est.close()

@@ -121,10 +121,11 @@ __device__ __forceinline__ VRange valid_range(int W, int H, const Method& m, int
     return r;
 }
 
-// Stage the reference rows/columns every vector of V can touch into this
-// warp's window with coalesced 16-byte loads.  Window origin in wx0/wy0.
-__device__ __forceinline__ void stage_window(uint8_t* win, const uint8_t* ref, int W, int H, int S,
-                                             int X0, int Y0, int lane, int& wx0, int& wy0)
+// Issue the copies of the reference rows/columns every vector of V can touch
+// into this warp's window (coalesced 16-byte asynchronous copies), without
+// waiting for them.  Window origin in wx0/wy0.
+__device__ __forceinline__ void stage_window_issue(uint8_t* win, const uint8_t* ref, int W, int H, int S,
+                                                   int X0, int Y0, int lane, int& wx0, int& wy0)
 {
     const int cs = ceil16(S), pitch = win_pitch(S);
     wy0 = max(0, Y0 - S);
@@ -145,8 +146,22 @@ __device__ __forceinline__ void stage_window(uint8_t* win, const uint8_t* ref, i
                      "l"(src0 + (size_t)r * W + 16 * ch)
                      : "memory");
     }
+}
+
+// Wait for this lane's window copies, then make the whole window visible to
+// the warp.
+__device__ __forceinline__ void stage_window_wait()
+{
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
+}
+
+// Stage the window and wait for it.
+__device__ __forceinline__ void stage_window(uint8_t* win, const uint8_t* ref, int W, int H, int S,
+                                             int X0, int Y0, int lane, int& wx0, int& wy0)
+{
+    stage_window_issue(win, ref, W, H, S, X0, Y0, lane, wx0, wy0);
+    stage_window_wait();
 }
 
 // ------------------------------------------------- packed 8-pixel samples --
@@ -434,24 +449,39 @@ __device__ __forceinline__ void fill_rcp(float* rcp)
     }
 }
 
-__device__ __forceinline__ void grad_factors8(const uint8_t* cur, int W, int H, int x0, int y, const P8& c,
-                                              float theta, const float* rcp, float (&ux)[8], float (&uy)[8])
+// The samples around the lane's 8 pixels that the gradients need: the left
+// and right neighbours in the row, the rows above and below (0 outside).
+struct GradNb {
+    int left, right;
+    P8 up, dn;
+};
+__device__ __forceinline__ GradNb grad_loads(const uint8_t* cur, int W, int H, int x0, int y)
 {
-    const float lim = 2.0f * theta;
     const uint8_t* row = cur + (size_t)y * W;
-    const int left = x0 > 0 ? (int)__ldg(row + x0 - 1) : 0;
-    const int right = x0 + 8 < W ? (int)__ldg(row + x0 + 8) : 0;
-    P8 up = {0u, 0u}, dn = {0u, 0u};
+    GradNb n;
+    n.left = x0 > 0 ? (int)__ldg(row + x0 - 1) : 0;
+    n.right = x0 + 8 < W ? (int)__ldg(row + x0 + 8) : 0;
+    n.up = P8{0u, 0u};
+    n.dn = P8{0u, 0u};
     if (y > 0) {
         const uint2 t = __ldg(reinterpret_cast<const uint2*>(row - W + x0));
-        up.lo = t.x;
-        up.hi = t.y;
+        n.up.lo = t.x;
+        n.up.hi = t.y;
     }
     if (y < H - 1) {
         const uint2 t = __ldg(reinterpret_cast<const uint2*>(row + W + x0));
-        dn.lo = t.x;
-        dn.hi = t.y;
+        n.dn.lo = t.x;
+        n.dn.hi = t.y;
     }
+    return n;
+}
+
+__device__ __forceinline__ void grad_factors8(const GradNb& n, int W, int H, int x0, int y, const P8& c, float theta,
+                                              const float* rcp, float (&ux)[8], float (&uy)[8])
+{
+    const float lim = 2.0f * theta;
+    const int left = n.left, right = n.right;
+    const P8 up = n.up, dn = n.dn;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int x = x0 + k;
@@ -1067,10 +1097,10 @@ __device__ __forceinline__ void transparent_mb(const SeqDesc* sd, int idx, int k
 }
 
 // Eq. 4 factors of the lane's pixels and their counts over the MB.
-__device__ __forceinline__ void mb_factors(const uint8_t* cur, int W, int H, int x0, int y, const P8& c8, float theta,
+__device__ __forceinline__ void mb_factors(const GradNb& gn, int W, int H, int x0, int y, const P8& c8, float theta,
                                            const float* rcp, float (&ux)[8], float (&uy)[8], int& nx, int& ny)
 {
-    grad_factors8(cur, W, H, x0, y, c8, theta, rcp, ux, uy);
+    grad_factors8(gn, W, H, x0, y, c8, theta, rcp, ux, uy);
     int cx = 0, cy = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -1175,19 +1205,34 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
     const uint8_t* cur = sd->luma + (size_t)(k + rd) * FS;
     const int cls = __ldg(sd->cls + (size_t)(k + rd) * M + mb);
     const P8 c8 = load8(cur + (size_t)y * W + x0);
+    // The sparse schedule lists only non-transparent MBs: their window copies
+    // and the samples of the gradient factors are requested at once, with the
+    // loads above, so that one memory round trip serves them all.
+    int wx0, wy0;
+    GradNb gn;
+    if constexpr (kSparse) {
+        stage_window_issue(win, ref, W, H, m.S, X0, Y0, lane, wx0, wy0);
+        gn = grad_loads(cur, W, H, x0, y);
+    }
 
     if (cls == SME_TRANSPARENT) {
+        if constexpr (kSparse) stage_window_wait();
         L.publish(gid, 0, lane);
         transparent_mb(sd, idx, k, ref, c8, lane, FS, W, y, x0);
         return true;
     }
 
     // ---- work that does not depend on the neighbours: prefetch ----
-    int wx0, wy0;
-    stage_window(win, ref, W, H, m.S, X0, Y0, lane, wx0, wy0);
+    if constexpr (!kSparse) stage_window(win, ref, W, H, m.S, X0, Y0, lane, wx0, wy0);
     float ux[8], uy[8];
     int nx = 0, ny = 0;
-    if (cls == SME_OPAQUE) mb_factors(cur, W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny);
+    if constexpr (kSparse) {
+        if (cls == SME_OPAQUE) mb_factors(gn, W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny);
+        stage_window_wait();
+    } else {
+        if (cls == SME_OPAQUE)
+            mb_factors(grad_loads(cur, W, H, x0, y), W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny);
+    }
     const VRange V = valid_range(W, H, m, X0, Y0);
 
     // ---- candidates A, B, C, T (Fig. 1, Fig. 3) + optional seed ----
@@ -2576,7 +2621,7 @@ __device__ __forceinline__ bool me_one_mb4(const MeArgs& a, const Method& m, int
     stage_window(win, ref, W, H, m.S, X0, Y0, lane, wx0, wy0);
     float ux[8], uy[8];
     int nx = 0, ny = 0;
-    if (cls == SME_OPAQUE) mb_factors(cur, W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny);
+    if (cls == SME_OPAQUE) mb_factors(grad_loads(cur, W, H, x0, y), W, H, x0, y, c8, m.theta, s_rcp, ux, uy, nx, ny);
     const VRange V = valid_range(W, H, m, X0, Y0);
     const int lx = x0 - wx0, ly = y - wy0;
 
@@ -3090,7 +3135,7 @@ __global__ void __launch_bounds__(32 * kQueryWarps) query_kernel(const Geom g, c
     const P8 r8 = ref8(win, win_pitch(m.S), x0 - wx0, y - wy0, dx, dy, m.h);
     const unsigned sad = __reduce_add_sync(kFull, sad8(r8, c8));
     float ux[8], uy[8];
-    grad_factors8(a.cur, g.W, g.H, x0, y, c8, m.theta, s_rcp, ux, uy);
+    grad_factors8(grad_loads(a.cur, g.W, g.H, x0, y), g.W, g.H, x0, y, c8, m.theta, s_rcp, ux, uy);
     int cx = 0, cy = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {

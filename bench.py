@@ -1196,6 +1196,15 @@ def run_ours(args):
     net, train_info = None, None
     if not args.no_learned:
         net, train_info = train_seednet(sme, torch, args)
+    if args.cif_only:  # profiling: the CIF x 30 leg alone (ES, four vectors, learned), as its own line
+        cif = measure_cif(sme, torch, args, rank, dist, net, train_info)
+        if net is not None:
+            net.close()
+        if rank == 0:
+            print(json.dumps({"cif30": cif}))
+        if dist:
+            dist.destroy_process_group()
+        return
     head = measure_headline(sme, torch, args, net, dist, rank)
     if args.headline_only:
         args.no_cif = args.no_batch = args.no_hd = args.no_paper = True
@@ -1286,6 +1295,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the headline's host-buffer (end-to-end) runs")
     ap.add_argument("--no-rounds", action="store_true", help="skip the pair-round learned form at the headline")
     ap.add_argument("--headline-only", action="store_true", help="only the headline measurement (profiling)")
+    ap.add_argument("--cif-only", action="store_true", help="only the CIF x 30 measurements (profiling)")
     ap.add_argument("--hd-frames", type=int, default=300, help="frames of the 1920x1088 learned evaluation")
     ap.add_argument("--learn-pairs", type=int, default=2000, help="CIF VOP pairs the seed network is trained on")
     ap.add_argument("--learn-steps", type=int, default=800, help="Adam steps (32 pairs each)")

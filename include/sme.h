@@ -229,7 +229,8 @@ int sme_gradient_step(sme_ctx* ctx, const uint8_t* ref, const uint8_t* cur,
  *     other MBs in wavefront order, taking a transparent neighbour's (0,0)
  *     from the class map without waiting (never speculatively);
  *     SME_OPT_MB_CTAS_PER_SM 2 or 3 selects the search kernel built for
- *     that many resident CTAs per SM, else one;
+ *     that many resident 8-warp CTAs per SM, 5 the one built for five
+ *     4-warp CTAs per SM, else one 8-warp CTA;
  *     SME_SCHED_AUTO (default) -- chosen per workload.
  *   SME_OPT_PAIR_WARPS: warps (MB rows in flight) per CTA of the pair
  *     schedule, 1..16 (at most 8 used with SME_OPT_PAIR_DIRECT); 0
@@ -328,9 +329,10 @@ int sme_autotune(sme_ctx* ctx, const uint8_t* luma, const uint8_t* alpha, int n_
  *                      SME_SCHED_MB (param = CTAs per SM, 0..32, 0 = all that
  *                      fit; flag = speculation), SME_SCHED_PAIR (param =
  *                      warps per CTA, 0..16, 0 = automatic; flag = direct
- *                      transparent runs) or SME_SCHED_SPARSE (param 0..3: 2, 3
- *                      = the search kernel built for that many CTAs per SM; flag
- *                      0 or 1, unused); drops a captured graph (later runs
+ *                      transparent runs) or SME_SCHED_SPARSE (param 0..3 or 5:
+ *                      2, 3 = the search kernel built for that many 8-warp
+ *                      CTAs per SM, 5 = for five 4-warp CTAs; flag 0 or 1,
+ *                      unused); drops a captured graph (later runs
  *                      launch directly until sme_batch_tune).  SME_ERR_ARG on
  *                      other values.
  * Results per sequence are exactly those of sme_estimate_sequence on it. */

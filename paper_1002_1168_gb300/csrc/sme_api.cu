@@ -617,7 +617,7 @@ const ExecCfg kTuneCandidates[] = {
     {kSchedPair, 4, 0, 0, 0, 0},     {kSchedPair, 8, 0, 0, 0, 0},
     {kSchedPair, 16, 0, 0, 0, 0},    {kSchedCluster, 0, 0, 1, 16, 1}, {kSchedCluster, 0, 0, 0, 16, 1},
     {kSchedCluster, 0, 0, 1, 8, 1},  {kSchedSparse, 0, 1, 0, 0, 1},   {kSchedSparse, 0, 2, 0, 0, 1},
-    {kSchedSparse, 0, 3, 0, 0, 1},
+    {kSchedSparse, 0, 3, 0, 0, 1},   {kSchedSparse, 0, 5, 0, 0, 1},
 };
 
 // Device time of `trials` back-to-back runs of `enqueue` (the minimum), ms;
@@ -1713,7 +1713,7 @@ int sme_batch_set_config(sme_batch* b, int schedule, int param, int flag)
         e.speculate = flag;
         break;
     case kSchedSparse:
-        if (param < 0 || param > 3) return SME_ERR_ARG;
+        if (param < 0 || param > 5 || param == 4) return SME_ERR_ARG;
         e.mb_ctas_per_sm = param;
         e.speculate = flag;
         break;

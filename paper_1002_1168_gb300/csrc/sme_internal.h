@@ -31,6 +31,9 @@ static_assert(4 + 9 * kMaxIters <= kMaxLog, "block searches overrun the position
 static_assert(kMaxLog < 256, "distinct-position count does not fit its byte");
 constexpr long long kDefaultTimeoutNs = 1000000000LL;
 constexpr int kMeWarps = 8;        // warps (one MB each) per CTA of the per-MB ME kernel
+// Warps per CTA of the sparse schedule's search build for `min_blocks` CTAs
+// per SM: 4 for the five-CTA build, else kMeWarps.
+__host__ __device__ constexpr int sparse_cta_warps(int min_blocks) { return min_blocks == 5 ? 4 : kMeWarps; }
 constexpr int kClusterWarps = 12;  // warps (one MB each) per CTA of the cluster schedule
 constexpr int kPairWarpsMax = 16;  // warps (MB rows) per CTA of the per-pair ME kernel
 

@@ -844,12 +844,9 @@ __device__ __forceinline__ int prs_run(const Method& m, const uint8_t* win, int 
     return iters;
 }
 
-// Opaque MB after the candidate comparison: the pixel recursive search from
-// the winner; when a learned seed (candidate 4) won strictly, the search runs
-// from it and from the best plain candidate, and the plain result is kept
-// unless the seeded one ends strictly lower.  cand/costs/cs8 are the
-// candidates in order A, B, C, T(, seed); best is the winning index.
-__device__ __forceinline__ void opaque_search(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
+// The same search with the two searches of a seed-won MB inlined one after
+// the other.
+__device__ __forceinline__ void opaque_search_two_sites(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
                                               const P8& c8, const float (&ux)[8], const float (&uy)[8], int nx,
                                               int ny, const VRange& V, const int (&cand)[5],
                                               const unsigned (&costs)[5], const P8 (&cs8)[5], int nc, int best,
@@ -904,6 +901,91 @@ __device__ __forceinline__ void opaque_search(const Method& m, const uint8_t* wi
     } else {
         iters = prs_run(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, dx, dy, cost, r8, lastx, lasty, slog, nlog,
                         lane, spec && pack_mv(dx, dy) == spec_key, sp);
+    }
+    res.dx = dx;
+    res.dy = dy;
+    res.cost = cost;
+    res.r8 = r8;
+    res.iters = iters;
+    res.lastx = lastx;
+    res.lasty = lasty;
+}
+
+// Opaque MB after the candidate comparison: the pixel recursive search from
+// the winner; when a learned seed (candidate 4) won strictly, the search runs
+// from the best plain candidate and then from the seed, and the plain result
+// is kept unless the seeded one ends strictly lower.  kOneSite: both searches
+// go through one call site (in the sparse search the rarely taken second
+// search was a cold copy of the search code, slow to fetch and evicting the
+// hot one: 54 -> 38 ms on the learned headline search); else two inlined
+// searches (the per-MB and per-pair kernels keep their register allocation).
+// cand/costs/cs8 are the candidates in order A, B, C, T(, seed); best is the
+// winning index.
+template <bool kOneSite>
+__device__ __forceinline__ void opaque_search(const Method& m, const uint8_t* win, int pitch, int lx, int ly,
+                                              const P8& c8, const float (&ux)[8], const float (&uy)[8], int nx,
+                                              int ny, const VRange& V, const int (&cand)[5],
+                                              const unsigned (&costs)[5], const P8 (&cs8)[5], int nc, int best,
+                                              int* slog, int& nlog, int lane, bool spec, int spec_key,
+                                              const PrsStep& sp, MbResult& res)
+{
+    if constexpr (!kOneSite) {
+        opaque_search_two_sites(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, costs, cs8, nc, best, slog, nlog,
+                                lane, spec, spec_key, sp, res);
+        return;
+    }
+    const bool two = nc == 5 && best == 4;
+    // The first pass starts from the winner, or (two passes) from the first
+    // strict minimum of A, B, C, T.
+    int first = best;
+    if (two) {
+        first = 0;
+#pragma unroll
+        for (int c = 1; c < 4; ++c)
+            if (costs[c] < costs[first]) first = c;
+    }
+    int dx = mv_x(cand[0]), dy = mv_y(cand[0]);
+    unsigned cost = costs[0];
+    P8 r8 = cs8[0];
+#pragma unroll
+    for (int c = 1; c < 5; ++c)
+        if (c == first) {
+            dx = mv_x(cand[c]);
+            dy = mv_y(cand[c]);
+            cost = costs[c];
+            r8 = cs8[c];
+        }
+    float lastx, lasty;
+    int iters;
+    int px = 0, py = 0, pit = 0;
+    unsigned pc = 0;
+    P8 pr8 = r8;
+    float plx = 0.0f, ply = 0.0f;
+#pragma unroll 1
+    for (int pass = 0;; ++pass) {
+        iters = prs_run(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, dx, dy, cost, r8, lastx, lasty, slog, nlog,
+                        lane, spec && pack_mv(dx, dy) == spec_key, sp);
+        if (!two || pass == 1) break;
+        px = dx;
+        py = dy;
+        pc = cost;
+        pr8 = r8;
+        pit = iters;
+        plx = lastx;
+        ply = lasty;
+        dx = mv_x(cand[4]);
+        dy = mv_y(cand[4]);
+        cost = costs[4];
+        r8 = cs8[4];
+    }
+    if (two && !(cost < pc)) {
+        dx = px;
+        dy = py;
+        cost = pc;
+        r8 = pr8;
+        iters = pit;
+        lastx = plx;
+        lasty = ply;
     }
     res.dx = dx;
     res.dy = dy;
@@ -969,7 +1051,7 @@ __device__ __forceinline__ MbResult search_mb(const Method& m, int cls, const ui
                 best = c;
             }
         PrsStep none;
-        opaque_search(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, sad, cs8, nc, best, slog, nlog, lane, false,
+        opaque_search<false>(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, sad, cs8, nc, best, slog, nlog, lane, false,
                       0, none, res);
         res.nlog = nlog;
         return res;
@@ -1111,11 +1193,16 @@ __device__ __forceinline__ void mb_factors(const GradNb& gn, int W, int H, int x
     ny = (int)__reduce_add_sync(kFull, (unsigned)cy);
 }
 
+// The seed of MB idx in MV units, rounded and clamped to V.
+__device__ __forceinline__ int seed_key_of(float x, float y, int h, const VRange& V)
+{
+    const float sx = fminf(fmaxf(__fmul_rn((float)h, x), -1024.0f), 1024.0f);
+    const float sy = fminf(fmaxf(__fmul_rn((float)h, y), -1024.0f), 1024.0f);
+    return pack_mv(clampi((int)roundf(sx), V.lox, V.hix), clampi((int)roundf(sy), V.loy, V.hiy));
+}
 __device__ __forceinline__ int seed_key(const SeqDesc* sd, int idx, int h, const VRange& V)
 {
-    const float sx = fminf(fmaxf(__fmul_rn((float)h, __ldg(sd->seed + 2 * (size_t)idx)), -1024.0f), 1024.0f);
-    const float sy = fminf(fmaxf(__fmul_rn((float)h, __ldg(sd->seed + 2 * (size_t)idx + 1)), -1024.0f), 1024.0f);
-    return pack_mv(clampi((int)roundf(sx), V.lox, V.hix), clampi((int)roundf(sy), V.loy, V.hiy));
+    return seed_key_of(__ldg(sd->seed + 2 * (size_t)idx), __ldg(sd->seed + 2 * (size_t)idx + 1), h, V);
 }
 
 __device__ __forceinline__ P8 load8(const uint8_t* p)
@@ -1210,9 +1297,14 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
     // loads above, so that one memory round trip serves them all.
     int wx0, wy0;
     GradNb gn;
+    float seed_x = 0.0f, seed_y = 0.0f;
     if constexpr (kSparse) {
         stage_window_issue(win, ref, W, H, m.S, X0, Y0, lane, wx0, wy0);
         gn = grad_loads(cur, W, H, x0, y);
+        if (lane == 4 && sd->seed) {  // the learned seed: its read flies with the others
+            seed_x = __ldg(sd->seed + 2 * (size_t)idx);
+            seed_y = __ldg(sd->seed + 2 * (size_t)idx + 1);
+        }
     }
 
     if (cls == SME_TRANSPARENT) {
@@ -1256,7 +1348,7 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
     int key = 0;
     if (lane == 3 && k == 0 && sd->temporal_in)
         key = (int)__ldg(reinterpret_cast<const unsigned*>(sd->temporal_in + mb));
-    if (lane == 4 && sd->seed) key = seed_key(sd, idx, h, V);
+    if (lane == 4 && sd->seed) key = kSparse ? seed_key_of(seed_x, seed_y, h, V) : seed_key(sd, idx, h, V);
     if (lane < 4) key = pack_mv(clampi(mv_x(key), V.lox, V.hix), clampi(mv_y(key), V.loy, V.hiy));
     const int nc = sd->seed ? 5 : 4;
     bool res_l = dep < 0;
@@ -1421,7 +1513,7 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
     if (cls == SME_OPAQUE) {
         // Sec. 3.2 (the first step may be the speculative one, taken at
         // the same position).
-        opaque_search(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, ccost, cs8, nc, bi, slog, nlog, lane,
+        opaque_search<kSparse>(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, ccost, cs8, nc, bi, slog, nlog, lane,
                       spec, spec_key, sp, r);
     } else {
         int bk = cand[0];
@@ -1755,10 +1847,11 @@ __device__ __forceinline__ int seq_of_gid(const int* seq_base, int n, int gid)
 // The per-MB search over the list of non-transparent MBs.  Every dependency
 // of an MB has a smaller key, hence an earlier ticket, so the warps (all
 // resident) can always make progress, as in me_kernel.
-// kMinBlocks: CTAs per SM the register budget is cut for (1: no spills, one
-// 8-warp CTA per SM; 2 and 3: more warps, with some spills), chosen by tuning.
+// kMinBlocks: CTAs per SM the register budget is cut for (1: one 8-warp CTA
+// per SM, 2: two without spills, 3: three with some spills; 5: five CTAs of
+// 4 warps, 20 warps per SM at 96 registers), chosen by tuning.
 template <bool kVariants, int kMinBlocks>
-__global__ void __launch_bounds__(32 * kMeWarps, kMinBlocks) me_sparse_kernel(const MeArgs a)
+__global__ void __launch_bounds__(32 * sparse_cta_warps(kMinBlocks), kMinBlocks) me_sparse_kernel(const MeArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -3265,6 +3358,7 @@ cudaError_t sparse_attr(const void** fn, size_t smem)
 
 cudaError_t sparse_kernel(bool variants, int min_blocks, size_t smem, const void** fn)
 {
+    if (min_blocks == 5) return variants ? sparse_attr<true, 5>(fn, smem) : sparse_attr<false, 5>(fn, smem);
     if (variants)
         return min_blocks >= 3   ? sparse_attr<true, 3>(fn, smem)
                : min_blocks == 2 ? sparse_attr<true, 2>(fn, smem)
@@ -3276,23 +3370,25 @@ cudaError_t sparse_kernel(bool variants, int min_blocks, size_t smem, const void
 
 cudaError_t me_sparse_occupancy(int S, int min_blocks, int* blocks_per_sm, bool variants)
 {
-    const size_t smem = me_smem_bytes(S);
+    const int warps = sparse_cta_warps(min_blocks);
+    const size_t smem = (size_t)warps * warp_smem(S);
     const void* fn = nullptr;
     cudaError_t e = sparse_kernel(variants, min_blocks, smem, &fn);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 32 * kMeWarps, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 32 * warps, smem);
 }
 
 cudaError_t launch_me_sparse(const Method& m, const MeArgs& a, int grid, int min_blocks, cudaStream_t s)
 {
     // cooperative for the same reason as launch_me: warps wait on each other
-    const size_t smem = me_smem_bytes(m.S);
+    const int warps = sparse_cta_warps(min_blocks);
+    const size_t smem = (size_t)warps * warp_smem(m.S);
     const void* fn = nullptr;
     cudaError_t e = sparse_kernel(m.tt != 0, min_blocks, smem, &fn);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(32 * kMeWarps);
+    cfg.blockDim = dim3(32 * warps);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

@@ -75,7 +75,8 @@ def test_autotune_context_keeps_results(sme):
     est.close()
 
 
-@pytest.mark.parametrize("schedule,param,flag", [("sparse", 1, 1), ("sparse", 2, 0), ("sparse", 3, 0), ("mb", 0, 1),
+@pytest.mark.parametrize("schedule,param,flag", [("sparse", 1, 1), ("sparse", 2, 0), ("sparse", 3, 0), ("sparse", 5, 0),
+                                                 ("mb", 0, 1),
                                                  ("pair", 8, 1), ("pair", 4, 0)])
 def test_batch_each_configuration_matches_oracle(sme, schedule, param, flag):
     """Every execution configuration of a batch, set explicitly, gives the
@@ -108,8 +109,9 @@ def test_batch_set_config_rejects_bad_values(sme):
     b = sme.Batch([torch.from_numpy(l).cuda() for l, _ in seqs], [torch.from_numpy(a).cuda() for _, a in seqs])
     with pytest.raises(sme.SmeError):
         b.set_config("cluster")
-    with pytest.raises(sme.SmeError):
-        b.set_config("sparse", 4)
+    for bad in (4, 6):
+        with pytest.raises(sme.SmeError):
+            b.set_config("sparse", bad)
     with pytest.raises(sme.SmeError):
         b.set_config("pair", 17)
     b.close()

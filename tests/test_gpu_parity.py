@@ -33,17 +33,17 @@ def cuda(a):
 # "pair_staged": the pair schedule with every MB staged by TMA (transparent
 # MBs included) instead of finishing transparent runs from global memory.
 # "sparse3": the sparse schedule with its search kernel built for three CTAs
-# per SM (the most registers cut).
-SCHEDULES = ["pair", "pair_staged", "mb", "cluster", "sparse", "sparse3"]
+# per SM (the most registers cut); "sparse5": built for five 4-warp CTAs.
+SCHEDULES = ["pair", "pair_staged", "mb", "cluster", "sparse", "sparse3", "sparse5"]
 
 
 def set_schedule(sme, est, schedule, pair_warps=0):
     if schedule == "pair_staged":
         est.set_schedule("pair", pair_warps=pair_warps)
         est.set_option(sme.SME_OPT_PAIR_DIRECT, 0)
-    elif schedule == "sparse3":
+    elif schedule in ("sparse3", "sparse5"):
         est.set_schedule("sparse")
-        est.set_option(sme.SME_OPT_MB_CTAS_PER_SM, 3)
+        est.set_option(sme.SME_OPT_MB_CTAS_PER_SM, int(schedule[-1]))
     else:
         est.set_schedule(schedule, pair_warps=pair_warps if schedule == "pair" else 0)
 

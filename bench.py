@@ -153,10 +153,12 @@ def peaks():
 # ncu capture summarised in profiles/me_kernel_cif30_halfpel.md (set to None
 # whenever the kernel changes until it is captured again).
 ME_KERNEL_TRAFFIC_BYTES = 3510016 + 13568
-# DRAM bytes of one sparse search launch of the headline's learned run, from
-# an ncu capture scaled as the profile summary states (None until captured
-# for the current kernel).
-SEARCH_KERNEL_TRAFFIC_BYTES = None
+# DRAM bytes of one sparse search launch of the headline's learned run: the
+# ncu capture of the same build on one scene of the headline (20 frames,
+# 115,920 searched MBs; 66.18 MB read + 3.59 MB written, the
+# me_sparse_kernel profile summary) scaled by the searched MBs of the full
+# run (5,544,264).
+SEARCH_KERNEL_TRAFFIC_BYTES = int(round((66.178304e6 + 3.585536e6) * 5544264 / 115920))
 
 
 def algorithmic_bytes(P, M, F):

@@ -292,6 +292,17 @@ int sme_set_option(sme_ctx* ctx, int option, int value);
  * optional).  Asynchronous on the context's stream; SME_ERR_SIZE if the
  * search window does not fit in shared memory. */
 int sme_full_search(sme_ctx* ctx, const uint8_t* luma, int n_frames, sme_mv* mv, uint32_t* sad);
+/* Measurement helper (no counterpart in the paper): the device's rate of the
+ * packed-SAD operation mix that the integer roofline of the search and of
+ * the exhaustive search counts -- per 32-bit word of a row, one funnel-shift
+ * alignment, one __vsadu4 absolute difference and one add -- on independent
+ * register-resident chains over the whole GPU.  Launches ctas_per_sm (1..8)
+ * CTAs of 256 threads per SM on cuda_stream, each thread running iters steps
+ * of 8 chains (24 operations per step), and writes one word per thread to
+ * out (device, [grid * 256] uint32) so that the work is kept; *grid (host)
+ * receives the number of CTAs.  The caller times the launch on the stream:
+ * operations = grid * 256 * iters * 24.  SME_ERR_ARG on other values. */
+int sme_packed_sad_rate_launch(int ctas_per_sm, int iters, uint32_t* out, void* cuda_stream, int* grid);
 
 /* The current value of an option (e.g. what sme_autotune chose). */
 int sme_get_option(sme_ctx* ctx, int option, int* value);

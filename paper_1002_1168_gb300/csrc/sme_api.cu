@@ -1119,6 +1119,12 @@ int sme_full_search(sme_ctx* c, const uint8_t* luma, int n_frames, sme_mv* mv, u
     return cuda_status(launch_es(luma, c->g.W, c->g.H, c->m.S, c->m.h, rd, n_frames - rd, mv, sad, c->stream));
 }
 
+int sme_packed_sad_rate_launch(int ctas_per_sm, int iters, uint32_t* out, void* cuda_stream, int* grid)
+{
+    if (ctas_per_sm < 1 || ctas_per_sm > 8 || iters < 1 || !out || !grid) return SME_ERR_ARG;
+    return cuda_status(launch_packed_sad_rate(ctas_per_sm, iters, out, (cudaStream_t)cuda_stream, grid));
+}
+
 int sme_get_option(sme_ctx* c, int option, int* value)
 {
     if (!c || !value) return SME_ERR_ARG;

@@ -131,7 +131,42 @@ __global__ void __launch_bounds__(kEsThreads) es_kernel(const uint8_t* __restric
     }
 }
 
+// The packed-SAD operation mix of the integer roofline (per 32-bit word: a
+// funnel-shift alignment, a __vsadu4 absolute difference, an add), on 8
+// register-resident chains per thread; chain k aligns its own value with its
+// neighbour's, so nothing is loop-invariant.  Per step 24 operations.
+__global__ void __launch_bounds__(256) packed_sad_rate_kernel(int iters, uint32_t* out)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc[8], z[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        acc[k] = t * 0x9E3779B9u + (uint32_t)k * 0x85EBCA6Bu;
+        z[k] = t ^ ((uint32_t)k * 0x27D4EB2Du);
+    }
+    const int sh = (int)(t & 3u) * 8;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = __vsadu4(__funnelshift_r(acc[k], acc[(k + 1) & 7], sh), z[k]) + acc[k];
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r ^= acc[k];
+    out[t] = r;
+}
+
 }  // namespace
+
+cudaError_t launch_packed_sad_rate(int ctas_per_sm, int iters, uint32_t* out, cudaStream_t s, int* grid)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *grid = sms * ctas_per_sm;
+    packed_sad_rate_kernel<<<*grid, 256, 0, s>>>(iters, out);
+    return cudaGetLastError();
+}
 
 size_t es_smem_bytes(int S, int h)
 {

@@ -33,7 +33,7 @@ EXPORTS = [
     "sme_advance", "sme_score", "sme_get_temporal_field", "sme_set_temporal_field", "sme_set_seed_field",
     "sme_compensate", "sme_psnr", "sme_eval_costs", "sme_gradient_step", "sme_profile_begin",
     "sme_profile_end", "sme_estimate_sequence_noalloc", "sme_set_option", "sme_get_option", "sme_autotune",
-    "sme_full_search",
+    "sme_full_search", "sme_packed_sad_rate_launch",
     "sme_batch_create", "sme_batch_tune", "sme_batch_run", "sme_batch_synchronize", "sme_batch_config",
     "sme_batch_set_config", "sme_batch_run_stage", "sme_batch_class_map", "sme_seednet_forward_active_table",
     "sme_batch_upload", "sme_batch_download", "sme_batch_set_pair_rounds", "sme_batch_run_pair",
@@ -118,6 +118,7 @@ def _lib():
             "sme_set_option": (i, [vp, i, i]),
             "sme_get_option": (i, [vp, i, C.POINTER(C.c_int)]),
             "sme_full_search": (i, [vp, vp, i, vp, vp]),
+            "sme_packed_sad_rate_launch": (i, [i, i, vp, vp, C.POINTER(C.c_int)]),
             "sme_autotune": (i, [vp, vp, vp, i, C.POINTER(Outputs), i]),
             "sme_batch_create": (i, [ip, C.POINTER(Params), C.POINTER(Sequence), i, vp]),
             "sme_batch_tune": (i, [vp, i]),
@@ -681,6 +682,30 @@ class SeedNet:
             self.close()
         except Exception:
             pass
+
+
+def packed_sad_rate(ctas_per_sm=8, iters=50000, reps=3):
+    """Measured rate (operations per second, best of `reps` launches timed
+    with events on the current stream) of the packed-SAD operation mix the
+    integer rooflines count (sme_packed_sad_rate_launch)."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    n = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * ctas_per_sm * 256
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    grid = C.c_int()
+    best = None
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _check(_lib().sme_packed_sad_rate_launch(int(ctas_per_sm), int(iters), _ptr(out), C.c_void_p(st.cuda_stream),
+                                                 C.byref(grid)), "sme_packed_sad_rate_launch")
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None or ms < best else best
+    assert grid.value * 256 == n
+    return grid.value * 256 * iters * 24 / (best / 1e3)
 
 
 def pack_params(params):

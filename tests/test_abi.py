@@ -136,3 +136,14 @@ def test_noalloc_argument_errors_before_touching_cuda(lib, case):
         lib.sme_default_params(C.byref(p), 1920, 1088)
         frames, want = 12, 8
     assert lib.sme_estimate_sequence_noalloc(C.byref(p), luma, alpha, frames, None, None, C.byref(out), None) == want
+
+
+def test_packed_sad_rate_rejects_bad_arguments_before_touching_cuda(lib):
+    """The measurement helper checks its arguments before any CUDA call."""
+    out = (C.c_uint32 * 4)()
+    grid = C.c_int(-1)
+    f = lib.sme_packed_sad_rate_launch
+    for cps, iters, o, g in ((0, 10, out, grid), (9, 10, out, grid), (1, 0, out, grid), (1, 10, None, grid),
+                             (1, 10, out, None)):
+        assert f(cps, iters, o, None, g if g is None else C.byref(g)) == 1  # SME_ERR_ARG
+    assert grid.value == -1

@@ -67,3 +67,42 @@ def test_flat_frames_tie_to_first_in_raster_order(sme):
 def test_ref_distance_two(sme):
     seq = synth.cif_sequence(frames=4)
     _check(sme, seq.luma, 16, 2, rd=2)
+
+
+def _vsad(a, b):
+    return sum(abs(((a >> (8 * i)) & 0xFF) - ((b >> (8 * i)) & 0xFF)) for i in range(4))
+
+
+def _fshr(lo, hi, sh):
+    return (((hi << 32) | lo) >> (sh & 31)) & 0xFFFFFFFF
+
+
+def test_packed_sad_rate_kernel_does_the_counted_work(sme):
+    """The measurement kernel behind the integer rooflines' measured op-mix
+    rate computes its chains exactly (checked for a few threads against a
+    host restatement of funnel shift, packed absolute difference and add),
+    so the timed work is the counted work."""
+    import ctypes as C
+    iters, cps = 7, 1
+    n = torch.cuda.get_device_properties(0).multi_processor_count * cps * 256
+    out = torch.zeros(n, dtype=torch.int32, device="cuda")
+    grid = C.c_int()
+    st = torch.cuda.current_stream()
+    assert sme._lib().sme_packed_sad_rate_launch(cps, iters, C.c_void_p(out.data_ptr()), C.c_void_p(st.cuda_stream),
+                                                 C.byref(grid)) == 0
+    torch.cuda.synchronize()
+    assert grid.value * 256 == n
+    got = out.cpu().numpy().view(np.uint32)
+    M = 0xFFFFFFFF
+    for t in (0, 1, 77, 255, 256, n - 1):
+        acc = [(t * 0x9E3779B9 + k * 0x85EBCA6B) & M for k in range(8)]
+        z = [(t ^ ((k * 0x27D4EB2D) & M)) & M for k in range(8)]
+        sh = (t & 3) * 8
+        for _ in range(iters):
+            for k in range(8):
+                acc[k] = (_vsad(_fshr(acc[k], acc[(k + 1) & 7], sh), z[k]) + acc[k]) & M
+        r = 0
+        for k in range(8):
+            r ^= acc[k]
+        assert int(got[t]) == r, t
+    assert sme.packed_sad_rate(ctas_per_sm=2, iters=2000, reps=1) > 0

@@ -336,9 +336,9 @@ def measure_learned(sme, torch, args, net, est, luma, alpha, flush):
 
 def learned_oracle_leg(seq, plain, learned, seeds, pairs_judged=(0, 9, 18, 27)):
     """Oracle leg of the learned measurement: the learned-seeded MV field
-    against the oracle given the same seeds, and the judge of both fields:
-    exhaustive search (the ES row of Table 1) on a sample of pairs, mean SAD
-    above the ES optimum over the opaque MBs."""
+    against the oracle given the same seeds, and both fields measured
+    against exhaustive search (the ES row of Table 1) on a sample of pairs:
+    mean SAD above the ES optimum over the opaque MBs."""
     import oracle as O
 
     p = O.OracleParams(W, H, S, SUBPEL)

@@ -1639,18 +1639,22 @@ int sme_batch_upload(sme_batch* b, const sme_host_io* io, int n)
         if (cudaStreamWaitEvent(b->copy[c], b->fork, 0) != cudaSuccess) return SME_ERR_CUDA;
     const void* last_luma = nullptr;
     int next = 0;
+    // A mapped pinned buffer is read by the SMs (on the batch's stream, after
+    // the work queued there); any other buffer goes to the copy engines.
+    auto copy = [&](void* dst, const void* src, size_t bytes) {
+        const void* m = mapped_host(src);
+        if (m && aligned16(m) && aligned16(dst) && bytes % 16 == 0)
+            return launch_host_copy(dst, m, bytes, b->num_sms, b->stream) == cudaSuccess;
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->copy[next++ % K]) == cudaSuccess;
+    };
     for (int i = 0; i < n; ++i) {
         const SeqDesc& d = b->host_desc[i];
         const size_t bytes = (size_t)d.F * d.W * d.H;
         // a luma plane shared with the previous sequence (the same device
         // address: the VOPs of one scene) is copied once
-        if (d.luma != last_luma && cudaMemcpyAsync((void*)d.luma, io[i].luma, bytes, cudaMemcpyHostToDevice,
-                                                   b->copy[next++ % K]) != cudaSuccess)
-            return SME_ERR_CUDA;
+        if (d.luma != last_luma && !copy((void*)d.luma, io[i].luma, bytes)) return SME_ERR_CUDA;
         last_luma = d.luma;
-        if (cudaMemcpyAsync((void*)d.alpha, io[i].alpha, bytes, cudaMemcpyHostToDevice, b->copy[next++ % K]) !=
-            cudaSuccess)
-            return SME_ERR_CUDA;
+        if (!copy((void*)d.alpha, io[i].alpha, bytes)) return SME_ERR_CUDA;
     }
     for (int c = 0; c < K; ++c)
         if (cudaEventRecord(b->join[c], b->copy[c]) != cudaSuccess ||

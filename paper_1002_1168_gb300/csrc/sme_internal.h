@@ -236,6 +236,7 @@ cudaError_t launch_me_sparse(const Method& m, const MeArgs& a, int grid, int min
 
 // Exhaustive search over V for every MB of `pairs` frame pairs (sme_es.cu).
 size_t es_smem_bytes(int S, int h);
+cudaError_t launch_host_copy(void* dst, const void* src, size_t bytes, int num_sms, cudaStream_t s);
 cudaError_t launch_packed_sad_rate(int ctas_per_sm, int iters, uint32_t* out, cudaStream_t s, int* grid);
 cudaError_t launch_es(const uint8_t* luma, int W, int H, int S, int h, int rd, int pairs, sme_mv* mv, uint32_t* sad,
                       cudaStream_t s);

@@ -1565,6 +1565,26 @@ __global__ void __launch_bounds__(32 * kMeWarps) me_kernel(const MeArgs a)
 }
 
 
+// ==================================================== host-buffer copies ==
+// dst <- src for n 16-byte words, src a pinned host buffer read through its
+// device mapping: every SM takes part, four loads in flight per thread, so
+// the CPU-GPU link rather than the copy engines sets the rate.
+__global__ void __launch_bounds__(1024) host_copy_kernel(uint4* __restrict__ dst, const uint4* __restrict__ src,
+                                                         size_t n)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n; i += stride) dst[i] = src[i];
+}
+
+
 // ===================================================== sparse schedule ==
 // Throughput form for batches where most MBs are transparent.  Fig. 1 gives
 // a transparent MB the vector (0,0) without any evaluation, so its outputs
@@ -3259,6 +3279,13 @@ __global__ void __launch_bounds__(32 * kQueryWarps) query_kernel(const Geom g, c
 }  // namespace
 
 size_t me_smem_bytes(int S) { return (size_t)kMeWarps * warp_smem(S); }
+
+cudaError_t launch_host_copy(void* dst, const void* src, size_t bytes, int num_sms, cudaStream_t s)
+{
+    host_copy_kernel<<<2 * num_sms, 1024, 0, s>>>(reinterpret_cast<uint4*>(dst), reinterpret_cast<const uint4*>(src),
+                                                   bytes / 16);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_classify(const Geom& g, const ClassifyArgs& a, cudaStream_t s)
 {

@@ -1051,8 +1051,8 @@ __device__ __forceinline__ MbResult search_mb(const Method& m, int cls, const ui
                 best = c;
             }
         PrsStep none;
-        opaque_search<false>(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, sad, cs8, nc, best, slog, nlog, lane, false,
-                      0, none, res);
+        opaque_search<false>(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, sad, cs8, nc, best, slog, nlog,
+                             lane, false, 0, none, res);
         res.nlog = nlog;
         return res;
     }
@@ -1193,7 +1193,7 @@ __device__ __forceinline__ void mb_factors(const GradNb& gn, int W, int H, int x
     ny = (int)__reduce_add_sync(kFull, (unsigned)cy);
 }
 
-// The seed of MB idx in MV units, rounded and clamped to V.
+// A seed (pixels) in MV units, rounded and clamped to V (reading c19).
 __device__ __forceinline__ int seed_key_of(float x, float y, int h, const VRange& V)
 {
     const float sx = fminf(fmaxf(__fmul_rn((float)h, x), -1024.0f), 1024.0f);
@@ -1513,8 +1513,8 @@ __device__ __forceinline__ bool me_one_mb(const MeArgs& a, const Method& m, int 
     if (cls == SME_OPAQUE) {
         // Sec. 3.2 (the first step may be the speculative one, taken at
         // the same position).
-        opaque_search<kSparse>(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, ccost, cs8, nc, bi, slog, nlog, lane,
-                      spec, spec_key, sp, r);
+        opaque_search<kSparse>(m, win, pitch, lx, ly, c8, ux, uy, nx, ny, V, cand, ccost, cs8, nc, bi, slog, nlog,
+                               lane, spec, spec_key, sp, r);
     } else {
         int bk = cand[0];
 #pragma unroll
